@@ -1,0 +1,127 @@
+/*
+ * lc.h -- C ABI of the GB300 LocalContraction connected-components library.
+ *
+ * Method: "Connected Components at Scale via Local Contractions" (Lacki,
+ * Mirrokni, Wlodarczyk; arXiv 1807.10727).  Each phase (Section 3) draws a fresh
+ * random vertex ordering rho, maps every vertex to the minimum-rank vertex of
+ * its closed neighbourhood N(v) (Section 2 defines N(v) to contain v), merges
+ * the arborescences of that parent map, found by pointer jumping (Theorem
+ * thm:tree-rounds), relabels, deduplicates and compacts the edges (the O(1)-round
+ * contraction lemma; isolated nodes dropped as in Section 7), and repeats until
+ * no edges remain (Section 3).  The per-phase maps are composed back down to the
+ * input vertices (Section 7) and every vertex is labelled with the smallest
+ * input id of its connected component.
+ *
+ * Conventions shared by every entry point:
+ *  - Vertex ids are uint32 in [0, n); n <= 2^32 - 1.  Edges are undirected COO
+ *    pairs (src[j], dst[j]), j < m, m <= 2^32 - 1; self-loops and duplicate
+ *    edges are allowed and ignored by the result.
+ *  - "device" pointers are CUDA global-memory pointers of the current device;
+ *    "host" pointers are CPU memory (pinned memory gives full copy speed).
+ *  - All GPU work is ordered on the CUDA stream given at creation (a
+ *    cudaStream_t passed as void*; NULL = the legacy default stream).
+ *    lc_run / lc_run_host return after the phase counters and labels have been
+ *    produced on that stream and the counters copied to the host.
+ *  - No call throws; every call returns an lc_status.  On an error the outputs
+ *    are unspecified and the context stays usable unless the status is
+ *    LC_ERR_CUDA (a CUDA runtime error, after which the context should be
+ *    destroyed).
+ *  - A context is not thread-safe: one host thread at a time per context.
+ */
+#ifndef LC_H
+#define LC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lc_ctx lc_ctx; /* opaque; owns all device scratch memory */
+
+typedef enum {
+  LC_OK = 0,
+  LC_ERR_INVALID = 1,        /* bad argument, vertex id >= n, or output cap too small */
+  LC_ERR_OOM = 2,            /* a device allocation failed */
+  LC_ERR_CUDA = 3,           /* a CUDA runtime call failed */
+  LC_ERR_NO_CONVERGENCE = 4, /* more phases than the round cap (64 + 4*ceil(log2 n)) */
+  LC_ERR_TIMEOUT = 5         /* a bounded device-side wait gave up */
+} lc_status;
+
+typedef enum {
+  LC_VARIANT_FOREST = 0,  /* closed-N parent, arborescences (default, Section 2/3) */
+  LC_VARIANT_TWO_HOP = 1, /* label = min rank over N(N(v)) (Section 3, LocalContraction) */
+  LC_VARIANT_TREE = 2     /* open-N parent, weakly connected components (TreeContraction) */
+} lc_variant;
+
+/* Create a context for one graph.
+ *   n        number of vertices.
+ *   d_src, d_dst  device uint32[m] edge endpoints, caller-owned, read-only for
+ *            the lifetime of the context (never written).  Both NULL: the
+ *            context allocates its own device input buffers of m edges, filled
+ *            by lc_run_host.
+ *   m        number of edges (may be 0).
+ *   seed     seed of the phase orderings: phase i ranks vertex v of G_i by the
+ *            high 32 bits of SplitMix64 (Steele, Lea, Flood 2014) output v+1 of
+ *            the stream seeded with output i+1 of the stream seeded with seed;
+ *            ties go to the smaller id (Section 3 asks for a uniformly random
+ *            priority, redrawn every phase).
+ *   stream   cudaStream_t as void*.
+ *   out      receives the context.
+ * Allocates all device scratch for a run (about 16*m + 40*n bytes plus sort
+ * status words); returns LC_ERR_OOM if that fails.  Ids are validated on the
+ * device during lc_run (LC_ERR_INVALID from lc_run). */
+lc_status lc_create(uint32_t n, const uint32_t* d_src, const uint32_t* d_dst, uint64_t m,
+                    uint64_t seed, void* stream, lc_ctx** out);
+
+/* Select the phase variant (default LC_VARIANT_FOREST) and the small-graph
+ * finish: once 0 < m_i <= finish_edges, that phase merges each connected
+ * component of G_i into one node (the paper's single-machine union-find finish,
+ * Section 7).  finish_edges = 0 (default) disables it.  Both change the phase
+ * count and per-phase sizes, never the labels. */
+lc_status lc_configure(lc_ctx* ctx, lc_variant variant, uint64_t finish_edges);
+
+/* Run the whole phase loop.
+ *   d_labels  device uint32[n], caller-owned: labels[v] = smallest vertex id in
+ *             v's connected component.
+ *   rounds    host: number of phases R.  R = 0 exactly when m == 0; an input of
+ *             self-loops only runs one phase.
+ *   n_i, m_i  host uint64[cap]: vertices and edges of G_i for i < R (G_0 is the
+ *             input as given, loops and duplicates counted in m_0).
+ *   cap       length of n_i and m_i; R > cap gives LC_ERR_INVALID with *rounds
+ *             set and the first cap entries filled.
+ * Any of rounds / n_i / m_i may be NULL (then cap is ignored). */
+lc_status lc_run(lc_ctx* ctx, uint32_t* d_labels, uint32_t* rounds, uint64_t* n_i, uint64_t* m_i,
+                 uint32_t cap);
+
+/* End-to-end variant for a context created with NULL edge pointers: copies the
+ * host edge arrays h_src/h_dst (uint32[m]) to the device, runs the phase loop
+ * and copies the labels to host h_labels (uint32[n]); other arguments as in
+ * lc_run. */
+lc_status lc_run_host(lc_ctx* ctx, const uint32_t* h_src, const uint32_t* h_dst,
+                      uint32_t* h_labels, uint32_t* rounds, uint64_t* n_i, uint64_t* m_i,
+                      uint32_t cap);
+
+/* Diagnostics of the last successful run, host uint64[cap] each (NULL to skip):
+ * mp_i = edges of phase i left after relabelling and loop removal, before
+ * deduplication.  Returns the phase count in *rounds. */
+lc_status lc_last_stats(const lc_ctx* ctx, uint32_t* rounds, uint64_t* mp_i, uint32_t cap);
+
+/* Release the context and all its device memory (stream-ordered frees after a
+ * synchronisation of the context's stream).  NULL is accepted. */
+lc_status lc_destroy(lc_ctx* ctx);
+
+/* Static text for a status code. */
+const char* lc_status_str(lc_status s);
+
+/* Phase ordering rank, for parity checks: the 32-bit rank of vertex v in phase
+ * i, computed on the device by the same code the phases use.  d_out is device
+ * uint32[count] receiving rank(seed, i, v0 + j) for j < count. */
+lc_status lc_rank_probe(uint64_t seed, uint32_t i, uint32_t v0, uint32_t count, uint32_t* d_out,
+                        void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LC_H */

@@ -1,0 +1,381 @@
+// C ABI of liblc.so (include/lc.h): context management and the host-driven
+// phase loop of LocalContraction (arXiv 1807.10727, Section 3), one CUDA
+// stream, one device synchronisation per phase to read the phase's sizes.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "lc_internal.cuh"
+
+using namespace lc;
+
+namespace {
+
+// Level storage of one phase: the root map, the min-original-id of each
+// node, and the exclusive scan of "node keeps an edge" (n + 1 words).
+struct Level {
+  uint32_t n;
+  uint32_t* root;
+  uint32_t* mo;
+  uint32_t* scan;
+};
+
+// Bump arena for the per-phase arrays; grows by whole chunks when a run needs
+// more than the first chunk (only when the phases shrink slowly).
+struct Arena {
+  std::vector<std::pair<uint32_t*, uint64_t>> chunks;  // (base, words)
+  size_t cur = 0;
+  uint64_t used = 0;
+  cudaError_t init(uint64_t words) {
+    uint32_t* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, std::max<uint64_t>(words, 1024) * 4);
+    if (e != cudaSuccess) return e;
+    chunks.push_back({p, std::max<uint64_t>(words, 1024)});
+    return cudaSuccess;
+  }
+  void reset() { cur = 0; used = 0; }
+  uint32_t* alloc(uint64_t words, cudaError_t* err) {
+    words = (words + 63) & ~63ull;  // 256-byte aligned pieces
+    while (cur < chunks.size()) {
+      if (used + words <= chunks[cur].second) {
+        uint32_t* p = chunks[cur].first + used;
+        used += words;
+        return p;
+      }
+      ++cur;
+      used = 0;
+    }
+    uint64_t sz = std::max<uint64_t>(words, chunks.empty() ? words : chunks.back().second);
+    uint32_t* p = nullptr;
+    *err = cudaMalloc(&p, sz * 4);
+    if (*err != cudaSuccess) return nullptr;
+    chunks.push_back({p, sz});
+    cur = chunks.size() - 1;
+    used = words;
+    return p;
+  }
+  void release() {
+    for (auto& c : chunks) cudaFree(c.first);
+    chunks.clear();
+  }
+};
+
+uint64_t host_mix(uint64_t z) { return splitmix_mix(z); }
+
+// Stream seed of phase i: output i+1 of the SplitMix64 stream seeded with seed.
+uint64_t phase_seed(uint64_t seed, uint32_t i) { return host_mix(seed + (uint64_t)(i + 1) * kGamma); }
+
+int bits_for(uint32_t n) {
+  int b = 1;
+  while (b < 32 && (1ull << b) < n) ++b;
+  return b;
+}
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+    else prev = -1;
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+}  // namespace
+
+struct lc_ctx {
+  uint32_t n = 0;
+  uint64_t m = 0;
+  uint64_t seed = 0;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  Launch L{};
+  lc_variant variant = LC_VARIANT_FOREST;
+  uint64_t finish_edges = 0;
+
+  const uint32_t* src = nullptr;
+  const uint32_t* dst = nullptr;
+  uint32_t* own_src = nullptr;
+  uint32_t* own_dst = nullptr;
+  uint32_t* own_labels = nullptr;
+
+  unsigned long long* minkey = nullptr;
+  uint8_t* flags = nullptr;
+  uint64_t* ebuf[2] = {nullptr, nullptr};
+  Counters* ctr = nullptr;
+  Counters* h_ctr = nullptr;
+  SortScratch sort;
+  Arena arena;
+  std::vector<Level> levels;
+
+  uint32_t last_rounds = 0;
+  std::vector<uint64_t> last_mp;
+};
+
+#define LC_TRY(call)                                  \
+  do {                                                \
+    cudaError_t e_ = (call);                          \
+    if (e_ != cudaSuccess) return status_of(e_);      \
+  } while (0)
+
+static lc_status status_of(cudaError_t e) {
+  if (e == cudaSuccess) return LC_OK;
+  if (e == cudaErrorMemoryAllocation) return LC_ERR_OOM;
+  return LC_ERR_CUDA;
+}
+
+static void free_ctx(lc_ctx* c) {
+  if (!c) return;
+  cudaFree(c->own_src);
+  cudaFree(c->own_dst);
+  cudaFree(c->own_labels);
+  cudaFree(c->minkey);
+  cudaFree(c->flags);
+  cudaFree(c->ebuf[0]);
+  cudaFree(c->ebuf[1]);
+  cudaFree(c->ctr);
+  if (c->h_ctr) cudaFreeHost(c->h_ctr);
+  cudaFree(c->sort.status);
+  cudaFree(c->sort.hist);
+  cudaFree(c->sort.tickets);
+  c->arena.release();
+  delete c;
+}
+
+static lc_status alloc_ctx(lc_ctx* c) {
+  const uint64_t n = c->n, m = c->m;
+  LC_TRY(cudaMalloc(&c->minkey, std::max<uint64_t>(n, 1) * 8));
+  LC_TRY(cudaMalloc(&c->flags, ((n + 15) & ~15ull) + 16));
+  LC_TRY(cudaMalloc(&c->ebuf[0], std::max<uint64_t>(m, 2) * 8));
+  LC_TRY(cudaMalloc(&c->ebuf[1], std::max<uint64_t>(m, 2) * 8));
+  LC_TRY(cudaMalloc(&c->ctr, sizeof(Counters)));
+  LC_TRY(cudaMemset(c->ctr, 0, sizeof(Counters)));
+  LC_TRY(cudaMallocHost(&c->h_ctr, sizeof(Counters)));
+  c->sort.status_words = std::max(sort_status_words(m), sort_status_words(n));
+  LC_TRY(cudaMalloc(&c->sort.status, c->sort.status_words * 8));
+  LC_TRY(cudaMemset(c->sort.status, 0, c->sort.status_words * 8));
+  LC_TRY(cudaMalloc(&c->sort.hist, sizeof(uint32_t) * kMaxPasses * kRadix));
+  LC_TRY(cudaMalloc(&c->sort.tickets, sizeof(unsigned) * 16));
+  // first arena chunk: 3 arrays per level for levels whose sizes sum to 2n,
+  // plus the next level's min-original-id array
+  LC_TRY(c->arena.init(4 * (2 * n + 256)));
+  return LC_OK;
+}
+
+extern "C" lc_status lc_create(uint32_t n, const uint32_t* d_src, const uint32_t* d_dst,
+                               uint64_t m, uint64_t seed, void* stream, lc_ctx** out) {
+  if (out == nullptr) return LC_ERR_INVALID;
+  *out = nullptr;
+  if ((d_src == nullptr) != (d_dst == nullptr)) return LC_ERR_INVALID;
+  if (m > 0xFFFFFFFFull) return LC_ERR_INVALID;
+  if (n == 0 && m > 0) return LC_ERR_INVALID;
+  lc_ctx* c = new (std::nothrow) lc_ctx();
+  if (!c) return LC_ERR_OOM;
+  c->n = n;
+  c->m = m;
+  c->seed = seed;
+  c->stream = (cudaStream_t)stream;
+  if (cudaGetDevice(&c->device) != cudaSuccess) {
+    delete c;
+    return LC_ERR_CUDA;
+  }
+  if (cudaDeviceGetAttribute(&c->L.sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) {
+    delete c;
+    return LC_ERR_CUDA;
+  }
+  c->L.stream = c->stream;
+  c->src = d_src;
+  c->dst = d_dst;
+  lc_status st = alloc_ctx(c);
+  if (st == LC_OK && d_src == nullptr) {
+    cudaError_t e = cudaMalloc(&c->own_src, std::max<uint64_t>(m, 1) * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&c->own_dst, std::max<uint64_t>(m, 1) * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&c->own_labels, std::max<uint64_t>(n, 1) * 4);
+    st = status_of(e);
+    c->src = c->own_src;
+    c->dst = c->own_dst;
+  }
+  if (st != LC_OK) {
+    free_ctx(c);
+    cudaGetLastError();
+    return st;
+  }
+  *out = c;
+  return LC_OK;
+}
+
+extern "C" lc_status lc_configure(lc_ctx* c, lc_variant variant, uint64_t finish_edges) {
+  if (!c) return LC_ERR_INVALID;
+  if (variant != LC_VARIANT_FOREST) return LC_ERR_INVALID;  // other variants: not built yet
+  c->variant = variant;
+  c->finish_edges = finish_edges;
+  if (finish_edges != 0) return LC_ERR_INVALID;
+  return LC_OK;
+}
+
+static uint32_t round_cap(uint32_t n) { return 64 + 4 * (uint32_t)bits_for(std::max(n, 2u)); }
+
+static lc_status run_loop(lc_ctx* c, uint32_t* d_labels, uint32_t* rounds, uint64_t* n_i,
+                          uint64_t* m_i, uint32_t cap) {
+  const Launch& L = c->L;
+  c->last_rounds = 0;
+  c->last_mp.clear();
+  if (rounds) *rounds = 0;
+  if (c->n == 0) return LC_OK;
+  if (c->m == 0) {
+    identity_labels(d_labels, c->n, L);
+    LC_TRY(cudaGetLastError());
+    LC_TRY(cudaStreamSynchronize(c->stream));
+    return LC_OK;
+  }
+  c->arena.reset();
+  c->levels.clear();
+  LC_TRY(cudaMemsetAsync(c->ctr, 0, sizeof(Counters), c->stream));
+  cudaError_t aerr = cudaSuccess;
+  uint32_t ni = c->n;
+  uint64_t mi = c->m;
+  const uint64_t* packed = nullptr;  // current edges when not the input
+  uint32_t* mo_cur = c->arena.alloc(ni, &aerr);
+  LC_TRY(aerr);
+  std::vector<uint64_t> hn, hm;
+  const uint32_t cap_rounds = round_cap(c->n);
+  unsigned* err = &c->ctr->err;
+  for (uint32_t i = 0; mi > 0; ++i) {
+    if (i >= cap_rounds) return LC_ERR_NO_CONVERGENCE;
+    Level lv{ni, c->arena.alloc(ni, &aerr), mo_cur, nullptr};
+    LC_TRY(aerr);
+    lv.scan = c->arena.alloc((uint64_t)ni + 1, &aerr);
+    LC_TRY(aerr);
+    uint32_t* mo_next = c->arena.alloc(ni, &aerr);
+    LC_TRY(aerr);
+    const uint64_t rk = phase_seed(c->seed, i);
+    const int bits = bits_for(ni);
+    // (a) + (b): ranks and closed-neighbourhood minimum
+    init_keys(c->minkey, i == 0 ? lv.mo : nullptr, ni, rk, L);
+    edge_min(i == 0 ? c->src : nullptr, i == 0 ? c->dst : nullptr, packed, mi, ni, rk, c->minkey,
+             err, L);
+    // (c): roots of the parent arborescences
+    jump(c->minkey, lv.root, lv.mo, ni, L);
+    // (d): relabel, drop loops, sort, deduplicate, compact
+    LC_TRY(cudaMemsetAsync(c->ctr, 0, 3 * sizeof(unsigned long long), c->stream));
+    LC_TRY(cudaMemsetAsync(c->flags, 0, ni, c->stream));
+    uint64_t* keys = (packed == c->ebuf[0]) ? c->ebuf[1] : c->ebuf[0];
+    uint64_t* alt = (keys == c->ebuf[0]) ? c->ebuf[1] : c->ebuf[0];
+    relabel(i == 0 ? c->src : nullptr, i == 0 ? c->dst : nullptr, packed, mi, ni, lv.root, bits,
+            keys, &c->ctr->mprime, L);
+    int which = radix_sort_u64(keys, alt, &c->ctr->mprime, mi, 2 * bits, c->sort, err, c->flags,
+                               bits, L);
+    uint64_t* sorted = which ? alt : keys;
+    uint64_t* next = which ? keys : alt;
+    scan_flags(c->flags, lv.scan, ni, lv.mo, mo_next, &c->ctr->n_next, c->sort, err, L);
+    unique_rename(sorted, &c->ctr->mprime, mi, bits, lv.scan, next, &c->ctr->m_next, c->sort, err,
+                  L);
+    LC_TRY(cudaGetLastError());
+    LC_TRY(cudaMemcpyAsync(c->h_ctr, c->ctr, sizeof(Counters), cudaMemcpyDeviceToHost, c->stream));
+    LC_TRY(cudaStreamSynchronize(c->stream));
+    if (c->h_ctr->err & kErrBadVertex) return LC_ERR_INVALID;
+    if (c->h_ctr->err & kErrTimeout) return LC_ERR_TIMEOUT;
+    hn.push_back(ni);
+    hm.push_back(mi);
+    c->last_mp.push_back(c->h_ctr->mprime);
+    c->levels.push_back(lv);
+    ni = (uint32_t)c->h_ctr->n_next;
+    mi = c->h_ctr->m_next;
+    packed = next;
+    mo_cur = mo_next;
+  }
+  const uint32_t R = (uint32_t)c->levels.size();
+  // (e): compose the phase maps top-down; level i's labels overwrite its root
+  // array in place (level 0 writes the caller's labels)
+  for (int i = (int)R - 1; i >= 0; --i) {
+    const Level& lv = c->levels[i];
+    const uint32_t* up = (i + 1 < (int)R) ? c->levels[i + 1].root : nullptr;
+    uint32_t* out = i == 0 ? d_labels : lv.root;
+    propagate(lv.root, lv.scan, lv.mo, up, out, lv.n, L);
+  }
+  LC_TRY(cudaGetLastError());
+  LC_TRY(cudaStreamSynchronize(c->stream));
+  c->last_rounds = R;
+  if (rounds) *rounds = R;
+  if (n_i || m_i) {
+    for (uint32_t i = 0; i < std::min(R, cap); ++i) {
+      if (n_i) n_i[i] = hn[i];
+      if (m_i) m_i[i] = hm[i];
+    }
+    if (R > cap) return LC_ERR_INVALID;
+  }
+  return LC_OK;
+}
+
+extern "C" lc_status lc_run(lc_ctx* c, uint32_t* d_labels, uint32_t* rounds, uint64_t* n_i,
+                            uint64_t* m_i, uint32_t cap) {
+  if (!c || (!d_labels && c->n > 0)) return LC_ERR_INVALID;
+  DeviceGuard g(c->device);
+  return run_loop(c, d_labels, rounds, n_i, m_i, cap);
+}
+
+extern "C" lc_status lc_run_host(lc_ctx* c, const uint32_t* h_src, const uint32_t* h_dst,
+                                 uint32_t* h_labels, uint32_t* rounds, uint64_t* n_i,
+                                 uint64_t* m_i, uint32_t cap) {
+  if (!c || !c->own_src) return LC_ERR_INVALID;
+  if (c->m > 0 && (!h_src || !h_dst)) return LC_ERR_INVALID;
+  if (c->n > 0 && !h_labels) return LC_ERR_INVALID;
+  DeviceGuard g(c->device);
+  if (c->m > 0) {
+    LC_TRY(cudaMemcpyAsync(c->own_src, h_src, c->m * 4, cudaMemcpyHostToDevice, c->stream));
+    LC_TRY(cudaMemcpyAsync(c->own_dst, h_dst, c->m * 4, cudaMemcpyHostToDevice, c->stream));
+  }
+  lc_status st = run_loop(c, c->own_labels, rounds, n_i, m_i, cap);
+  if (st != LC_OK && st != LC_ERR_INVALID) return st;
+  if (c->n > 0) {
+    LC_TRY(cudaMemcpyAsync(h_labels, c->own_labels, (uint64_t)c->n * 4, cudaMemcpyDeviceToHost,
+                           c->stream));
+    LC_TRY(cudaStreamSynchronize(c->stream));
+  }
+  return st;
+}
+
+extern "C" lc_status lc_last_stats(const lc_ctx* c, uint32_t* rounds, uint64_t* mp_i,
+                                   uint32_t cap) {
+  if (!c) return LC_ERR_INVALID;
+  if (rounds) *rounds = c->last_rounds;
+  if (mp_i)
+    for (uint32_t i = 0; i < std::min<uint32_t>(cap, (uint32_t)c->last_mp.size()); ++i)
+      mp_i[i] = c->last_mp[i];
+  return LC_OK;
+}
+
+extern "C" lc_status lc_destroy(lc_ctx* c) {
+  if (!c) return LC_OK;
+  DeviceGuard g(c->device);
+  cudaStreamSynchronize(c->stream);
+  free_ctx(c);
+  return LC_OK;
+}
+
+extern "C" const char* lc_status_str(lc_status s) {
+  switch (s) {
+    case LC_OK: return "ok";
+    case LC_ERR_INVALID: return "invalid argument or input";
+    case LC_ERR_OOM: return "device allocation failed";
+    case LC_ERR_CUDA: return "CUDA runtime error";
+    case LC_ERR_NO_CONVERGENCE: return "phase count exceeded the round cap";
+    case LC_ERR_TIMEOUT: return "a bounded device wait gave up";
+  }
+  return "unknown status";
+}
+
+extern "C" lc_status lc_rank_probe(uint64_t seed, uint32_t i, uint32_t v0, uint32_t count,
+                                   uint32_t* d_out, void* stream) {
+  if (count > 0 && !d_out) return LC_ERR_INVALID;
+  Launch L{(cudaStream_t)stream, 1};
+  int dev = 0;
+  LC_TRY(cudaGetDevice(&dev));
+  LC_TRY(cudaDeviceGetAttribute(&L.sms, cudaDevAttrMultiProcessorCount, dev));
+  rank_probe(phase_seed(seed, i), v0, count, d_out, L);
+  LC_TRY(cudaGetLastError());
+  return LC_OK;
+}

@@ -1,0 +1,75 @@
+// Device-side building blocks shared by the LocalContraction kernels.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "lc.h"
+
+namespace lc {
+
+// ---------------------------------------------------------------- ranking
+// SplitMix64 (Steele, Lea, Flood, "Fast splittable pseudorandom number
+// generators", OOPSLA 2014): state advances by the golden-ratio increment and
+// each output is the state passed through the variant-13 mixing function.
+constexpr uint64_t kGamma = 0x9E3779B97F4A7C15ull;
+
+__host__ __device__ __forceinline__ uint64_t splitmix_mix(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// Phase key of vertex v: rank in the high 32 bits, id in the low 32 bits, so
+// comparisons give a total order with ties broken by the smaller id.  `rk` is
+// the phase's stream seed (output i+1 of the stream seeded with the run seed).
+__device__ __forceinline__ uint64_t phase_key(uint64_t rk, uint32_t v) {
+  return (splitmix_mix(rk + (uint64_t)(v + 1ull) * kGamma) & 0xFFFFFFFF00000000ull) | v;
+}
+
+// ---------------------------------------------------------------- errors
+// Device error word bits (OR-ed in by kernels, read back by the host).
+enum : uint32_t {
+  kErrBadVertex = 1u,  // an input endpoint was >= n
+  kErrTimeout = 2u,    // a bounded spin-wait gave up
+};
+
+// Iteration limit of every spin-wait on another block's status word.
+constexpr uint32_t kSpinLimit = 1u << 24;
+
+// Per-run device counters, read back once per phase with one small copy.
+struct Counters {
+  unsigned long long mprime;   // keys emitted by relabel (m'_i)
+  unsigned long long m_next;   // unique edges (m_{i+1})
+  unsigned long long n_next;   // surviving nodes (n_{i+1})
+  unsigned int err;            // kErr* bits
+  unsigned int tile_ticket[7]; // dynamic tile counters (reset per launch)
+};
+
+__device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+  unsigned m;
+  asm volatile("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+// 64-bit status words of the single-pass (decoupled look-back) scans:
+// [63:34] epoch, [33:32] flag, [31:0] value.
+constexpr uint64_t kFlagAgg = 1ull;
+constexpr uint64_t kFlagPrefix = 2ull;
+
+__device__ __forceinline__ uint64_t pack_status(uint32_t epoch, uint64_t flag, uint32_t v) {
+  return ((uint64_t)epoch << 34) | (flag << 32) | v;
+}
+
+__device__ __forceinline__ void store_status(uint64_t* p, uint64_t w) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(w) : "memory");
+}
+
+__device__ __forceinline__ uint64_t load_status(const uint64_t* p) {
+  uint64_t w;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(w) : "l"(p) : "memory");
+  return w;
+}
+
+}  // namespace lc

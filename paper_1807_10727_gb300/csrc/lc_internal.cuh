@@ -1,0 +1,101 @@
+// Host-side launchers of the LocalContraction kernels (internal to liblc.so).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "lc_common.cuh"
+
+namespace lc {
+
+struct Launch {
+  cudaStream_t stream;
+  int sms;  // multiprocessor count of the device
+};
+
+// ---------------------------------------------------------- radix sort
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 16;
+constexpr int kSortTile = kSortThreads * kSortItems;  // 4096 keys per tile
+constexpr int kRadixBits = 8;
+constexpr int kRadix = 1 << kRadixBits;
+constexpr int kMaxPasses = 8;
+
+// Scratch of the onesweep sort and the single-pass scans.  `status` holds one
+// 64-bit look-back word per (tile, digit); epochs make stale words invalid so
+// the array never needs clearing between launches.
+struct SortScratch {
+  uint64_t* status = nullptr;     // [status_words]
+  uint64_t status_words = 0;
+  uint32_t* hist = nullptr;       // [kMaxPasses * kRadix] global digit counts / offsets
+  unsigned* tickets = nullptr;    // [16] dynamic tile counters
+  uint32_t epoch = 0;             // last epoch used (1..2^30-1)
+};
+
+uint64_t sort_status_words(uint64_t max_keys);
+
+// Next epoch for a look-back launch; clears the status array when the epoch
+// counter wraps.
+uint32_t next_epoch(SortScratch& s, const Launch& L);
+
+// Stable LSD radix sort of keys[0, *d_count) on bits [0, key_bits) with 8-bit
+// digits (onesweep: one histogram pass, then one single-pass scatter per digit
+// with decoupled look-back).  `max_count` bounds *d_count and sizes the grids.
+// The sorted keys end in keys or alt; the return value says which (0 = keys).
+// When mark_flags is non-null the last pass also sets mark_flags[a] =
+// mark_flags[b] = 1 for every key (a << half_bits | b) (used to find the nodes
+// that keep an edge).
+int radix_sort_u64(uint64_t* keys, uint64_t* alt, const unsigned long long* d_count,
+                   uint64_t max_count, int key_bits, SortScratch& s, unsigned* err,
+                   uint8_t* mark_flags, int half_bits, const Launch& L);
+
+// In-place exclusive scan of flags[0, n) (values 0/1 as uint8) into
+// out[0, n] (uint32, out[n] = total); for every kept r (flag set) also copies
+// mo_in[r] to mo_out[out[r]] when mo_out is non-null.  *total gets the sum.
+void scan_flags(const uint8_t* flags, uint32_t* out, uint32_t n, const uint32_t* mo_in,
+                uint32_t* mo_out, unsigned long long* total, SortScratch& s, unsigned* err,
+                const Launch& L);
+
+// Compaction of the sorted keys[0, *d_count): keeps the first key of each run
+// of equal keys and writes it renamed through newid as (newid[a] << 32 |
+// newid[b]) to out in sorted order; *m_next gets the number kept.
+void unique_rename(const uint64_t* keys, const unsigned long long* d_count, uint64_t max_count,
+                   int half_bits, const uint32_t* newid, uint64_t* out,
+                   unsigned long long* m_next, SortScratch& s, unsigned* err, const Launch& L);
+
+// ---------------------------------------------------------- phase steps
+// minkey[v] = key(v) for v < n; when mo is non-null also mo[v] = v (phase 0).
+void init_keys(unsigned long long* minkey, uint32_t* mo, uint32_t n, uint64_t rk,
+               const Launch& L);
+
+// Closed-neighbourhood minimum: minkey[u] = min(minkey[u], key(v)) and
+// minkey[v] = min(minkey[v], key(u)) for every edge.  Edges are either two
+// uint32 arrays (src, dst) with ids validated against n (bad ids set
+// kErrBadVertex and are skipped), or packed uint64 (a << 32 | b) sorted by a
+// (packed != nullptr), in which case a-side updates are combined per warp.
+void edge_min(const uint32_t* src, const uint32_t* dst, const uint64_t* packed, uint64_t m,
+              uint32_t n, uint64_t rk, unsigned long long* minkey, unsigned* err,
+              const Launch& L);
+
+// root[v] = root of v's arborescence (follows the parent stored in the low
+// half of minkey, compressing as it goes); mo[root] = min over the tree of
+// mo[v] (phase 0: mo[v] = v).
+void jump(unsigned long long* minkey, uint32_t* root, uint32_t* mo, uint32_t n, const Launch& L);
+
+// Relabel every edge through root, drop self-loops, emit (min << bits | max)
+// keys compacted to keys_out; *count gets the number emitted.
+void relabel(const uint32_t* src, const uint32_t* dst, const uint64_t* packed, uint64_t m,
+             uint32_t n, const uint32_t* root, int bits, uint64_t* keys_out,
+             unsigned long long* count, const Launch& L);
+
+// labels_out[v] = kept(root[v]) ? labels_up[scan[root[v]]] : mo[root[v]], with
+// kept(r) = scan[r+1] > scan[r].  labels_out may alias root.
+void propagate(const uint32_t* root, const uint32_t* scan, const uint32_t* mo,
+               const uint32_t* labels_up, uint32_t* labels_out, uint32_t n, const Launch& L);
+
+// labels[v] = v (a graph without edges).
+void identity_labels(uint32_t* labels, uint32_t n, const Launch& L);
+
+// out[j] = high 32 bits of key(v0 + j) in the phase with stream seed rk.
+void rank_probe(uint64_t rk, uint32_t v0, uint32_t count, uint32_t* out, const Launch& L);
+
+}  // namespace lc

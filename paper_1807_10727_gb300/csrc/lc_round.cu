@@ -1,0 +1,309 @@
+// Per-phase kernels of the LocalContraction round loop (arXiv 1807.10727):
+// ranking and closed-neighbourhood parent (Section 2 N(v), Section 3 random
+// ordering), contraction of the parent arborescences by pointer jumping
+// (Theorem thm:tree-rounds), relabelling of the edges (O(1)-round contraction
+// lemma) and composition of the per-phase maps back to the input (Section 7).
+#include <algorithm>
+
+#include "lc_internal.cuh"
+
+namespace lc {
+namespace {
+
+constexpr unsigned kFull = 0xFFFFFFFFu;
+constexpr int kThreads = 256;
+
+inline int grid_for(uint64_t work, int per_block, const Launch& L, int blocks_per_sm = 8) {
+  uint64_t b = (work + per_block - 1) / per_block;
+  uint64_t cap = (uint64_t)L.sms * blocks_per_sm;
+  return (int)std::max<uint64_t>(1, std::min(b, cap));
+}
+
+// ------------------------------------------------------------ ranking
+
+__global__ void k_init_keys(unsigned long long* __restrict__ minkey, uint32_t* __restrict__ mo,
+                            uint32_t n, uint64_t rk) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+    minkey[v] = phase_key(rk, (uint32_t)v);
+    if (mo != nullptr) mo[v] = (uint32_t)v;
+  }
+}
+
+__global__ void k_rank_probe(uint64_t rk, uint32_t v0, uint32_t count, uint32_t* out) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < count; j += stride)
+    out[j] = (uint32_t)(phase_key(rk, (uint32_t)(v0 + j)) >> 32);
+}
+
+// ---------------------------------------------------- closed-N minimum
+
+__device__ __forceinline__ void min_edge(uint32_t u, uint32_t v, uint32_t n, uint64_t rk,
+                                         unsigned long long* minkey, unsigned* err) {
+  if (u >= n || v >= n) {
+    atomicOr(err, kErrBadVertex);
+    return;
+  }
+  if (u == v) return;  // v is in its own closed neighbourhood already
+  atomicMin(&minkey[u], (unsigned long long)phase_key(rk, v));
+  atomicMin(&minkey[v], (unsigned long long)phase_key(rk, u));
+}
+
+// Input edges as two uint32 arrays; `vec` = both arrays 16-byte aligned.
+__global__ void __launch_bounds__(kThreads) k_edge_min_soa(
+    const uint32_t* __restrict__ src, const uint32_t* __restrict__ dst, uint64_t m, uint32_t n,
+    uint64_t rk, unsigned long long* minkey, unsigned* err, int vec) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  const uint64_t gt = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  uint64_t done = 0;
+  if (vec) {
+    const uint64_t nq = m / 4;
+    const uint4* s4 = reinterpret_cast<const uint4*>(src);
+    const uint4* d4 = reinterpret_cast<const uint4*>(dst);
+    for (uint64_t q = gt; q < nq; q += stride) {
+      uint4 s = __ldcs(s4 + q), d = __ldcs(d4 + q);
+      min_edge(s.x, d.x, n, rk, minkey, err);
+      min_edge(s.y, d.y, n, rk, minkey, err);
+      min_edge(s.z, d.z, n, rk, minkey, err);
+      min_edge(s.w, d.w, n, rk, minkey, err);
+    }
+    done = nq * 4;
+  }
+  for (uint64_t j = done + gt; j < m; j += stride) min_edge(__ldcs(src + j), __ldcs(dst + j), n, rk, minkey, err);
+}
+
+// Minimum of a 64-bit value over the lanes of `peers` (all calling with the
+// same mask): first over the high halves, then over the low halves of the
+// lanes that hold the minimum high half.
+__device__ __forceinline__ uint64_t group_min_u64(unsigned peers, uint64_t x) {
+  uint32_t hi = (uint32_t)(x >> 32), lo = (uint32_t)x;
+  uint32_t mhi = __reduce_min_sync(peers, hi);
+  unsigned tie = __ballot_sync(peers, hi == mhi) & peers;
+  uint32_t mlo = 0;
+  if (hi == mhi) mlo = __reduce_min_sync(tie, lo);
+  mlo = __shfl_sync(peers, mlo, __ffs(tie) - 1);
+  return ((uint64_t)mhi << 32) | mlo;
+}
+
+// Packed edges (a << 32 | b) with a < b, sorted by a: the a-side minima of a
+// warp are combined per distinct a before one atomic per group.
+__global__ void __launch_bounds__(kThreads) k_edge_min_packed(
+    const uint64_t* __restrict__ e, uint64_t m, uint64_t rk, unsigned long long* minkey) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  const uint64_t npair = (m + 1) / 2;
+  const ulonglong2* e2 = reinterpret_cast<const ulonglong2*>(e);
+  // the loop trip count is uniform across the warp so the warp intrinsics see
+  // all 32 lanes
+  const uint64_t warp0 = ((uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u));
+  for (uint64_t q0 = warp0; q0 < npair; q0 += stride) {
+    uint64_t q = q0 + lane_id();
+    uint64_t x0 = ~0ull, x1 = ~0ull;
+    if (q < npair) {
+      if (2 * q + 1 < m) {
+        ulonglong2 p = __ldcs(e2 + q);
+        x0 = p.x;
+        x1 = p.y;
+      } else {
+        x0 = __ldcs(e + 2 * q);
+      }
+    }
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      uint64_t x = s == 0 ? x0 : x1;
+      bool valid = x != ~0ull;
+      uint32_t a = (uint32_t)(x >> 32), b = (uint32_t)x;
+      uint64_t kb = valid ? phase_key(rk, b) : ~0ull;
+      unsigned peers = __match_any_sync(kFull, valid ? a : 0xFFFFFFFFu);
+      uint64_t mk = group_min_u64(peers, kb);
+      if (valid) {
+        if ((peers & lanemask_lt()) == 0) atomicMin(&minkey[a], (unsigned long long)mk);
+        atomicMin(&minkey[b], (unsigned long long)phase_key(rk, a));
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------- pointer jumping
+
+__global__ void __launch_bounds__(kThreads) k_jump(unsigned long long* minkey,
+                                                   uint32_t* __restrict__ root,
+                                                   uint32_t* mo, uint32_t n) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+    uint32_t p = (uint32_t)minkey[v];
+    if (p != (uint32_t)v) {
+      // every stored pointer leads to an ancestor, so chasing ends at the
+      // root (the only vertex whose stored pointer is itself)
+      for (;;) {
+        uint32_t q = (uint32_t)minkey[p];
+        if (q == p) break;
+        p = q;
+      }
+      minkey[v] = p;  // compress: later chases through v go straight to the root
+      atomicMin(&mo[p], mo[v]);
+    }
+    root[v] = p;
+  }
+}
+
+// ----------------------------------------------------------- relabel
+
+constexpr int kRelItems = 16;
+
+__device__ __forceinline__ void relabel_one(uint32_t u, uint32_t v, bool valid, uint32_t n,
+                                            const uint32_t* __restrict__ root, int bits,
+                                            uint64_t& key, bool& keep) {
+  keep = false;
+  if (!valid || u >= n || v >= n) return;
+  uint32_t a = __ldg(root + u), b = __ldg(root + v);
+  if (a == b) return;
+  uint32_t lo = min(a, b), hi = max(a, b);
+  key = ((uint64_t)lo << bits) | hi;
+  keep = true;
+}
+
+// Each block handles tiles of kThreads * kRelItems edges; the block's keys are
+// compacted with a block scan and appended after one atomicAdd per tile.
+template <bool kPacked>
+__global__ void __launch_bounds__(kThreads) k_relabel(
+    const uint32_t* __restrict__ src, const uint32_t* __restrict__ dst,
+    const uint64_t* __restrict__ packed, uint64_t m, uint32_t n, const uint32_t* __restrict__ root,
+    int bits, uint64_t* __restrict__ keys_out, unsigned long long* count, int vec) {
+  __shared__ uint32_t ws[kThreads / 32];
+  __shared__ unsigned long long s_base;
+  const uint64_t tile_edges = (uint64_t)kThreads * kRelItems;
+  const uint64_t ntiles = (m + tile_edges - 1) / tile_edges;
+  const unsigned tid = threadIdx.x, lane = lane_id(), w = tid >> 5;
+  for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    // thread item i handles edge base + w*32*kRelItems + i*32 + lane (coalesced)
+    const uint64_t base = t * tile_edges + (uint64_t)w * 32 * kRelItems;
+    uint64_t key[kRelItems];
+    uint32_t keepmask = 0;
+#pragma unroll
+    for (int i = 0; i < kRelItems; ++i) {
+      uint64_t j = base + (uint64_t)i * 32 + lane;
+      bool valid = j < m;
+      uint32_t u = 0, v = 0;
+      if (valid) {
+        if (kPacked) {
+          uint64_t x = __ldcs(packed + j);
+          u = (uint32_t)(x >> 32);
+          v = (uint32_t)x;
+        } else {
+          u = __ldcs(src + j);
+          v = __ldcs(dst + j);
+        }
+      }
+      bool keep;
+      key[i] = 0;
+      relabel_one(u, v, valid, n, root, bits, key[i], keep);
+      keepmask |= (keep ? 1u : 0u) << i;
+    }
+    (void)vec;
+    // warp-level compaction offsets, then one block scan over warp totals
+    uint32_t mine = __popc(keepmask);
+    uint32_t incl = mine;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t y = __shfl_up_sync(kFull, incl, o);
+      if (lane >= (unsigned)o) incl += y;
+    }
+    if (lane == 31) ws[w] = incl;
+    __syncthreads();
+    if (tid == 0) {
+      uint32_t run = 0;
+      for (int k = 0; k < kThreads / 32; ++k) {
+        uint32_t c = ws[k];
+        ws[k] = run;
+        run += c;
+      }
+      s_base = run ? atomicAdd(count, (unsigned long long)run) : 0ull;
+    }
+    __syncthreads();
+    uint64_t pos = s_base + ws[w] + (incl - mine);
+#pragma unroll
+    for (int i = 0; i < kRelItems; ++i)
+      if (keepmask & (1u << i)) keys_out[pos++] = key[i];
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------ label composition
+
+__global__ void __launch_bounds__(kThreads) k_propagate(const uint32_t* root,
+                                                        const uint32_t* __restrict__ scan,
+                                                        const uint32_t* __restrict__ mo,
+                                                        const uint32_t* __restrict__ labels_up,
+                                                        uint32_t* labels_out, uint32_t n) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+    uint32_t r = root[v];
+    uint32_t s0 = scan[r], s1 = scan[r + 1];
+    labels_out[v] = s1 > s0 ? labels_up[s0] : mo[r];
+  }
+}
+
+__global__ void k_identity(uint32_t* labels, uint32_t n) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride)
+    labels[v] = (uint32_t)v;
+}
+
+}  // namespace
+
+void init_keys(unsigned long long* minkey, uint32_t* mo, uint32_t n, uint64_t rk,
+               const Launch& L) {
+  if (n == 0) return;
+  k_init_keys<<<grid_for(n, kThreads, L), kThreads, 0, L.stream>>>(minkey, mo, n, rk);
+}
+
+void edge_min(const uint32_t* src, const uint32_t* dst, const uint64_t* packed, uint64_t m,
+              uint32_t n, uint64_t rk, unsigned long long* minkey, unsigned* err,
+              const Launch& L) {
+  if (m == 0) return;
+  if (packed != nullptr) {
+    k_edge_min_packed<<<grid_for((m + 1) / 2, kThreads, L), kThreads, 0, L.stream>>>(packed, m, rk,
+                                                                                    minkey);
+  } else {
+    int vec = ((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst)) & 15) == 0;
+    k_edge_min_soa<<<grid_for((m + 3) / 4, kThreads, L), kThreads, 0, L.stream>>>(
+        src, dst, m, n, rk, minkey, err, vec);
+  }
+}
+
+void jump(unsigned long long* minkey, uint32_t* root, uint32_t* mo, uint32_t n, const Launch& L) {
+  if (n == 0) return;
+  k_jump<<<grid_for(n, kThreads, L), kThreads, 0, L.stream>>>(minkey, root, mo, n);
+}
+
+void relabel(const uint32_t* src, const uint32_t* dst, const uint64_t* packed, uint64_t m,
+             uint32_t n, const uint32_t* root, int bits, uint64_t* keys_out,
+             unsigned long long* count, const Launch& L) {
+  if (m == 0) return;
+  int grid = grid_for(m, kThreads * kRelItems, L, 4);
+  if (packed != nullptr)
+    k_relabel<true><<<grid, kThreads, 0, L.stream>>>(nullptr, nullptr, packed, m, n, root, bits,
+                                                     keys_out, count, 0);
+  else
+    k_relabel<false><<<grid, kThreads, 0, L.stream>>>(src, dst, nullptr, m, n, root, bits,
+                                                      keys_out, count, 0);
+}
+
+void propagate(const uint32_t* root, const uint32_t* scan, const uint32_t* mo,
+               const uint32_t* labels_up, uint32_t* labels_out, uint32_t n, const Launch& L) {
+  if (n == 0) return;
+  k_propagate<<<grid_for(n, kThreads, L), kThreads, 0, L.stream>>>(root, scan, mo, labels_up,
+                                                                   labels_out, n);
+}
+
+void identity_labels(uint32_t* labels, uint32_t n, const Launch& L) {
+  if (n == 0) return;
+  k_identity<<<grid_for(n, kThreads, L), kThreads, 0, L.stream>>>(labels, n);
+}
+
+void rank_probe(uint64_t rk, uint32_t v0, uint32_t count, uint32_t* out, const Launch& L) {
+  if (count == 0) return;
+  k_rank_probe<<<grid_for(count, kThreads, L), kThreads, 0, L.stream>>>(rk, v0, count, out);
+}
+
+}  // namespace lc

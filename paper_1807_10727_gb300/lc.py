@@ -1,0 +1,220 @@
+"""Thin ctypes binding of ``liblc.so`` (C ABI in ``include/lc.h``).
+
+Argument marshalling only: every step of the connected-components path runs in
+the library's CUDA kernels.  Functions carry the C names (``lc_create``,
+``lc_run``, ...); :class:`LocalContraction` and :func:`connected_components`
+wrap them for torch tensors.  PyTorch supplies device memory and streams.
+
+There is no fallback: if the library has not been built, or CUDA is not
+available, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import _build
+
+LC_OK, LC_ERR_INVALID, LC_ERR_OOM, LC_ERR_CUDA, LC_ERR_NO_CONVERGENCE, LC_ERR_TIMEOUT = range(6)
+LC_VARIANT_FOREST, LC_VARIANT_TWO_HOP, LC_VARIANT_TREE = 0, 1, 2
+
+# every symbol include/lc.h declares (checked by the CPU test suite)
+EXPORTED = ("lc_create", "lc_configure", "lc_run", "lc_run_host", "lc_last_stats", "lc_destroy",
+            "lc_status_str", "lc_rank_probe")
+
+_lib = None
+
+
+class LCError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__("%s failed: %s (status %d)" % (what, lc_status_str(code), code))
+        self.code = code
+
+
+def load(path: str | None = None):
+    """Load liblc.so (built by ``__graft_entry__.build()``); raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or _build.LC_SO
+    if not os.path.exists(path):
+        raise RuntimeError("liblc.so not built (%s); run __graft_entry__.build()" % path)
+    lib = ctypes.CDLL(path)
+    u32, u64, i32, p = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int, ctypes.c_void_p
+    pu32, pu64 = ctypes.POINTER(u32), ctypes.POINTER(u64)
+    lib.lc_create.argtypes = [u32, p, p, u64, u64, p, ctypes.POINTER(p)]
+    lib.lc_configure.argtypes = [p, i32, u64]
+    lib.lc_run.argtypes = [p, p, pu32, pu64, pu64, u32]
+    lib.lc_run_host.argtypes = [p, p, p, p, pu32, pu64, pu64, u32]
+    lib.lc_last_stats.argtypes = [p, pu32, pu64, u32]
+    lib.lc_destroy.argtypes = [p]
+    lib.lc_status_str.argtypes = [i32]
+    lib.lc_status_str.restype = ctypes.c_char_p
+    lib.lc_rank_probe.argtypes = [u64, u32, u32, u32, p, p]
+    for name in EXPORTED:
+        if name != "lc_status_str":
+            getattr(lib, name).restype = i32
+    _lib = lib
+    return lib
+
+
+def lc_status_str(code: int) -> str:
+    return load().lc_status_str(code).decode()
+
+
+def _check(code: int, what: str) -> None:
+    if code != LC_OK:
+        raise LCError(code, what)
+
+
+def _stream_handle(stream) -> int:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+def _dev_ptr(t, n: int, what: str) -> int:
+    if t is None:
+        return 0
+    if not t.is_cuda:
+        raise ValueError("%s must be a CUDA tensor" % what)
+    if t.element_size() != 4 or not t.is_contiguous() or t.numel() < n:
+        raise ValueError("%s must be a contiguous 32-bit tensor with >= %d elements" % (what, n))
+    return t.data_ptr()
+
+
+# ------------------------------------------------------------ C names
+
+def lc_create(n: int, d_src: int, d_dst: int, m: int, seed: int, stream: int) -> int:
+    out = ctypes.c_void_p()
+    _check(load().lc_create(n, d_src, d_dst, m, seed, stream, ctypes.byref(out)), "lc_create")
+    return out.value
+
+
+def lc_configure(ctx: int, variant: int, finish_edges: int = 0) -> None:
+    _check(load().lc_configure(ctx, variant, finish_edges), "lc_configure")
+
+
+def lc_run(ctx: int, d_labels: int, cap: int = 1024):
+    R = ctypes.c_uint32(0)
+    n_i = (ctypes.c_uint64 * cap)()
+    m_i = (ctypes.c_uint64 * cap)()
+    _check(load().lc_run(ctx, d_labels, ctypes.byref(R), n_i, m_i, cap), "lc_run")
+    r = R.value
+    return r, list(n_i[:r]), list(m_i[:r])
+
+
+def lc_run_host(ctx: int, h_src: np.ndarray, h_dst: np.ndarray, h_labels: np.ndarray,
+                cap: int = 1024):
+    R = ctypes.c_uint32(0)
+    n_i = (ctypes.c_uint64 * cap)()
+    m_i = (ctypes.c_uint64 * cap)()
+    _check(load().lc_run_host(ctx, h_src.ctypes.data, h_dst.ctypes.data, h_labels.ctypes.data,
+                              ctypes.byref(R), n_i, m_i, cap), "lc_run_host")
+    r = R.value
+    return r, list(n_i[:r]), list(m_i[:r])
+
+
+def lc_last_stats(ctx: int, cap: int = 1024) -> list[int]:
+    R = ctypes.c_uint32(0)
+    mp = (ctypes.c_uint64 * cap)()
+    _check(load().lc_last_stats(ctx, ctypes.byref(R), mp, cap), "lc_last_stats")
+    return list(mp[:min(R.value, cap)])
+
+
+def lc_destroy(ctx: int) -> None:
+    if ctx:
+        _check(load().lc_destroy(ctx), "lc_destroy")
+
+
+def lc_rank_probe(seed: int, i: int, v0: int, count: int, d_out: int, stream: int) -> None:
+    _check(load().lc_rank_probe(seed, i, v0, count, d_out, stream), "lc_rank_probe")
+
+
+# ------------------------------------------------------------ wrappers
+
+@dataclass
+class Result:
+    rounds: int
+    n_i: list
+    m_i: list
+
+
+class LocalContraction:
+    """One graph resident on the device.
+
+    ``src``/``dst`` are CUDA int32/uint32 tensors of length m (kept alive by this
+    object; never written).  With ``src is None`` the context owns its input
+    buffers and :meth:`run_host` takes host arrays.
+    """
+
+    def __init__(self, n: int, src=None, dst=None, m: int | None = None, seed: int = 0,
+                 stream=None, variant: int = LC_VARIANT_FOREST, finish_edges: int = 0):
+        if src is None:
+            if m is None:
+                raise ValueError("m is required when the context owns its inputs")
+            self.m = int(m)
+        else:
+            self.m = int(src.numel())
+            if dst is None or dst.numel() != self.m:
+                raise ValueError("src and dst must have the same length")
+        self.n = int(n)
+        self._src, self._dst = src, dst  # keep the caller's buffers alive
+        self.stream = stream
+        self.ctx = lc_create(self.n, _dev_ptr(src, self.m, "src"), _dev_ptr(dst, self.m, "dst"),
+                             self.m, seed, _stream_handle(stream))
+        if variant != LC_VARIANT_FOREST or finish_edges:
+            lc_configure(self.ctx, variant, finish_edges)
+
+    def run(self, labels=None, cap: int = 1024):
+        import torch
+        if labels is None:
+            dev = self._src.device if self._src is not None else torch.device("cuda")
+            labels = torch.empty(self.n, dtype=torch.int32, device=dev)
+        r, n_i, m_i = lc_run(self.ctx, _dev_ptr(labels, self.n, "labels"), cap)
+        return labels, Result(r, n_i, m_i)
+
+    def run_host(self, h_src: np.ndarray, h_dst: np.ndarray, h_labels: np.ndarray | None = None,
+                 cap: int = 1024):
+        for a in (h_src, h_dst):
+            if a.dtype != np.uint32 or not a.flags.c_contiguous or a.size != self.m:
+                raise ValueError("host edges must be contiguous uint32 arrays of length m")
+        if h_labels is None:
+            h_labels = np.empty(self.n, dtype=np.uint32)
+        r, n_i, m_i = lc_run_host(self.ctx, h_src, h_dst, h_labels, cap)
+        return h_labels, Result(r, n_i, m_i)
+
+    def mprime(self) -> list[int]:
+        return lc_last_stats(self.ctx)
+
+    def close(self) -> None:
+        if getattr(self, "ctx", None):
+            lc_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def connected_components(n: int, src, dst, seed: int = 0, stream=None):
+    """Labels (smallest vertex id per component) of the graph (src[j], dst[j]),
+    plus the phase count and per-phase sizes.  src/dst: CUDA 32-bit tensors."""
+    ctx = LocalContraction(n, src, dst, seed=seed, stream=stream)
+    try:
+        return ctx.run()
+    finally:
+        ctx.close()
+
+
+def rank_probe(seed: int, i: int, v0: int, count: int, stream=None):
+    import torch
+    out = torch.empty(count, dtype=torch.int32, device="cuda")
+    lc_rank_probe(seed, i, v0, count, out.data_ptr() if count else 0, _stream_handle(stream))
+    return out

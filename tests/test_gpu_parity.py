@@ -1,0 +1,169 @@
+"""GPU path (through the C ABI of liblc.so) against the CPU oracle: labels,
+phase count and every per-phase (n_i, m_i) bit-exact, plus the diagnostic m'_i.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1807_10727_gb300 import lc, synth
+
+pytestmark = pytest.mark.gpu
+
+
+def dev(a, cuda):
+    import torch
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.uint32))
+    return torch.from_numpy(a.view(np.int32)).to(cuda)
+
+
+def gpu_run(n, s, d, seed, cuda, **kw):
+    ts, td = dev(s, cuda), dev(d, cuda)
+    ctx = lc.LocalContraction(n, ts, td, seed=seed, **kw)
+    try:
+        labels, res = ctx.run()
+        mp = ctx.mprime()
+    finally:
+        ctx.close()
+    return labels.cpu().numpy().view(np.uint32), res, mp
+
+
+def assert_parity(n, s, d, seed, cuda, **kw):
+    labels, res, mp = gpu_run(n, s, d, seed, cuda)
+    ref = oracle.lc_run(n, s, d, seed)
+    assert res.rounds == ref.rounds
+    assert [(a, b) for a, b in zip(res.n_i, res.m_i)] == ref.sizes()
+    assert mp == [int(x) for x in ref.mp_i]
+    assert np.array_equal(labels, ref.labels)
+    return res
+
+
+def test_rank_probe_matches_oracle(lc_lib, cuda):
+    for seed, i, v0, count in [(1, 0, 0, 1 << 20), (7, 3, 2**32 - 5000, 4999), (2**63 + 5, 40, 12345, 77)]:
+        got = lc.rank_probe(seed, i, v0, count).cpu().numpy().view(np.uint32)
+        assert np.array_equal(got, oracle.ranks(seed, i, v0, count))
+
+
+@pytest.mark.parametrize("name", ["er16", "rmat14", "rmat18", "gridmix_small"])
+def test_workload_parity(lc_lib, cuda, name):
+    g = synth.workload(name)
+    assert_parity(g.n, g.src, g.dst, g.seed, cuda)
+
+
+def test_er16_several_seeds(lc_lib, cuda):
+    g = synth.workload("er16")
+    for seed in (0, 2, 3, 2**40 + 1):
+        assert_parity(g.n, g.src, g.dst, seed, cuda)
+
+
+def test_many_small_random_graphs(lc_lib, cuda):
+    rng = np.random.default_rng(17)
+    for t in range(120):
+        n = int(rng.integers(1, 70))
+        m = int(rng.integers(0, 3 * n))
+        s = rng.integers(0, n, m)
+        d = rng.integers(0, n, m)
+        assert_parity(n, s, d, t, cuda)
+
+
+def test_ragged_sizes_across_tiles(lc_lib, cuda):
+    """Sizes around the 4096-key tile and the 16-element vector widths."""
+    rng = np.random.default_rng(23)
+    for n, m in [(4097, 4095), (4096, 4097), (5000, 8191), (70001, 123457), (3, 100003)]:
+        s = rng.integers(0, n, m)
+        d = rng.integers(0, n, m)
+        assert_parity(n, s, d, 9, cuda)
+
+
+# ---------------------------------------------------------- edge cases
+
+def test_no_edges(lc_lib, cuda):
+    labels, res, _ = gpu_run(10, [], [], 1, cuda)
+    assert res.rounds == 0 and list(labels) == list(range(10))
+
+
+def test_single_vertex_with_loop(lc_lib, cuda):
+    res = assert_parity(1, [0], [0], 1, cuda)
+    assert res.rounds == 1
+
+
+def test_loops_and_duplicates_only(lc_lib, cuda):
+    assert_parity(6, [2, 2, 5, 5], [2, 2, 5, 5], 3, cuda)
+    assert_parity(6, [1] * 1000 + [4], [3] * 1000 + [4], 3, cuda)
+
+
+def test_star_hub(lc_lib, cuda):
+    k = 20000
+    s = np.zeros(k, dtype=np.uint32)
+    d = np.arange(1, k + 1, dtype=np.uint32)
+    for seed in (1, 2):
+        assert_parity(k + 1, s, d, seed, cuda)
+        assert_parity(k + 1, d, s, seed, cuda)
+
+
+def test_long_path_many_phases(lc_lib, cuda):
+    n = 100000
+    s = np.arange(n - 1, dtype=np.uint32)
+    perm = np.random.default_rng(1).permutation(n).astype(np.uint32)
+    res = assert_parity(n, perm[s], perm[s + 1], 5, cuda)
+    assert res.rounds > 5
+
+
+def test_complete_graph(lc_lib, cuda):
+    n = 300
+    iu = np.triu_indices(n, 1)
+    res = assert_parity(n, iu[0], iu[1], 4, cuda)
+    assert res.rounds == 1
+
+
+def test_unaligned_input_pointers(lc_lib, cuda):
+    """Caller buffers that are offset views (not 16-byte aligned)."""
+    g = synth.workload("rmat14")
+    ts, td = dev(np.concatenate([[0], g.src]), cuda), dev(np.concatenate([[0, 0], g.dst]), cuda)
+    ctx = lc.LocalContraction(g.n, ts[1:], td[2:], seed=g.seed)
+    labels, res = ctx.run()
+    ctx.close()
+    ref = oracle.lc_run(g.n, g.src, g.dst, g.seed)
+    assert res.rounds == ref.rounds
+    assert np.array_equal(labels.cpu().numpy().view(np.uint32), ref.labels)
+
+
+def test_vertex_id_out_of_range_is_rejected(lc_lib, cuda):
+    ts, td = dev([0, 1, 7], cuda), dev([1, 2, 3], cuda)
+    ctx = lc.LocalContraction(5, ts, td, seed=1)
+    with pytest.raises(lc.LCError) as ei:
+        ctx.run()
+    assert ei.value.code == lc.LC_ERR_INVALID
+    ctx.close()
+
+
+def test_context_reuse_is_repeatable(lc_lib, cuda):
+    g = synth.workload("rmat16")
+    ts, td = dev(g.src, cuda), dev(g.dst, cuda)
+    ctx = lc.LocalContraction(g.n, ts, td, seed=g.seed)
+    a, ra = ctx.run()
+    b, rb = ctx.run()
+    ctx.close()
+    assert (a == b).all().item() and ra == rb
+
+
+def test_run_host_matches_oracle(lc_lib, cuda):
+    g = synth.workload("gridmix_small")
+    ctx = lc.LocalContraction(g.n, m=g.m, seed=g.seed)
+    labels, res = ctx.run_host(g.src, g.dst)
+    labels2, res2 = ctx.run_host(g.src, g.dst)
+    ctx.close()
+    ref = oracle.lc_run(g.n, g.src, g.dst, g.seed)
+    assert res.rounds == ref.rounds and [(a, b) for a, b in zip(res.n_i, res.m_i)] == ref.sizes()
+    assert np.array_equal(labels, ref.labels) and np.array_equal(labels2, ref.labels)
+
+
+def test_output_cap_too_small(lc_lib, cuda):
+    g = synth.workload("rmat14")
+    ts, td = dev(g.src, cuda), dev(g.dst, cuda)
+    ctx = lc.LocalContraction(g.n, ts, td, seed=g.seed)
+    import torch
+    labels = torch.empty(g.n, dtype=torch.int32, device=cuda)
+    with pytest.raises(lc.LCError) as ei:
+        lc.lc_run(ctx.ctx, labels.data_ptr(), cap=1)
+    assert ei.value.code == lc.LC_ERR_INVALID
+    ctx.close()
