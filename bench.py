@@ -1,0 +1,352 @@
+"""Benchmark: input edges/s of the LocalContraction connected-components path
+on one GB300 (R-MAT scale 26, 2^30 edges, permuted ids, rank seed 7).
+
+One step = one lc_run over the whole phase loop (rank, closed-neighbourhood
+minimum, pointer jumping, relabel/sort/dedup/compact every phase, then label
+composition) with the input already resident in HBM.  The input (8 GiB) is
+far larger than the 129 MB L2, so no flush is needed between steps.
+
+Extra keys on the JSON line:
+  roofline      dominant kernel: algorithmic bytes / its CUDA-event-timed
+                device time, against the measured HBM copy peak.
+  path_roofline whole step: algorithmic bytes of all phases / step time.
+  e2e           the same metric through lc_run_host (pinned host buffers,
+                host->device copy of the edges and device->host copy of the
+                labels inside the timed region).
+  cpu_baseline  the CPU oracle (single thread) on a bounded prefix sample.
+
+--impl reference times the CPU oracle on the same bounded sample per step
+(the "reference" of this build is the oracle written from the paper).
+Multi-GPU (--gpus N under torchrun): the single-graph path does not shard, so
+every rank runs its own replica (weak scaling); value = all ranks' edges /
+the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+REPO = os.path.dirname(os.path.abspath(__file__))
+if REPO not in sys.path:
+    sys.path.insert(0, REPO)
+
+METRIC = "input edges/sec to final labels (1 GB300), HBM roofline %"
+UNIT = "edges/s"
+CPU_SAMPLE_EDGES = 1 << 24
+
+
+def peaks():
+    path = os.path.join(REPO, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# Algorithmic bytes of one launch of each kernel, from the phase sizes
+# (n_i vertices, m_i edges, mp_i keys after relabel, m_{i+1} unique edges).
+# Random-gather sector amplification and the repeated sort passes beyond one
+# read+write of the keys are not algorithmic and are not counted.
+def algorithmic_bytes(n_i, m_i, mp_i, passes_i):
+    per = {}
+
+    def add(k, b):
+        per[k] = per.get(k, 0) + b
+
+    R = len(n_i)
+    for i in range(R):
+        n, m, mp = n_i[i], m_i[i], mp_i[i]
+        m_next = m_i[i + 1] if i + 1 < R else 0
+        edge_bytes = 8 * m
+        add("init_keys", 8 * n + (4 * n if i == 0 else 0))
+        add("edge_min_soa" if i == 0 else "edge_min_packed", edge_bytes + 8 * n)
+        add("jump", 8 * n + 4 * n + 4 * n)
+        add("relabel_soa" if i == 0 else "relabel_packed", edge_bytes + 4 * n + 8 * mp)
+        if mp:
+            add("sort_hist", 8 * mp)
+            add("sort_pass", 16 * mp * passes_i[i])
+            add("unique_rename", 8 * mp + 8 * m_next)
+        add("scan_flags", n + 4 * n + 4 * n)
+        add("propagate", 4 * n + 4 * n)
+    return per
+
+
+def path_bytes(n_i, m_i, mp_i):
+    """Whole-path algorithmic bytes: edges read by the minimum and relabel
+    steps, keys written, one read+write of the keys for deduplication, the
+    renamed edges written, and the per-vertex arrays of every phase."""
+    total = 0
+    R = len(n_i)
+    for i in range(R):
+        n, m, mp = n_i[i], m_i[i], mp_i[i]
+        m_next = m_i[i + 1] if i + 1 < R else 0
+        total += 8 * m + 8 * m + 8 * mp + 16 * mp + 8 * m_next
+        total += n * (8 + 4 + 8 + 4 + 4)
+    total += sum(8 * n for n in n_i) + 8 * (n_i[0] if n_i else 0)
+    return total
+
+
+def sort_passes(n):
+    bits = 1
+    while bits < 32 and (1 << bits) < n:
+        bits += 1
+    return (2 * bits + 7) // 8
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples every 200 ms during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.path = os.path.join("/tmp", "lc_clocks_%d.csv" % os.getpid())
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", self.gpu_id, "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def gpu_id_for(device_index: int) -> str:
+    import torch
+    try:
+        p = torch.cuda.get_device_properties(device_index)
+        return "%08x:%02x:%02x.0" % (p.pci_domain_id, p.pci_bus_id, p.pci_device_id)
+    except Exception:
+        return str(device_index)
+
+
+def cpu_baseline(g, sample_edges=CPU_SAMPLE_EDGES):
+    """The oracle (single-threaded C++) on the first `sample_edges` edges of
+    the same edge list, over all n vertices."""
+    import oracle
+    k = min(sample_edges, g.m)
+    s, d = np.ascontiguousarray(g.src[:k]), np.ascontiguousarray(g.dst[:k])
+    t0 = time.perf_counter()
+    oracle.lc_run(g.n, s, d, g.seed)
+    dt = time.perf_counter() - t0
+    return {"value": k / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "first %d of %d edges of the same graph (all %d vertices), one oracle run, %.1f s"
+                      % (k, g.m, g.n, dt)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_reference(args):
+    """The oracle, as it stands, timed on the host cores on a bounded sample."""
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return
+    from paper_1807_10727_gb300 import synth
+    import oracle
+    oracle.build()
+    g = synth.workload(args.workload)
+    k = min(CPU_SAMPLE_EDGES, g.m)
+    s, d = np.ascontiguousarray(g.src[:k]), np.ascontiguousarray(g.dst[:k])
+    for _ in range(args.warmup):
+        oracle.lc_run(g.n, s, d, g.seed)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.lc_run(g.n, s, d, g.seed)
+    dt = (time.perf_counter() - t0) / max(1, args.steps)
+    value = k / dt
+    sample = "first %d of %d edges of %s (all %d vertices) per step" % (k, g.m, args.workload, g.n)
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32/u64",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "n": g.n, "m": g.m, "sample_edges": k},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="rmat26")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-profile", action="store_true",
+                    help="skip the per-kernel event timing (roofline) of the timed steps")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    import torch.distributed as dist
+
+    from paper_1807_10727_gb300 import lc, synth
+
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    lc.load()
+    g = synth.workload(args.workload)
+    src = torch.from_numpy(g.src.view(np.int32)).to(dev)
+    dst = torch.from_numpy(g.dst.view(np.int32)).to(dev)
+    labels = torch.empty(g.n, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    ctx = lc.LocalContraction(g.n, src, dst, seed=g.seed, stream=stream)
+
+    for _ in range(max(3, args.warmup)):
+        _, res = ctx.run(labels)
+    mp = ctx.mprime()
+
+    clocks = ClockSampler(gpu_id_for(local))
+    ctx.profile(not args.no_profile)
+    barrier()
+    torch.cuda.synchronize(dev)
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        ctx.run(labels)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    kstats = ctx.kernel_stats()
+    ctx.profile(False)
+    launches = sum(v[0] for v in kstats.values())
+
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+
+    # dominant kernel and its roofline
+    peak, peak_kind = peaks()
+    passes = [sort_passes(n) for n in res.n_i]
+    alg = algorithmic_bytes(res.n_i, res.m_i, mp, passes)
+    top = max(kstats.items(), key=lambda kv: kv[1][1])
+    top_name, (top_launches, top_ms) = top
+    roof = None
+    if top_ms > 0:
+        achieved = alg.get(top_name, 0) * args.steps / (top_ms / 1e3) / 1e9
+        roof = {"bound": "hbm", "kernel": top_name, "achieved": achieved, "peak": peak,
+                "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind,
+                "traffic": None, "launches_per_step": top_launches / args.steps,
+                "share_of_step": top_ms / args.steps / ms}
+    pb = path_bytes(res.n_i, res.m_i, mp)
+    path_roof = {"bytes_per_step": pb, "achieved": pb / (ms / 1e3) / 1e9, "peak": peak,
+                 "unit": "GB/s", "frac": pb / (ms / 1e3) / 1e9 / peak}
+    kernels = {k: {"launches_per_step": v[0] / args.steps, "ms_per_step": v[1] / args.steps}
+               for k, v in kstats.items() if v[0]}
+
+    # end to end through the public host-buffer entry point
+    e2e = None
+    if not args.no_e2e:
+        del src, dst
+        ctx.close()
+        torch.cuda.empty_cache()
+        h_src = torch.from_numpy(g.src.view(np.int32)).pin_memory().numpy().view(np.uint32)
+        h_dst = torch.from_numpy(g.dst.view(np.int32)).pin_memory().numpy().view(np.uint32)
+        h_lab = torch.empty(g.n, dtype=torch.int32).pin_memory().numpy().view(np.uint32)
+        hctx = lc.LocalContraction(g.n, m=g.m, seed=g.seed, stream=stream)
+        hctx.run_host(h_src, h_dst, h_lab)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            hctx.run_host(h_src, h_dst, h_lab)
+        e2e_s = (time.perf_counter() - t0) / args.steps
+        hctx.close()
+        te = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(te, op=dist.ReduceOp.MAX)
+        e2e = {"value": world * g.m / float(te.item()), "unit": UNIT,
+               "h2d_bytes_per_step": 8 * g.m, "d2h_bytes_per_step": 4 * g.n,
+               "ms_per_step": float(te.item()) * 1e3}
+    else:
+        ctx.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(g)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": world * g.m / (ms_max / 1e3), "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": max(3, args.warmup),
+            "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32/u64", "data": "synthetic",
+            "config": {"workload": args.workload, "n": g.n, "m": g.m, "rank_seed": g.seed,
+                       "rounds": res.rounds, "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "inputs (8 B/edge) larger than L2; no flush"},
+            "roofline": roof, "path_roofline": path_roof,
+            "e2e": e2e, "cpu_baseline": cpu, "gpu_launches": launches,
+            "clocks": clk, "kernels": kernels,
+            "sizes": [[int(a), int(b), int(c)] for a, b, c in zip(res.n_i, res.m_i, mp)],
+        }
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -107,6 +107,20 @@ lc_status lc_run_host(lc_ctx* ctx, const uint32_t* h_src, const uint32_t* h_dst,
  * deduplication.  Returns the phase count in *rounds. */
 lc_status lc_last_stats(const lc_ctx* ctx, uint32_t* rounds, uint64_t* mp_i, uint32_t cap);
 
+/* Per-kernel instrumentation (no counterpart in the paper; used to measure
+ * the kernels against the HBM roofline).  Launch counts of every kernel are
+ * always kept.  lc_profile(ctx, 1) additionally records a CUDA event pair
+ * around every kernel launch on the context's stream and accumulates each
+ * kernel's device time; lc_profile(ctx, 0) stops that.  Either call first
+ * synchronises the stream and resets all counts and times to zero. */
+lc_status lc_profile(lc_ctx* ctx, int on);
+
+/* Counters of kernel k (k = 0, 1, ... until LC_ERR_INVALID): its name
+ * (static string), launches and accumulated device milliseconds since the
+ * last lc_profile call.  Any output pointer may be NULL. */
+lc_status lc_kernel_stats(const lc_ctx* ctx, uint32_t k, const char** name, uint64_t* launches,
+                          double* ms);
+
 /* Release the context and all its device memory (stream-ordered frees after a
  * synchronisation of the context's stream).  NULL is accepted. */
 lc_status lc_destroy(lc_ctx* ctx);

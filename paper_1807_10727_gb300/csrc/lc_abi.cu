@@ -11,6 +11,53 @@
 
 using namespace lc;
 
+namespace lc {
+
+const char* kernel_name(int id) {
+  static const char* names[kNumKernels] = {
+      "init_keys",   "edge_min_soa", "edge_min_packed", "jump",          "relabel_soa",
+      "relabel_packed", "sort_hist", "hist_scan",       "sort_pass",     "scan_flags",
+      "unique_rename", "propagate",  "identity",        "rank_probe"};
+  return (id >= 0 && id < kNumKernels) ? names[id] : "unknown";
+}
+
+cudaEvent_t Prof::get() {
+  if (!pool.empty()) {
+    cudaEvent_t e = pool.back();
+    pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+void Prof::resolve() {
+  for (auto& t : pending) {
+    float ms_ = 0.f;
+    if (cudaEventElapsedTime(&ms_, std::get<1>(t), std::get<2>(t)) == cudaSuccess)
+      ms[std::get<0>(t)] += ms_;
+    pool.push_back(std::get<1>(t));
+    pool.push_back(std::get<2>(t));
+  }
+  pending.clear();
+}
+
+void Prof::reset() {
+  for (int k = 0; k < kNumKernels; ++k) {
+    launches[k] = 0;
+    ms[k] = 0.0;
+  }
+}
+
+void Prof::release() {
+  resolve();
+  for (auto e : pool) cudaEventDestroy(e);
+  pool.clear();
+}
+
+}  // namespace lc
+
 namespace {
 
 // Level storage of one phase: the root map, the min-original-id of each
@@ -93,6 +140,7 @@ struct lc_ctx {
   cudaStream_t stream = nullptr;
   int device = 0;
   Launch L{};
+  Prof prof;
   lc_variant variant = LC_VARIANT_FOREST;
   uint64_t finish_edges = 0;
 
@@ -142,6 +190,7 @@ static void free_ctx(lc_ctx* c) {
   cudaFree(c->sort.hist);
   cudaFree(c->sort.tickets);
   c->arena.release();
+  c->prof.release();
   delete c;
 }
 
@@ -187,6 +236,7 @@ extern "C" lc_status lc_create(uint32_t n, const uint32_t* d_src, const uint32_t
     return LC_ERR_CUDA;
   }
   c->L.stream = c->stream;
+  c->L.prof = &c->prof;
   c->src = d_src;
   c->dst = d_dst;
   lc_status st = alloc_ctx(c);
@@ -229,6 +279,7 @@ static lc_status run_loop(lc_ctx* c, uint32_t* d_labels, uint32_t* rounds, uint6
     identity_labels(d_labels, c->n, L);
     LC_TRY(cudaGetLastError());
     LC_TRY(cudaStreamSynchronize(c->stream));
+    c->prof.resolve();
     return LC_OK;
   }
   c->arena.reset();
@@ -276,6 +327,7 @@ static lc_status run_loop(lc_ctx* c, uint32_t* d_labels, uint32_t* rounds, uint6
     LC_TRY(cudaGetLastError());
     LC_TRY(cudaMemcpyAsync(c->h_ctr, c->ctr, sizeof(Counters), cudaMemcpyDeviceToHost, c->stream));
     LC_TRY(cudaStreamSynchronize(c->stream));
+    c->prof.resolve();
     if (c->h_ctr->err & kErrBadVertex) return LC_ERR_INVALID;
     if (c->h_ctr->err & kErrTimeout) return LC_ERR_TIMEOUT;
     hn.push_back(ni);
@@ -298,6 +350,7 @@ static lc_status run_loop(lc_ctx* c, uint32_t* d_labels, uint32_t* rounds, uint6
   }
   LC_TRY(cudaGetLastError());
   LC_TRY(cudaStreamSynchronize(c->stream));
+  c->prof.resolve();
   c->last_rounds = R;
   if (rounds) *rounds = R;
   if (n_i || m_i) {
@@ -345,6 +398,25 @@ extern "C" lc_status lc_last_stats(const lc_ctx* c, uint32_t* rounds, uint64_t* 
   if (mp_i)
     for (uint32_t i = 0; i < std::min<uint32_t>(cap, (uint32_t)c->last_mp.size()); ++i)
       mp_i[i] = c->last_mp[i];
+  return LC_OK;
+}
+
+extern "C" lc_status lc_profile(lc_ctx* c, int on) {
+  if (!c) return LC_ERR_INVALID;
+  DeviceGuard g(c->device);
+  LC_TRY(cudaStreamSynchronize(c->stream));
+  c->prof.resolve();
+  c->prof.reset();
+  c->prof.on = on != 0;
+  return LC_OK;
+}
+
+extern "C" lc_status lc_kernel_stats(const lc_ctx* c, uint32_t k, const char** name,
+                                     uint64_t* launches, double* ms) {
+  if (!c || k >= (uint32_t)kNumKernels) return LC_ERR_INVALID;
+  if (name) *name = kernel_name((int)k);
+  if (launches) *launches = c->prof.launches[k];
+  if (ms) *ms = c->prof.ms[k];
   return LC_OK;
 }
 

@@ -1,15 +1,77 @@
 // Host-side launchers of the LocalContraction kernels (internal to liblc.so).
 #pragma once
 #include <cstdint>
+#include <tuple>
+#include <vector>
 #include <cuda_runtime.h>
 
 #include "lc_common.cuh"
 
 namespace lc {
 
+// Every kernel of the library, for launch counting and per-kernel timing.
+enum KernelId : int {
+  kKInitKeys,
+  kKEdgeMinSoa,
+  kKEdgeMinPacked,
+  kKJump,
+  kKRelabelSoa,
+  kKRelabelPacked,
+  kKSortHist,
+  kKHistScan,
+  kKSortPass,
+  kKScanFlags,
+  kKUniqueRename,
+  kKPropagate,
+  kKIdentity,
+  kKRankProbe,
+  kNumKernels
+};
+
+const char* kernel_name(int id);
+
+// Launch counts (always) and, when `on`, device time of every launch measured
+// with a CUDA event pair recorded around it on the launching stream.
+struct Prof {
+  bool on = false;
+  uint64_t launches[kNumKernels] = {};
+  double ms[kNumKernels] = {};
+  std::vector<std::tuple<int, cudaEvent_t, cudaEvent_t>> pending;
+  std::vector<cudaEvent_t> pool;
+  cudaEvent_t get();
+  void resolve();  // call after the stream has been synchronised
+  void reset();
+  void release();
+};
+
 struct Launch {
   cudaStream_t stream;
-  int sms;  // multiprocessor count of the device
+  int sms;             // multiprocessor count of the device
+  Prof* prof = nullptr;
+};
+
+// Scope around one kernel launch: counts it and, when timing is on, brackets
+// it with events.
+struct KScope {
+  const Launch& L;
+  int id;
+  cudaEvent_t e0 = nullptr;
+  KScope(const Launch& l, int k) : L(l), id(k) {
+    if (L.prof) {
+      ++L.prof->launches[k];
+      if (L.prof->on) {
+        e0 = L.prof->get();
+        cudaEventRecord(e0, L.stream);
+      }
+    }
+  }
+  ~KScope() {
+    if (e0) {
+      cudaEvent_t e1 = L.prof->get();
+      cudaEventRecord(e1, L.stream);
+      L.prof->pending.emplace_back(id, e0, e1);
+    }
+  }
 };
 
 // ---------------------------------------------------------- radix sort

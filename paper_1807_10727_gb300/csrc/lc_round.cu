@@ -254,6 +254,7 @@ __global__ void k_identity(uint32_t* labels, uint32_t n) {
 void init_keys(unsigned long long* minkey, uint32_t* mo, uint32_t n, uint64_t rk,
                const Launch& L) {
   if (n == 0) return;
+  KScope ks(L, kKInitKeys);
   k_init_keys<<<grid_for(n, kThreads, L), kThreads, 0, L.stream>>>(minkey, mo, n, rk);
 }
 
@@ -262,10 +263,12 @@ void edge_min(const uint32_t* src, const uint32_t* dst, const uint64_t* packed, 
               const Launch& L) {
   if (m == 0) return;
   if (packed != nullptr) {
+    KScope ks(L, kKEdgeMinPacked);
     k_edge_min_packed<<<grid_for((m + 1) / 2, kThreads, L), kThreads, 0, L.stream>>>(packed, m, rk,
                                                                                     minkey);
   } else {
     int vec = ((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst)) & 15) == 0;
+    KScope ks(L, kKEdgeMinSoa);
     k_edge_min_soa<<<grid_for((m + 3) / 4, kThreads, L), kThreads, 0, L.stream>>>(
         src, dst, m, n, rk, minkey, err, vec);
   }
@@ -273,6 +276,7 @@ void edge_min(const uint32_t* src, const uint32_t* dst, const uint64_t* packed, 
 
 void jump(unsigned long long* minkey, uint32_t* root, uint32_t* mo, uint32_t n, const Launch& L) {
   if (n == 0) return;
+  KScope ks(L, kKJump);
   k_jump<<<grid_for(n, kThreads, L), kThreads, 0, L.stream>>>(minkey, root, mo, n);
 }
 
@@ -281,28 +285,34 @@ void relabel(const uint32_t* src, const uint32_t* dst, const uint64_t* packed, u
              unsigned long long* count, const Launch& L) {
   if (m == 0) return;
   int grid = grid_for(m, kThreads * kRelItems, L, 4);
-  if (packed != nullptr)
+  if (packed != nullptr) {
+    KScope ks(L, kKRelabelPacked);
     k_relabel<true><<<grid, kThreads, 0, L.stream>>>(nullptr, nullptr, packed, m, n, root, bits,
                                                      keys_out, count, 0);
-  else
+  } else {
+    KScope ks(L, kKRelabelSoa);
     k_relabel<false><<<grid, kThreads, 0, L.stream>>>(src, dst, nullptr, m, n, root, bits,
                                                       keys_out, count, 0);
+  }
 }
 
 void propagate(const uint32_t* root, const uint32_t* scan, const uint32_t* mo,
                const uint32_t* labels_up, uint32_t* labels_out, uint32_t n, const Launch& L) {
   if (n == 0) return;
+  KScope ks(L, kKPropagate);
   k_propagate<<<grid_for(n, kThreads, L), kThreads, 0, L.stream>>>(root, scan, mo, labels_up,
                                                                    labels_out, n);
 }
 
 void identity_labels(uint32_t* labels, uint32_t n, const Launch& L) {
   if (n == 0) return;
+  KScope ks(L, kKIdentity);
   k_identity<<<grid_for(n, kThreads, L), kThreads, 0, L.stream>>>(labels, n);
 }
 
 void rank_probe(uint64_t rk, uint32_t v0, uint32_t count, uint32_t* out, const Launch& L) {
   if (count == 0) return;
+  KScope ks(L, kKRankProbe);
   k_rank_probe<<<grid_for(count, kThreads, L), kThreads, 0, L.stream>>>(rk, v0, count, out);
 }
 

@@ -384,13 +384,20 @@ int radix_sort_u64(uint64_t* keys, uint64_t* alt, const unsigned long long* d_co
   cudaMemsetAsync(s.tickets, 0, sizeof(unsigned) * 16, L.stream);
   uint64_t tiles = (max_count + kSortTile - 1) / kSortTile;
   int hgrid = (int)std::min<uint64_t>(tiles, (uint64_t)L.sms * 4);
-  k_sort_hist<<<hgrid, kSortThreads, 0, L.stream>>>(keys, d_count, passes, s.hist);
-  k_hist_scan<<<passes, kRadix, 0, L.stream>>>(s.hist);
+  {
+    KScope ks(L, kKSortHist);
+    k_sort_hist<<<hgrid, kSortThreads, 0, L.stream>>>(keys, d_count, passes, s.hist);
+  }
+  {
+    KScope ks(L, kKHistScan);
+    k_hist_scan<<<passes, kRadix, 0, L.stream>>>(s.hist);
+  }
   uint64_t* src = keys;
   uint64_t* dst = alt;
   for (int p = 0; p < passes; ++p) {
     uint32_t epoch = next_epoch(s, L);
     bool last = p == passes - 1;
+    KScope ks(L, kKSortPass);
     k_sort_pass<<<(unsigned)tiles, kSortThreads, 0, L.stream>>>(
         src, dst, d_count, kRadixBits * p, s.hist + p * kRadix, s.status, epoch, s.tickets + p,
         err, last ? mark_flags : nullptr, half_bits);
@@ -406,6 +413,7 @@ void scan_flags(const uint8_t* flags, uint32_t* out, uint32_t n, const uint32_t*
   uint32_t epoch = next_epoch(s, L);
   cudaMemsetAsync(s.tickets + 8, 0, sizeof(unsigned), L.stream);
   uint64_t tiles = ((uint64_t)n + kScanTile - 1) / kScanTile;
+  KScope ks(L, kKScanFlags);
   k_scan_flags<<<(unsigned)tiles, kSortThreads, 0, L.stream>>>(flags, out, n, mo_in, mo_out, total,
                                                               s.status, epoch, s.tickets + 8, err);
 }
@@ -417,6 +425,7 @@ void unique_rename(const uint64_t* keys, const unsigned long long* d_count, uint
   uint32_t epoch = next_epoch(s, L);
   cudaMemsetAsync(s.tickets + 9, 0, sizeof(unsigned), L.stream);
   uint64_t tiles = (max_count + kScanTile - 1) / kScanTile;
+  KScope ks(L, kKUniqueRename);
   k_unique_rename<<<(unsigned)tiles, kSortThreads, 0, L.stream>>>(
       keys, d_count, half_bits, newid, out, m_next, s.status, epoch, s.tickets + 9, err);
 }

@@ -22,8 +22,8 @@ LC_OK, LC_ERR_INVALID, LC_ERR_OOM, LC_ERR_CUDA, LC_ERR_NO_CONVERGENCE, LC_ERR_TI
 LC_VARIANT_FOREST, LC_VARIANT_TWO_HOP, LC_VARIANT_TREE = 0, 1, 2
 
 # every symbol include/lc.h declares (checked by the CPU test suite)
-EXPORTED = ("lc_create", "lc_configure", "lc_run", "lc_run_host", "lc_last_stats", "lc_destroy",
-            "lc_status_str", "lc_rank_probe")
+EXPORTED = ("lc_create", "lc_configure", "lc_run", "lc_run_host", "lc_last_stats", "lc_profile",
+            "lc_kernel_stats", "lc_destroy", "lc_status_str", "lc_rank_probe")
 
 _lib = None
 
@@ -50,6 +50,9 @@ def load(path: str | None = None):
     lib.lc_run.argtypes = [p, p, pu32, pu64, pu64, u32]
     lib.lc_run_host.argtypes = [p, p, p, p, pu32, pu64, pu64, u32]
     lib.lc_last_stats.argtypes = [p, pu32, pu64, u32]
+    lib.lc_profile.argtypes = [p, i32]
+    lib.lc_kernel_stats.argtypes = [p, u32, ctypes.POINTER(ctypes.c_char_p), pu64,
+                                    ctypes.POINTER(ctypes.c_double)]
     lib.lc_destroy.argtypes = [p]
     lib.lc_status_str.argtypes = [i32]
     lib.lc_status_str.restype = ctypes.c_char_p
@@ -126,6 +129,26 @@ def lc_last_stats(ctx: int, cap: int = 1024) -> list[int]:
     return list(mp[:min(R.value, cap)])
 
 
+def lc_profile(ctx: int, on: bool) -> None:
+    _check(load().lc_profile(ctx, 1 if on else 0), "lc_profile")
+
+
+def lc_kernel_stats(ctx: int) -> dict:
+    """{kernel name: (launches, device ms)} since the last lc_profile call."""
+    out = {}
+    k = 0
+    lib = load()
+    while True:
+        name = ctypes.c_char_p()
+        launches = ctypes.c_uint64()
+        ms = ctypes.c_double()
+        if lib.lc_kernel_stats(ctx, k, ctypes.byref(name), ctypes.byref(launches),
+                               ctypes.byref(ms)) != LC_OK:
+            return out
+        out[name.value.decode()] = (int(launches.value), float(ms.value))
+        k += 1
+
+
 def lc_destroy(ctx: int) -> None:
     if ctx:
         _check(load().lc_destroy(ctx), "lc_destroy")
@@ -190,6 +213,12 @@ class LocalContraction:
 
     def mprime(self) -> list[int]:
         return lc_last_stats(self.ctx)
+
+    def profile(self, on: bool) -> None:
+        lc_profile(self.ctx, on)
+
+    def kernel_stats(self) -> dict:
+        return lc_kernel_stats(self.ctx)
 
     def close(self) -> None:
         if getattr(self, "ctx", None):
