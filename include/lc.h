@@ -81,6 +81,20 @@ lc_status lc_create(uint32_t n, const uint32_t* d_src, const uint32_t* d_dst, ui
  * count and per-phase sizes, never the labels. */
 lc_status lc_configure(lc_ctx* ctx, lc_variant variant, uint64_t finish_edges);
 
+typedef enum {
+  LC_DEDUP_HASH = 0, /* hashed bucket partition + per-bucket hash set (default) */
+  LC_DEDUP_SORT = 1  /* full LSD radix sort of the edge keys, keep the first of each run */
+} lc_dedup;
+
+/* How each phase removes duplicate edges after relabelling (the "potential
+ * duplicates are removed in a standard way" step of the O(1)-round
+ * contraction lemma).  Both give the same edge set, hence the same labels,
+ * phase count and per-phase sizes; they differ in speed and in the order of
+ * the edges inside the context (sorted with LC_DEDUP_SORT, unspecified with
+ * LC_DEDUP_HASH).  LC_DEDUP_HASH falls back to the sort for a phase whose
+ * hash buckets overflow. */
+lc_status lc_set_dedup(lc_ctx* ctx, lc_dedup mode);
+
 /* Run the whole phase loop.
  *   d_labels  device uint32[n], caller-owned: labels[v] = smallest vertex id in
  *             v's connected component.

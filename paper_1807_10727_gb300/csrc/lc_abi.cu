@@ -17,7 +17,8 @@ const char* kernel_name(int id) {
   static const char* names[kNumKernels] = {
       "init_keys",   "edge_min_soa", "edge_min_packed", "jump",          "relabel_soa",
       "relabel_packed", "sort_hist", "hist_scan",       "sort_pass",     "scan_flags",
-      "unique_rename", "propagate",  "identity",        "rank_probe"};
+      "unique_rename", "propagate",  "bucket_bounds",   "bucket_dedup",  "rename",
+      "identity",      "rank_probe"};
   return (id >= 0 && id < kNumKernels) ? names[id] : "unknown";
 }
 
@@ -159,6 +160,10 @@ struct lc_ctx {
   Arena arena;
   std::vector<Level> levels;
 
+  uint32_t* bounds = nullptr;  // bucket boundaries of the hashed dedup
+  uint64_t fallbacks = 0;      // phases that needed the full-sort dedup
+  bool dedup_sort = false;     // deduplicate by a full radix sort every phase
+
   uint32_t last_rounds = 0;
   std::vector<uint64_t> last_mp;
 };
@@ -189,6 +194,7 @@ static void free_ctx(lc_ctx* c) {
   cudaFree(c->sort.status);
   cudaFree(c->sort.hist);
   cudaFree(c->sort.tickets);
+  cudaFree(c->bounds);
   c->arena.release();
   c->prof.release();
   delete c;
@@ -208,6 +214,7 @@ static lc_status alloc_ctx(lc_ctx* c) {
   LC_TRY(cudaMemset(c->sort.status, 0, c->sort.status_words * 8));
   LC_TRY(cudaMalloc(&c->sort.hist, sizeof(uint32_t) * kMaxPasses * kRadix));
   LC_TRY(cudaMalloc(&c->sort.tickets, sizeof(unsigned) * 16));
+  LC_TRY(cudaMalloc(&c->bounds, sizeof(uint32_t) * ((1ull << hash_bits_for(m)) + 1)));
   // first arena chunk: 3 arrays per level for levels whose sizes sum to 2n,
   // plus the next level's min-original-id array
   LC_TRY(c->arena.init(4 * (2 * n + 256)));
@@ -310,26 +317,59 @@ static lc_status run_loop(lc_ctx* c, uint32_t* d_labels, uint32_t* rounds, uint6
              err, L);
     // (c): roots of the parent arborescences
     jump(c->minkey, lv.root, lv.mo, ni, L);
-    // (d): relabel, drop loops, sort, deduplicate, compact
+    // (d): relabel, drop loops, deduplicate, compact
     LC_TRY(cudaMemsetAsync(c->ctr, 0, 3 * sizeof(unsigned long long), c->stream));
     LC_TRY(cudaMemsetAsync(c->flags, 0, ni, c->stream));
     uint64_t* keys = (packed == c->ebuf[0]) ? c->ebuf[1] : c->ebuf[0];
     uint64_t* alt = (keys == c->ebuf[0]) ? c->ebuf[1] : c->ebuf[0];
     relabel(i == 0 ? c->src : nullptr, i == 0 ? c->dst : nullptr, packed, mi, ni, lv.root, bits,
             keys, &c->ctr->mprime, L);
-    int which = radix_sort_u64(keys, alt, &c->ctr->mprime, mi, 2 * bits, c->sort, err, c->flags,
-                               bits, L);
-    uint64_t* sorted = which ? alt : keys;
-    uint64_t* next = which ? keys : alt;
-    scan_flags(c->flags, lv.scan, ni, lv.mo, mo_next, &c->ctr->n_next, c->sort, err, L);
-    unique_rename(sorted, &c->ctr->mprime, mi, bits, lv.scan, next, &c->ctr->m_next, c->sort, err,
-                  L);
-    LC_TRY(cudaGetLastError());
-    LC_TRY(cudaMemcpyAsync(c->h_ctr, c->ctr, sizeof(Counters), cudaMemcpyDeviceToHost, c->stream));
-    LC_TRY(cudaStreamSynchronize(c->stream));
-    c->prof.resolve();
-    if (c->h_ctr->err & kErrBadVertex) return LC_ERR_INVALID;
-    if (c->h_ctr->err & kErrTimeout) return LC_ERR_TIMEOUT;
+    uint64_t* next = alt;
+    bool by_sort = c->dedup_sort;
+    if (!by_sort) {
+      int which = hash_dedup(keys, alt, &c->ctr->mprime, mi, bits, c->flags, c->bounds,
+                             &c->ctr->m_next, c->sort, err, L);
+      uint64_t* part = which ? alt : keys;
+      next = which ? keys : alt;
+      scan_flags(c->flags, lv.scan, ni, lv.mo, mo_next, &c->ctr->n_next, c->sort, err, L);
+      rename_edges(next, &c->ctr->m_next, mi, bits, lv.scan, L);
+      LC_TRY(cudaGetLastError());
+      LC_TRY(
+          cudaMemcpyAsync(c->h_ctr, c->ctr, sizeof(Counters), cudaMemcpyDeviceToHost, c->stream));
+      LC_TRY(cudaStreamSynchronize(c->stream));
+      c->prof.resolve();
+      if (c->h_ctr->err & kErrBadVertex) return LC_ERR_INVALID;
+      if (c->h_ctr->err & kErrTimeout) return LC_ERR_TIMEOUT;
+      if (c->h_ctr->err & kErrOverflow) {
+        // a bucket held more distinct keys than its shared-memory set: redo
+        // this phase's deduplication by a full sort of the intact keys
+        ++c->fallbacks;
+        by_sort = true;
+        keys = part;
+        alt = next;
+        LC_TRY(cudaMemsetAsync(&c->ctr->m_next, 0, 2 * sizeof(unsigned long long), c->stream));
+        LC_TRY(cudaMemsetAsync(&c->ctr->err, 0, sizeof(unsigned), c->stream));
+        LC_TRY(cudaMemsetAsync(c->flags, 0, ni, c->stream));
+      }
+    }
+    if (by_sort) {
+      // sort all key bits, mark endpoints of distinct keys, keep the first of
+      // each run renamed (output sorted)
+      int w2 = radix_sort_u64(keys, alt, &c->ctr->mprime, mi, 2 * bits, c->sort, err, c->flags,
+                              bits, L);
+      uint64_t* sorted = w2 ? alt : keys;
+      next = w2 ? keys : alt;
+      scan_flags(c->flags, lv.scan, ni, lv.mo, mo_next, &c->ctr->n_next, c->sort, err, L);
+      unique_rename(sorted, &c->ctr->mprime, mi, bits, lv.scan, next, &c->ctr->m_next, c->sort,
+                    err, L);
+      LC_TRY(cudaGetLastError());
+      LC_TRY(
+          cudaMemcpyAsync(c->h_ctr, c->ctr, sizeof(Counters), cudaMemcpyDeviceToHost, c->stream));
+      LC_TRY(cudaStreamSynchronize(c->stream));
+      c->prof.resolve();
+      if (c->h_ctr->err & kErrBadVertex) return LC_ERR_INVALID;
+      if (c->h_ctr->err & kErrTimeout) return LC_ERR_TIMEOUT;
+    }
     hn.push_back(ni);
     hm.push_back(mi);
     c->last_mp.push_back(c->h_ctr->mprime);
@@ -398,6 +438,13 @@ extern "C" lc_status lc_last_stats(const lc_ctx* c, uint32_t* rounds, uint64_t* 
   if (mp_i)
     for (uint32_t i = 0; i < std::min<uint32_t>(cap, (uint32_t)c->last_mp.size()); ++i)
       mp_i[i] = c->last_mp[i];
+  return LC_OK;
+}
+
+extern "C" lc_status lc_set_dedup(lc_ctx* c, lc_dedup mode) {
+  if (!c) return LC_ERR_INVALID;
+  if (mode != LC_DEDUP_HASH && mode != LC_DEDUP_SORT) return LC_ERR_INVALID;
+  c->dedup_sort = mode == LC_DEDUP_SORT;
   return LC_OK;
 }
 

@@ -31,7 +31,25 @@ __device__ __forceinline__ uint64_t phase_key(uint64_t rk, uint32_t v) {
 enum : uint32_t {
   kErrBadVertex = 1u,  // an input endpoint was >= n
   kErrTimeout = 2u,    // a bounded spin-wait gave up
+  kErrOverflow = 4u,   // a dedup bucket held more distinct keys than its table
 };
+
+// Mixer of an edge key for bucketing and hash-set slots (xorshift-multiply
+// rounds; any well-mixing bijection serves, the result never reaches the
+// output).
+__device__ __forceinline__ uint64_t key_mix(uint64_t k) {
+  k ^= k >> 32;
+  k *= 0xD6E8FEB86659FD93ull;
+  k ^= k >> 32;
+  k *= 0xD6E8FEB86659FD93ull;
+  k ^= k >> 32;
+  return k;
+}
+
+// Bucket of a key: the top hb bits of its mix (0 when hb == 0).
+__device__ __forceinline__ uint64_t bucket_hash(uint64_t k, int hb) {
+  return hb ? key_mix(k) >> (64 - hb) : 0ull;
+}
 
 // Iteration limit of every spin-wait on another block's status word.
 constexpr uint32_t kSpinLimit = 1u << 24;

@@ -23,6 +23,9 @@ enum KernelId : int {
   kKScanFlags,
   kKUniqueRename,
   kKPropagate,
+  kKBucketBounds,
+  kKBucketDedup,
+  kKRename,
   kKIdentity,
   kKRankProbe,
   kNumKernels
@@ -81,6 +84,8 @@ constexpr int kSortTile = kSortThreads * kSortItems;  // 4096 keys per tile
 constexpr int kRadixBits = 8;
 constexpr int kRadix = 1 << kRadixBits;
 constexpr int kMaxPasses = 8;
+constexpr int kBucketTarget = 2048;  // average keys per dedup bucket
+constexpr int kMaxHashBits = 24;
 
 // Scratch of the onesweep sort and the single-pass scans.  `status` holds one
 // 64-bit look-back word per (tile, digit); epochs make stale words invalid so
@@ -109,6 +114,28 @@ uint32_t next_epoch(SortScratch& s, const Launch& L);
 int radix_sort_u64(uint64_t* keys, uint64_t* alt, const unsigned long long* d_count,
                    uint64_t max_count, int key_bits, SortScratch& s, unsigned* err,
                    uint8_t* mark_flags, int half_bits, const Launch& L);
+
+// Bucket-hash bits used for max_count keys (0 when one bucket suffices).
+int hash_bits_for(uint64_t max_count);
+
+// Duplicate removal without a full sort: a stable LSD partition of
+// keys[0, *d_count) by an hb-bit hash of each key (hb = hash_bits_for(max_count),
+// at most 3 passes), so all copies of a key share one bucket of about
+// kBucketTarget keys; then one block per bucket keeps the distinct keys with a
+// shared-memory hash set, appends them (in no particular order) to the other
+// buffer, counts them in *m_next and marks both endpoints in flags.  Returns
+// which buffer holds the partitioned keys (0 = keys, 1 = alt); the distinct
+// keys are in the other one.  A bucket whose distinct keys overflow the set
+// raises kErrOverflow (the caller then falls back to radix_sort_u64).
+// `bounds` holds (1 << hb) + 1 words.
+int hash_dedup(uint64_t* keys, uint64_t* alt, const unsigned long long* d_count,
+               uint64_t max_count, int half_bits, uint8_t* flags, uint32_t* bounds,
+               unsigned long long* m_next, SortScratch& s, unsigned* err, const Launch& L);
+
+// e[j] = (newid[a] << 32 | newid[b]) for each key e[j] = (a << half_bits | b),
+// j < *d_count.
+void rename_edges(uint64_t* e, const unsigned long long* d_count, uint64_t max_count,
+                  int half_bits, const uint32_t* newid, const Launch& L);
 
 // In-place exclusive scan of flags[0, n) (values 0/1 as uint8) into
 // out[0, n] (uint32, out[n] = total); for every kept r (flag set) also copies

@@ -72,54 +72,27 @@ __global__ void __launch_bounds__(kThreads) k_edge_min_soa(
   for (uint64_t j = done + gt; j < m; j += stride) min_edge(__ldcs(src + j), __ldcs(dst + j), n, rk, minkey, err);
 }
 
-// Minimum of a 64-bit value over the lanes of `peers` (all calling with the
-// same mask): first over the high halves, then over the low halves of the
-// lanes that hold the minimum high half.
-__device__ __forceinline__ uint64_t group_min_u64(unsigned peers, uint64_t x) {
-  uint32_t hi = (uint32_t)(x >> 32), lo = (uint32_t)x;
-  uint32_t mhi = __reduce_min_sync(peers, hi);
-  unsigned tie = __ballot_sync(peers, hi == mhi) & peers;
-  uint32_t mlo = 0;
-  if (hi == mhi) mlo = __reduce_min_sync(tie, lo);
-  mlo = __shfl_sync(peers, mlo, __ffs(tie) - 1);
-  return ((uint64_t)mhi << 32) | mlo;
-}
-
-// Packed edges (a << 32 | b) with a < b, sorted by a: the a-side minima of a
-// warp are combined per distinct a before one atomic per group.
+// Packed edges (a << 32 | b), two per 128-bit load.
 __global__ void __launch_bounds__(kThreads) k_edge_min_packed(
     const uint64_t* __restrict__ e, uint64_t m, uint64_t rk, unsigned long long* minkey) {
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  const uint64_t npair = (m + 1) / 2;
+  const uint64_t npair = m / 2;
   const ulonglong2* e2 = reinterpret_cast<const ulonglong2*>(e);
-  // the loop trip count is uniform across the warp so the warp intrinsics see
-  // all 32 lanes
-  const uint64_t warp0 = ((uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u));
-  for (uint64_t q0 = warp0; q0 < npair; q0 += stride) {
-    uint64_t q = q0 + lane_id();
-    uint64_t x0 = ~0ull, x1 = ~0ull;
-    if (q < npair) {
-      if (2 * q + 1 < m) {
-        ulonglong2 p = __ldcs(e2 + q);
-        x0 = p.x;
-        x1 = p.y;
-      } else {
-        x0 = __ldcs(e + 2 * q);
-      }
-    }
-#pragma unroll
-    for (int s = 0; s < 2; ++s) {
-      uint64_t x = s == 0 ? x0 : x1;
-      bool valid = x != ~0ull;
-      uint32_t a = (uint32_t)(x >> 32), b = (uint32_t)x;
-      uint64_t kb = valid ? phase_key(rk, b) : ~0ull;
-      unsigned peers = __match_any_sync(kFull, valid ? a : 0xFFFFFFFFu);
-      uint64_t mk = group_min_u64(peers, kb);
-      if (valid) {
-        if ((peers & lanemask_lt()) == 0) atomicMin(&minkey[a], (unsigned long long)mk);
-        atomicMin(&minkey[b], (unsigned long long)phase_key(rk, a));
-      }
-    }
+  const uint64_t gt = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (uint64_t q = gt; q < npair; q += stride) {
+    ulonglong2 p = __ldcs(e2 + q);
+    uint32_t a0 = (uint32_t)(p.x >> 32), b0 = (uint32_t)p.x;
+    uint32_t a1 = (uint32_t)(p.y >> 32), b1 = (uint32_t)p.y;
+    atomicMin(&minkey[a0], (unsigned long long)phase_key(rk, b0));
+    atomicMin(&minkey[b0], (unsigned long long)phase_key(rk, a0));
+    atomicMin(&minkey[a1], (unsigned long long)phase_key(rk, b1));
+    atomicMin(&minkey[b1], (unsigned long long)phase_key(rk, a1));
+  }
+  if ((m & 1) && gt == 0) {
+    uint64_t x = e[m - 1];
+    uint32_t a = (uint32_t)(x >> 32), b = (uint32_t)x;
+    atomicMin(&minkey[a], (unsigned long long)phase_key(rk, b));
+    atomicMin(&minkey[b], (unsigned long long)phase_key(rk, a));
   }
 }
 
@@ -264,8 +237,8 @@ void edge_min(const uint32_t* src, const uint32_t* dst, const uint64_t* packed, 
   if (m == 0) return;
   if (packed != nullptr) {
     KScope ks(L, kKEdgeMinPacked);
-    k_edge_min_packed<<<grid_for((m + 1) / 2, kThreads, L), kThreads, 0, L.stream>>>(packed, m, rk,
-                                                                                    minkey);
+    k_edge_min_packed<<<grid_for(m / 2 + 1, kThreads, L), kThreads, 0, L.stream>>>(packed, m, rk,
+                                                                                   minkey);
   } else {
     int vec = ((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst)) & 15) == 0;
     KScope ks(L, kKEdgeMinSoa);

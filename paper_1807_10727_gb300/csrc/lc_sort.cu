@@ -88,9 +88,31 @@ __device__ __forceinline__ uint32_t look_back(uint64_t* status, uint32_t tile, u
 
 // ------------------------------------------------------------- histogram
 
+// Digit of a key in one pass: bits [shift, shift + bits) of the key itself
+// (plain sort) or of its hb-bit bucket hash (hash partition).
+struct DigitFn {
+  int shift;
+  uint32_t mask;
+  int hb;
+  __device__ __forceinline__ uint32_t operator()(uint64_t k) const {
+    uint64_t x = hb ? bucket_hash(k, hb) : k;
+    return (uint32_t)(x >> shift) & mask;
+  }
+};
+
+struct PassPlan {
+  int passes;
+  int hb;
+  int shift[kMaxPasses];
+  int bits[kMaxPasses];
+  __host__ __device__ DigitFn digit(int p) const {
+    return DigitFn{shift[p], (1u << bits[p]) - 1u, hb};
+  }
+};
+
 __global__ void __launch_bounds__(kSortThreads) k_sort_hist(const uint64_t* __restrict__ keys,
                                                             const unsigned long long* d_count,
-                                                            int passes, uint32_t* ghist) {
+                                                            PassPlan plan, uint32_t* ghist) {
   __shared__ uint32_t h[kMaxPasses][kRadix];
   for (int i = threadIdx.x; i < kMaxPasses * kRadix; i += blockDim.x) (&h[0][0])[i] = 0;
   __syncthreads();
@@ -98,10 +120,14 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_hist(const uint64_t* __re
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride) {
     uint64_t k = __ldcs(keys + i);
-    for (int p = 0; p < passes; ++p) atomicAdd(&h[p][(k >> (kRadixBits * p)) & (kRadix - 1)], 1u);
+    uint64_t x = plan.hb ? bucket_hash(k, plan.hb) : k;
+#pragma unroll
+    for (int p = 0; p < kMaxPasses; ++p)
+      if (p < plan.passes)
+        atomicAdd(&h[p][(uint32_t)(x >> plan.shift[p]) & ((1u << plan.bits[p]) - 1u)], 1u);
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < passes * kRadix; i += blockDim.x) {
+  for (int i = threadIdx.x; i < plan.passes * kRadix; i += blockDim.x) {
     uint32_t c = (&h[0][0])[i];
     if (c) atomicAdd(&ghist[i], c);
   }
@@ -118,14 +144,17 @@ __global__ void __launch_bounds__(kRadix) k_hist_scan(uint32_t* ghist) {
 
 // ------------------------------------------------------------ one pass
 
-__global__ void __launch_bounds__(kSortThreads) k_sort_pass(
+// One stable counting pass over a 4096-key tile.  Lanes holding the same
+// digit are found by slicing the digit into bits and intersecting ballots
+// (one vote per digit bit), so ranking needs no match instruction; each warp
+// counts its digits in its own shared-memory row.
+__global__ void __launch_bounds__(kSortThreads, 3) k_sort_pass(
     const uint64_t* __restrict__ in, uint64_t* __restrict__ out, const unsigned long long* d_count,
-    int shift, const uint32_t* __restrict__ digit_offset, uint64_t* status, uint32_t epoch,
-    unsigned* ticket, unsigned* err, uint8_t* mark_flags, int half_bits) {
+    DigitFn dg, int bits, const uint32_t* __restrict__ digit_offset, uint64_t* status,
+    uint32_t epoch, unsigned* ticket, unsigned* err, uint8_t* mark_flags, int half_bits) {
   __shared__ uint64_t sk[kSortTile];
   __shared__ uint32_t whist[kWarps][kRadix];
-  __shared__ uint32_t tstart[kRadix];
-  __shared__ uint32_t gbase[kRadix];
+  __shared__ uint32_t gofs[kRadix];
   __shared__ uint32_t ws[kWarps];
   __shared__ uint32_t s_tile;
   __shared__ int s_bad;
@@ -141,29 +170,37 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_pass(
   const uint64_t count = *d_count;
   const uint64_t base = (uint64_t)tile * kSortTile;
   if (base >= count) return;
-  const uint32_t nvalid = (uint32_t)(count - base < (uint64_t)kSortTile ? count - base : (uint64_t)kSortTile);
+  const uint32_t nvalid =
+      (uint32_t)(count - base < (uint64_t)kSortTile ? count - base : (uint64_t)kSortTile);
 
-  // load: warp w owns tile positions [w*32*kSortItems, (w+1)*32*kSortItems),
-  // item i of lane l is position w*32*kSortItems + i*32 + l
+  // warp w owns tile positions [w*32*kSortItems, (w+1)*32*kSortItems); item i
+  // of lane l is position w*32*kSortItems + i*32 + l
   uint64_t k[kSortItems];
   uint32_t off[kSortItems];
   const uint32_t wbase = w * 32 * kSortItems;
 #pragma unroll
   for (int i = 0; i < kSortItems; ++i) {
     uint32_t pos = wbase + i * 32 + lane;
-    k[i] = pos < nvalid ? __ldcs(in + base + pos) : ~0ull;
+    k[i] = pos < nvalid ? __ldcs(in + base + pos) : 0ull;
   }
-  // stable warp-level ranking: earlier items, then lower lanes, come first
+  const unsigned lt = lanemask_lt();
 #pragma unroll
   for (int i = 0; i < kSortItems; ++i) {
-    uint32_t pos = wbase + i * 32 + lane;
-    uint32_t d = pos < nvalid ? (uint32_t)(k[i] >> shift) & (kRadix - 1) : (uint32_t)kRadix;
-    unsigned peers = __match_any_sync(kFull, d);
-    uint32_t r = __popc(peers & lanemask_lt());
-    uint32_t cnt = d < (uint32_t)kRadix ? whist[w][d] : 0u;
+    const bool valid = wbase + i * 32 + lane < nvalid;
+    const uint32_t d = dg(k[i]);
+    unsigned peers = __ballot_sync(kFull, valid);
+#pragma unroll
+    for (int b = 0; b < kRadixBits; ++b) {
+      if (b < bits) {
+        unsigned v = __ballot_sync(kFull, (d >> b) & 1u);
+        peers &= ((d >> b) & 1u) ? v : ~v;
+      }
+    }
+    uint32_t r = __popc(peers & lt);
+    uint32_t cnt = valid ? whist[w][d] : 0u;
     off[i] = cnt + r;
     __syncwarp();
-    if (d < (uint32_t)kRadix && r == 0) whist[w][d] = cnt + __popc(peers);
+    if (valid && r == 0) whist[w][d] = cnt + __popc(peers);
     __syncwarp();
   }
   __syncthreads();
@@ -178,10 +215,9 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_pass(
     run += t;
   }
   const uint32_t tcount = run;
+  uint32_t prefix = 0;
   {
-    // status words of this pass: [tile][digit] laid out digit-major per tile
     uint64_t* st = status + (uint64_t)tile * kRadix + d;
-    uint32_t prefix = 0;
     if (tile == 0) {
       store_status(st, pack_status(epoch, kFlagPrefix, tcount));
     } else {
@@ -210,36 +246,135 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_pass(
       }
       store_status(st, pack_status(epoch, kFlagPrefix, prefix + tcount));
     }
-    gbase[d] = digit_offset[d] + prefix;
   }
   uint32_t total;
-  tstart[d] = block_exclusive_scan(tcount, ws, &total);
+  const uint32_t tstart = block_exclusive_scan(tcount, ws, &total);
+#pragma unroll
+  for (int ww = 0; ww < kWarps; ++ww) whist[ww][d] += tstart;
+  gofs[d] = digit_offset[d] + prefix - tstart;
   __syncthreads();
   if (s_bad) return;  // offsets unknown: write nothing (the host sees kErrTimeout)
 
   // stage the tile in digit order
 #pragma unroll
   for (int i = 0; i < kSortItems; ++i) {
-    uint32_t pos = wbase + i * 32 + lane;
-    if (pos < nvalid) {
-      uint32_t dd = (uint32_t)(k[i] >> shift) & (kRadix - 1);
-      sk[tstart[dd] + whist[w][dd] + off[i]] = k[i];
-    }
+    if (wbase + i * 32 + lane < nvalid) sk[whist[w][dg(k[i])] + off[i]] = k[i];
   }
   __syncthreads();
 
   // coalesced write-out; optionally mark both endpoints of every key that
-  // starts a run of equal keys inside the tile
+  // starts a run of equal keys inside the tile (the full-sort path)
   const uint64_t half_mask = (half_bits >= 64) ? ~0ull : ((1ull << half_bits) - 1);
   for (uint32_t j = tid; j < nvalid; j += kSortThreads) {
     uint64_t key = sk[j];
-    uint32_t dd = (uint32_t)(key >> shift) & (kRadix - 1);
-    uint64_t gpos = (uint64_t)gbase[dd] + (j - tstart[dd]);
+    uint64_t gpos = (uint64_t)gofs[dg(key)] + j;
     if (gpos < count) out[gpos] = key;
     if (mark_flags != nullptr && (j == 0 || sk[j - 1] != key)) {
       mark_flags[key >> half_bits] = 1;
       mark_flags[key & half_mask] = 1;
     }
+  }
+}
+
+// --------------------------------------------- hashed buckets and dedup
+
+// bounds[b] = first position whose bucket hash is >= b, for b in [0, nb];
+// the keys are partitioned in ascending order of their bucket hash.
+__global__ void k_bucket_bounds(const uint64_t* __restrict__ keys,
+                                const unsigned long long* d_count, int hb, uint32_t nb,
+                                uint32_t* __restrict__ bounds) {
+  const uint64_t count = *d_count;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; b <= nb; b += stride) {
+    uint64_t lo = 0, hi = count;
+    while (lo < hi) {
+      uint64_t mid = (lo + hi) >> 1;
+      if (bucket_hash(keys[mid], hb) < b) lo = mid + 1;
+      else hi = mid;
+    }
+    bounds[b] = (uint32_t)lo;
+  }
+}
+
+constexpr int kTableSlots = 4096;  // per-bucket shared-memory hash set (32 KB)
+constexpr uint64_t kEmpty = ~0ull;  // never a key: keys are (a << bits | b) with a < b
+
+// One bucket per iteration (claimed by ticket): insert its keys into a
+// shared-memory open-addressing set, then append the distinct keys to `out`
+// (one atomicAdd per bucket) and mark both endpoints of each in `flags`.
+__global__ void __launch_bounds__(kSortThreads) k_bucket_dedup(
+    const uint64_t* __restrict__ keys, const uint32_t* __restrict__ bounds, uint32_t nb,
+    uint64_t* __restrict__ out, unsigned long long* m_next, uint8_t* flags, int half_bits,
+    unsigned* ticket, unsigned* err) {
+  __shared__ uint64_t table[kTableSlots];
+  __shared__ uint32_t ws[kWarps];
+  __shared__ uint32_t s_b;
+  __shared__ unsigned long long s_base;
+  __shared__ int s_over;
+  const unsigned tid = threadIdx.x;
+  constexpr int kPer = kTableSlots / kSortThreads;
+  for (int i = tid; i < kTableSlots; i += kSortThreads) table[i] = kEmpty;
+  if (tid == 0) s_over = 0;
+  const uint64_t half_mask = (1ull << half_bits) - 1;
+  for (;;) {
+    if (tid == 0) s_b = atomicAdd(ticket, 1u);
+    __syncthreads();
+    const uint32_t b = s_b;
+    if (b >= nb) break;
+    const uint32_t lo = bounds[b], hi = bounds[b + 1];
+    for (uint32_t i = lo + tid; i < hi; i += kSortThreads) {
+      const uint64_t key = __ldcs(keys + i);
+      uint32_t slot = (uint32_t)key_mix(key) & (kTableSlots - 1);
+      int probe = 0;
+      for (; probe < kTableSlots; ++probe) {
+        uint64_t cur = *(volatile uint64_t*)&table[slot];
+        if (cur == key) break;
+        if (cur == kEmpty) {
+          uint64_t prev = atomicCAS((unsigned long long*)&table[slot], kEmpty, key);
+          if (prev == kEmpty || prev == key) break;
+        }
+        slot = (slot + 1) & (kTableSlots - 1);
+      }
+      if (probe == kTableSlots) s_over = 1;
+    }
+    __syncthreads();
+    uint32_t cnt = 0;
+#pragma unroll
+    for (int s = 0; s < kPer; ++s) cnt += table[tid * kPer + s] != kEmpty;
+    uint32_t total;
+    uint32_t excl = block_exclusive_scan(cnt, ws, &total);
+    if (tid == 0) {
+      s_base = total ? atomicAdd(m_next, (unsigned long long)total) : 0ull;
+      if (s_over) {
+        atomicOr(err, kErrOverflow);
+        s_over = 0;
+      }
+    }
+    __syncthreads();
+    uint64_t pos = s_base + excl;
+#pragma unroll
+    for (int s = 0; s < kPer; ++s) {
+      uint64_t v = table[tid * kPer + s];
+      if (v != kEmpty) {
+        out[pos++] = v;
+        flags[v >> half_bits] = 1;
+        flags[v & half_mask] = 1;
+        table[tid * kPer + s] = kEmpty;
+      }
+    }
+    // the next iteration's barrier orders these clears before new inserts
+  }
+}
+
+// e[j] = (newid[a] << 32 | newid[b]) for e[j] = (a << half_bits | b).
+__global__ void k_rename(uint64_t* __restrict__ e, const unsigned long long* d_count,
+                         int half_bits, const uint32_t* __restrict__ newid) {
+  const uint64_t count = *d_count;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  const uint64_t half_mask = (1ull << half_bits) - 1;
+  for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < count; j += stride) {
+    uint64_t k = e[j];
+    e[j] = ((uint64_t)newid[k >> half_bits] << 32) | newid[k & half_mask];
   }
 }
 
@@ -375,35 +510,95 @@ uint32_t next_epoch(SortScratch& s, const Launch& L) {
   return ++s.epoch;
 }
 
-int radix_sort_u64(uint64_t* keys, uint64_t* alt, const unsigned long long* d_count,
-                   uint64_t max_count, int key_bits, SortScratch& s, unsigned* err,
-                   uint8_t* mark_flags, int half_bits, const Launch& L) {
-  if (max_count == 0) return 0;
-  int passes = (std::max(key_bits, 1) + kRadixBits - 1) / kRadixBits;
+static int run_passes(uint64_t* keys, uint64_t* alt, const unsigned long long* d_count,
+                      uint64_t max_count, const PassPlan& plan, SortScratch& s, unsigned* err,
+                      uint8_t* mark_flags, int half_bits, const Launch& L) {
+  if (max_count == 0 || plan.passes == 0) return 0;
   cudaMemsetAsync(s.hist, 0, sizeof(uint32_t) * kMaxPasses * kRadix, L.stream);
-  cudaMemsetAsync(s.tickets, 0, sizeof(unsigned) * 16, L.stream);
+  cudaMemsetAsync(s.tickets, 0, sizeof(unsigned) * 8, L.stream);
   uint64_t tiles = (max_count + kSortTile - 1) / kSortTile;
   int hgrid = (int)std::min<uint64_t>(tiles, (uint64_t)L.sms * 4);
   {
     KScope ks(L, kKSortHist);
-    k_sort_hist<<<hgrid, kSortThreads, 0, L.stream>>>(keys, d_count, passes, s.hist);
+    k_sort_hist<<<hgrid, kSortThreads, 0, L.stream>>>(keys, d_count, plan, s.hist);
   }
   {
     KScope ks(L, kKHistScan);
-    k_hist_scan<<<passes, kRadix, 0, L.stream>>>(s.hist);
+    k_hist_scan<<<plan.passes, kRadix, 0, L.stream>>>(s.hist);
   }
   uint64_t* src = keys;
   uint64_t* dst = alt;
-  for (int p = 0; p < passes; ++p) {
+  for (int p = 0; p < plan.passes; ++p) {
     uint32_t epoch = next_epoch(s, L);
-    bool last = p == passes - 1;
+    bool last = p == plan.passes - 1;
     KScope ks(L, kKSortPass);
     k_sort_pass<<<(unsigned)tiles, kSortThreads, 0, L.stream>>>(
-        src, dst, d_count, kRadixBits * p, s.hist + p * kRadix, s.status, epoch, s.tickets + p,
-        err, last ? mark_flags : nullptr, half_bits);
+        src, dst, d_count, plan.digit(p), plan.bits[p], s.hist + p * kRadix, s.status, epoch,
+        s.tickets + p, err, last ? mark_flags : nullptr, half_bits);
     std::swap(src, dst);
   }
-  return passes & 1;
+  return plan.passes & 1;
+}
+
+int radix_sort_u64(uint64_t* keys, uint64_t* alt, const unsigned long long* d_count,
+                   uint64_t max_count, int key_bits, SortScratch& s, unsigned* err,
+                   uint8_t* mark_flags, int half_bits, const Launch& L) {
+  PassPlan plan{};
+  plan.hb = 0;
+  plan.passes = (std::max(key_bits, 1) + kRadixBits - 1) / kRadixBits;
+  for (int p = 0; p < plan.passes; ++p) {
+    plan.shift[p] = kRadixBits * p;
+    plan.bits[p] = kRadixBits;
+  }
+  return run_passes(keys, alt, d_count, max_count, plan, s, err, mark_flags, half_bits, L);
+}
+
+int hash_bits_for(uint64_t max_count) {
+  int b = 0;
+  while (b < kMaxHashBits && ((uint64_t)kBucketTarget << b) < max_count) ++b;
+  return b;
+}
+
+int hash_dedup(uint64_t* keys, uint64_t* alt, const unsigned long long* d_count,
+               uint64_t max_count, int half_bits, uint8_t* flags, uint32_t* bounds,
+               unsigned long long* m_next, SortScratch& s, unsigned* err, const Launch& L) {
+  if (max_count == 0) return 0;
+  const int hb = hash_bits_for(max_count);
+  PassPlan plan{};
+  plan.hb = hb;
+  plan.passes = (hb + kRadixBits - 1) / kRadixBits;
+  int shift = 0;
+  for (int p = 0; p < plan.passes; ++p) {
+    int w = hb / plan.passes + (p < hb % plan.passes ? 1 : 0);
+    plan.shift[p] = shift;
+    plan.bits[p] = w;
+    shift += w;
+  }
+  int which = run_passes(keys, alt, d_count, max_count, plan, s, err, nullptr, half_bits, L);
+  uint64_t* part = which ? alt : keys;
+  uint64_t* out = which ? keys : alt;
+  const uint32_t nb = 1u << hb;
+  {
+    KScope ks(L, kKBucketBounds);
+    int g = (int)std::min<uint64_t>(((uint64_t)nb + 256) / 256, (uint64_t)L.sms * 8);
+    k_bucket_bounds<<<g, 256, 0, L.stream>>>(part, d_count, hb, nb, bounds);
+  }
+  cudaMemsetAsync(s.tickets + 10, 0, sizeof(unsigned), L.stream);
+  {
+    KScope ks(L, kKBucketDedup);
+    int g = (int)std::min<uint64_t>(nb, (uint64_t)L.sms * 6);
+    k_bucket_dedup<<<g, kSortThreads, 0, L.stream>>>(part, bounds, nb, out, m_next, flags,
+                                                     half_bits, s.tickets + 10, err);
+  }
+  return which;  // keys partitioned in `part` (0: keys, 1: alt); distinct keys in the other
+}
+
+void rename_edges(uint64_t* e, const unsigned long long* d_count, uint64_t max_count,
+                  int half_bits, const uint32_t* newid, const Launch& L) {
+  if (max_count == 0) return;
+  KScope ks(L, kKRename);
+  int g = (int)std::min<uint64_t>((max_count + 255) / 256, (uint64_t)L.sms * 8);
+  k_rename<<<g, 256, 0, L.stream>>>(e, d_count, half_bits, newid);
 }
 
 void scan_flags(const uint8_t* flags, uint32_t* out, uint32_t n, const uint32_t* mo_in,

@@ -22,7 +22,8 @@ LC_OK, LC_ERR_INVALID, LC_ERR_OOM, LC_ERR_CUDA, LC_ERR_NO_CONVERGENCE, LC_ERR_TI
 LC_VARIANT_FOREST, LC_VARIANT_TWO_HOP, LC_VARIANT_TREE = 0, 1, 2
 
 # every symbol include/lc.h declares (checked by the CPU test suite)
-EXPORTED = ("lc_create", "lc_configure", "lc_run", "lc_run_host", "lc_last_stats", "lc_profile",
+LC_DEDUP_HASH, LC_DEDUP_SORT = 0, 1
+EXPORTED = ("lc_create", "lc_configure", "lc_set_dedup", "lc_run", "lc_run_host", "lc_last_stats", "lc_profile",
             "lc_kernel_stats", "lc_destroy", "lc_status_str", "lc_rank_probe")
 
 _lib = None
@@ -47,6 +48,7 @@ def load(path: str | None = None):
     pu32, pu64 = ctypes.POINTER(u32), ctypes.POINTER(u64)
     lib.lc_create.argtypes = [u32, p, p, u64, u64, p, ctypes.POINTER(p)]
     lib.lc_configure.argtypes = [p, i32, u64]
+    lib.lc_set_dedup.argtypes = [p, i32]
     lib.lc_run.argtypes = [p, p, pu32, pu64, pu64, u32]
     lib.lc_run_host.argtypes = [p, p, p, p, pu32, pu64, pu64, u32]
     lib.lc_last_stats.argtypes = [p, pu32, pu64, u32]
@@ -100,6 +102,10 @@ def lc_create(n: int, d_src: int, d_dst: int, m: int, seed: int, stream: int) ->
 
 def lc_configure(ctx: int, variant: int, finish_edges: int = 0) -> None:
     _check(load().lc_configure(ctx, variant, finish_edges), "lc_configure")
+
+
+def lc_set_dedup(ctx: int, mode: int) -> None:
+    _check(load().lc_set_dedup(ctx, mode), "lc_set_dedup")
 
 
 def lc_run(ctx: int, d_labels: int, cap: int = 1024):
@@ -176,7 +182,8 @@ class LocalContraction:
     """
 
     def __init__(self, n: int, src=None, dst=None, m: int | None = None, seed: int = 0,
-                 stream=None, variant: int = LC_VARIANT_FOREST, finish_edges: int = 0):
+                 stream=None, variant: int = LC_VARIANT_FOREST, finish_edges: int = 0,
+                 dedup: int = LC_DEDUP_HASH):
         if src is None:
             if m is None:
                 raise ValueError("m is required when the context owns its inputs")
@@ -192,6 +199,8 @@ class LocalContraction:
                              self.m, seed, _stream_handle(stream))
         if variant != LC_VARIANT_FOREST or finish_edges:
             lc_configure(self.ctx, variant, finish_edges)
+        if dedup != LC_DEDUP_HASH:
+            lc_set_dedup(self.ctx, dedup)
 
     def run(self, labels=None, cap: int = 1024):
         import torch

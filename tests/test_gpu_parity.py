@@ -28,7 +28,7 @@ def gpu_run(n, s, d, seed, cuda, **kw):
 
 
 def assert_parity(n, s, d, seed, cuda, **kw):
-    labels, res, mp = gpu_run(n, s, d, seed, cuda)
+    labels, res, mp = gpu_run(n, s, d, seed, cuda, **kw)
     ref = oracle.lc_run(n, s, d, seed)
     assert res.rounds == ref.rounds
     assert [(a, b) for a, b in zip(res.n_i, res.m_i)] == ref.sizes()
@@ -43,10 +43,11 @@ def test_rank_probe_matches_oracle(lc_lib, cuda):
         assert np.array_equal(got, oracle.ranks(seed, i, v0, count))
 
 
+@pytest.mark.parametrize("dedup", [lc.LC_DEDUP_HASH, lc.LC_DEDUP_SORT])
 @pytest.mark.parametrize("name", ["er16", "rmat14", "rmat18", "gridmix_small"])
-def test_workload_parity(lc_lib, cuda, name):
+def test_workload_parity(lc_lib, cuda, name, dedup):
     g = synth.workload(name)
-    assert_parity(g.n, g.src, g.dst, g.seed, cuda)
+    assert_parity(g.n, g.src, g.dst, g.seed, cuda, dedup=dedup)
 
 
 def test_er16_several_seeds(lc_lib, cuda):
@@ -55,23 +56,27 @@ def test_er16_several_seeds(lc_lib, cuda):
         assert_parity(g.n, g.src, g.dst, seed, cuda)
 
 
-def test_many_small_random_graphs(lc_lib, cuda):
+@pytest.mark.parametrize("dedup", [lc.LC_DEDUP_HASH, lc.LC_DEDUP_SORT])
+def test_many_small_random_graphs(lc_lib, cuda, dedup):
     rng = np.random.default_rng(17)
     for t in range(120):
         n = int(rng.integers(1, 70))
         m = int(rng.integers(0, 3 * n))
         s = rng.integers(0, n, m)
         d = rng.integers(0, n, m)
-        assert_parity(n, s, d, t, cuda)
+        assert_parity(n, s, d, t, cuda, dedup=dedup)
 
 
-def test_ragged_sizes_across_tiles(lc_lib, cuda):
-    """Sizes around the 4096-key tile and the 16-element vector widths."""
+@pytest.mark.parametrize("dedup", [lc.LC_DEDUP_HASH, lc.LC_DEDUP_SORT])
+def test_ragged_sizes_across_tiles(lc_lib, cuda, dedup):
+    """Sizes around the 4096-key tile, the 2048-key dedup bucket and the
+    16-element vector widths."""
     rng = np.random.default_rng(23)
-    for n, m in [(4097, 4095), (4096, 4097), (5000, 8191), (70001, 123457), (3, 100003)]:
+    for n, m in [(4097, 4095), (4096, 4097), (5000, 8191), (70001, 123457), (3, 100003),
+                 (2049, 2048), (100, 2049)]:
         s = rng.integers(0, n, m)
         d = rng.integers(0, n, m)
-        assert_parity(n, s, d, 9, cuda)
+        assert_parity(n, s, d, 9, cuda, dedup=dedup)
 
 
 # ---------------------------------------------------------- edge cases
