@@ -95,6 +95,15 @@ typedef enum {
  * hash buckets overflow. */
 lc_status lc_set_dedup(lc_ctx* ctx, lc_dedup mode);
 
+/* Tuning parameters (no counterpart in the paper; they change speed only,
+ * never results):
+ *   "window_bytes"  L2 budget (bytes, >= 1 MiB) of one pass of the phase-0
+ *                   closed-neighbourhood minimum: vertices are processed in
+ *                   windows of window_bytes / 8 ids, one pass over the input
+ *                   edges per window (default 128 MiB).
+ * Unknown names or out-of-range values give LC_ERR_INVALID. */
+lc_status lc_set_param(lc_ctx* ctx, const char* name, uint64_t value);
+
 /* Run the whole phase loop.
  *   d_labels  device uint32[n], caller-owned: labels[v] = smallest vertex id in
  *             v's connected component.

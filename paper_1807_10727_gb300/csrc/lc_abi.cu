@@ -163,6 +163,7 @@ struct lc_ctx {
   uint32_t* bounds = nullptr;  // bucket boundaries of the hashed dedup
   uint64_t fallbacks = 0;      // phases that needed the full-sort dedup
   bool dedup_sort = false;     // deduplicate by a full radix sort every phase
+  uint64_t window_bytes = 128ull << 20;  // L2 budget of one phase-0 minimum pass
 
   uint32_t last_rounds = 0;
   std::vector<uint64_t> last_mp;
@@ -314,20 +315,20 @@ static lc_status run_loop(lc_ctx* c, uint32_t* d_labels, uint32_t* rounds, uint6
     // (a) + (b): ranks and closed-neighbourhood minimum
     init_keys(c->minkey, i == 0 ? lv.mo : nullptr, ni, rk, L);
     edge_min(i == 0 ? c->src : nullptr, i == 0 ? c->dst : nullptr, packed, mi, ni, rk, c->minkey,
-             err, L);
+             err, c->window_bytes, L);
     // (c): roots of the parent arborescences
     jump(c->minkey, lv.root, lv.mo, ni, L);
     // (d): relabel, drop loops, deduplicate, compact
-    LC_TRY(cudaMemsetAsync(c->ctr, 0, 3 * sizeof(unsigned long long), c->stream));
+    LC_TRY(cudaMemsetAsync(c->ctr, 0, 4 * sizeof(unsigned long long), c->stream));
     LC_TRY(cudaMemsetAsync(c->flags, 0, ni, c->stream));
     uint64_t* keys = (packed == c->ebuf[0]) ? c->ebuf[1] : c->ebuf[0];
     uint64_t* alt = (keys == c->ebuf[0]) ? c->ebuf[1] : c->ebuf[0];
     relabel(i == 0 ? c->src : nullptr, i == 0 ? c->dst : nullptr, packed, mi, ni, lv.root, bits,
-            keys, &c->ctr->mprime, L);
+            keys, &c->ctr->mprime, &c->ctr->emitted, L);
     uint64_t* next = alt;
     bool by_sort = c->dedup_sort;
     if (!by_sort) {
-      int which = hash_dedup(keys, alt, &c->ctr->mprime, mi, bits, c->flags, c->bounds,
+      int which = hash_dedup(keys, alt, &c->ctr->emitted, mi, bits, c->flags, c->bounds,
                              &c->ctr->m_next, c->sort, err, L);
       uint64_t* part = which ? alt : keys;
       next = which ? keys : alt;
@@ -355,12 +356,12 @@ static lc_status run_loop(lc_ctx* c, uint32_t* d_labels, uint32_t* rounds, uint6
     if (by_sort) {
       // sort all key bits, mark endpoints of distinct keys, keep the first of
       // each run renamed (output sorted)
-      int w2 = radix_sort_u64(keys, alt, &c->ctr->mprime, mi, 2 * bits, c->sort, err, c->flags,
+      int w2 = radix_sort_u64(keys, alt, &c->ctr->emitted, mi, 2 * bits, c->sort, err, c->flags,
                               bits, L);
       uint64_t* sorted = w2 ? alt : keys;
       next = w2 ? keys : alt;
       scan_flags(c->flags, lv.scan, ni, lv.mo, mo_next, &c->ctr->n_next, c->sort, err, L);
-      unique_rename(sorted, &c->ctr->mprime, mi, bits, lv.scan, next, &c->ctr->m_next, c->sort,
+      unique_rename(sorted, &c->ctr->emitted, mi, bits, lv.scan, next, &c->ctr->m_next, c->sort,
                     err, L);
       LC_TRY(cudaGetLastError());
       LC_TRY(
@@ -446,6 +447,16 @@ extern "C" lc_status lc_set_dedup(lc_ctx* c, lc_dedup mode) {
   if (mode != LC_DEDUP_HASH && mode != LC_DEDUP_SORT) return LC_ERR_INVALID;
   c->dedup_sort = mode == LC_DEDUP_SORT;
   return LC_OK;
+}
+
+extern "C" lc_status lc_set_param(lc_ctx* c, const char* name, uint64_t value) {
+  if (!c || !name) return LC_ERR_INVALID;
+  if (std::strcmp(name, "window_bytes") == 0) {
+    if (value < (1u << 20)) return LC_ERR_INVALID;
+    c->window_bytes = value;
+    return LC_OK;
+  }
+  return LC_ERR_INVALID;
 }
 
 extern "C" lc_status lc_profile(lc_ctx* c, int on) {

@@ -56,11 +56,12 @@ constexpr uint32_t kSpinLimit = 1u << 24;
 
 // Per-run device counters, read back once per phase with one small copy.
 struct Counters {
-  unsigned long long mprime;   // keys emitted by relabel (m'_i)
-  unsigned long long m_next;   // unique edges (m_{i+1})
+  unsigned long long mprime;   // non-loop edges after relabelling (m'_i)
+  unsigned long long m_next;   // distinct edges (m_{i+1})
   unsigned long long n_next;   // surviving nodes (n_{i+1})
+  unsigned long long emitted;  // keys written by relabel (m'_i minus repeats it dropped)
   unsigned int err;            // kErr* bits
-  unsigned int tile_ticket[7]; // dynamic tile counters (reset per launch)
+  unsigned int pad;
 };
 
 __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }

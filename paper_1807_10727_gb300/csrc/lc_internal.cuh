@@ -160,10 +160,12 @@ void init_keys(unsigned long long* minkey, uint32_t* mo, uint32_t n, uint64_t rk
 // minkey[v] = min(minkey[v], key(u)) for every edge.  Edges are either two
 // uint32 arrays (src, dst) with ids validated against n (bad ids set
 // kErrBadVertex and are skipped), or packed uint64 (a << 32 | b) sorted by a
-// (packed != nullptr), in which case a-side updates are combined per warp.
+// (packed != nullptr).  For the uint32 form, vertices are processed in windows
+// of at most window_bytes / 8 ids, one pass over the edges per window, so that
+// each pass's atomics stay inside an L2-sized slice of minkey.
 void edge_min(const uint32_t* src, const uint32_t* dst, const uint64_t* packed, uint64_t m,
               uint32_t n, uint64_t rk, unsigned long long* minkey, unsigned* err,
-              const Launch& L);
+              uint64_t window_bytes, const Launch& L);
 
 // root[v] = root of v's arborescence (follows the parent stored in the low
 // half of minkey, compressing as it goes); mo[root] = min over the tree of
@@ -171,10 +173,12 @@ void edge_min(const uint32_t* src, const uint32_t* dst, const uint64_t* packed, 
 void jump(unsigned long long* minkey, uint32_t* root, uint32_t* mo, uint32_t n, const Launch& L);
 
 // Relabel every edge through root, drop self-loops, emit (min << bits | max)
-// keys compacted to keys_out; *count gets the number emitted.
+// keys compacted to keys_out.  *mprime gets the number of non-loop edges;
+// *emitted the number of keys written, which omits repeats of a key that the
+// same block has already written (the written keys hold every distinct key).
 void relabel(const uint32_t* src, const uint32_t* dst, const uint64_t* packed, uint64_t m,
              uint32_t n, const uint32_t* root, int bits, uint64_t* keys_out,
-             unsigned long long* count, const Launch& L);
+             unsigned long long* mprime, unsigned long long* emitted, const Launch& L);
 
 // labels_out[v] = kept(root[v]) ? labels_up[scan[root[v]]] : mo[root[v]], with
 // kept(r) = scan[r+1] > scan[r].  labels_out may alias root.

@@ -49,10 +49,26 @@ __device__ __forceinline__ void min_edge(uint32_t u, uint32_t v, uint32_t n, uin
   atomicMin(&minkey[v], (unsigned long long)phase_key(rk, u));
 }
 
+// Window form of min_edge: only endpoints in [lo, lo + span) are updated, so
+// the updates of one pass over the edges touch an L2-sized slice of minkey.
+__device__ __forceinline__ void min_edge_window(uint32_t u, uint32_t v, uint32_t n, uint64_t rk,
+                                                unsigned long long* minkey, unsigned* err,
+                                                uint32_t lo, uint32_t span, bool check) {
+  if (check && (u >= n || v >= n)) {
+    atomicOr(err, kErrBadVertex);
+    return;
+  }
+  if (u == v) return;
+  if (u - lo < span) atomicMin(&minkey[u], (unsigned long long)phase_key(rk, v));
+  if (v - lo < span) atomicMin(&minkey[v], (unsigned long long)phase_key(rk, u));
+}
+
 // Input edges as two uint32 arrays; `vec` = both arrays 16-byte aligned.
+// Updates only vertices in [lo, lo + span); ids are validated when `check`.
 __global__ void __launch_bounds__(kThreads) k_edge_min_soa(
     const uint32_t* __restrict__ src, const uint32_t* __restrict__ dst, uint64_t m, uint32_t n,
-    uint64_t rk, unsigned long long* minkey, unsigned* err, int vec) {
+    uint64_t rk, unsigned long long* minkey, unsigned* err, int vec, uint32_t lo, uint32_t span,
+    int check) {
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   const uint64_t gt = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   uint64_t done = 0;
@@ -62,14 +78,15 @@ __global__ void __launch_bounds__(kThreads) k_edge_min_soa(
     const uint4* d4 = reinterpret_cast<const uint4*>(dst);
     for (uint64_t q = gt; q < nq; q += stride) {
       uint4 s = __ldcs(s4 + q), d = __ldcs(d4 + q);
-      min_edge(s.x, d.x, n, rk, minkey, err);
-      min_edge(s.y, d.y, n, rk, minkey, err);
-      min_edge(s.z, d.z, n, rk, minkey, err);
-      min_edge(s.w, d.w, n, rk, minkey, err);
+      min_edge_window(s.x, d.x, n, rk, minkey, err, lo, span, check);
+      min_edge_window(s.y, d.y, n, rk, minkey, err, lo, span, check);
+      min_edge_window(s.z, d.z, n, rk, minkey, err, lo, span, check);
+      min_edge_window(s.w, d.w, n, rk, minkey, err, lo, span, check);
     }
     done = nq * 4;
   }
-  for (uint64_t j = done + gt; j < m; j += stride) min_edge(__ldcs(src + j), __ldcs(dst + j), n, rk, minkey, err);
+  for (uint64_t j = done + gt; j < m; j += stride)
+    min_edge_window(__ldcs(src + j), __ldcs(dst + j), n, rk, minkey, err, lo, span, check);
 }
 
 // Packed edges (a << 32 | b), two per 128-bit load.
@@ -135,23 +152,36 @@ __device__ __forceinline__ void relabel_one(uint32_t u, uint32_t v, bool valid, 
   keep = true;
 }
 
-// Each block handles tiles of kThreads * kRelItems edges; the block's keys are
-// compacted with a block scan and appended after one atomicAdd per tile.
+constexpr int kRelCache = 4096;  // per-block direct-mapped cache of emitted keys
+
+// Each block handles tiles of kThreads * kRelItems edges.  Every non-loop
+// edge is counted in *mprime; its key is written only if the block's cache
+// does not already hold it.  The cache slot of a key is overwritten by the
+// thread that writes the key, so a key is dropped only after this block has
+// written a copy of it: the written keys contain every distinct key.  Heavily
+// repeated keys (pairs of large trees) are thus written about once per block,
+// which keeps the dedup buckets small.  The written keys are compacted with a
+// block scan and appended after one atomicAdd per tile.
 template <bool kPacked>
 __global__ void __launch_bounds__(kThreads) k_relabel(
     const uint32_t* __restrict__ src, const uint32_t* __restrict__ dst,
     const uint64_t* __restrict__ packed, uint64_t m, uint32_t n, const uint32_t* __restrict__ root,
-    int bits, uint64_t* __restrict__ keys_out, unsigned long long* count, int vec) {
+    int bits, uint64_t* __restrict__ keys_out, unsigned long long* mprime,
+    unsigned long long* emitted) {
+  __shared__ uint64_t cache[kRelCache];
   __shared__ uint32_t ws[kThreads / 32];
+  __shared__ uint32_t wk[kThreads / 32];
   __shared__ unsigned long long s_base;
   const uint64_t tile_edges = (uint64_t)kThreads * kRelItems;
   const uint64_t ntiles = (m + tile_edges - 1) / tile_edges;
   const unsigned tid = threadIdx.x, lane = lane_id(), w = tid >> 5;
+  for (int i = tid; i < kRelCache; i += kThreads) cache[i] = ~0ull;
+  __syncthreads();
   for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
     // thread item i handles edge base + w*32*kRelItems + i*32 + lane (coalesced)
     const uint64_t base = t * tile_edges + (uint64_t)w * 32 * kRelItems;
     uint64_t key[kRelItems];
-    uint32_t keepmask = 0;
+    uint32_t keepmask = 0, emitmask = 0;
 #pragma unroll
     for (int i = 0; i < kRelItems; ++i) {
       uint64_t j = base + (uint64_t)i * 32 + lane;
@@ -172,31 +202,45 @@ __global__ void __launch_bounds__(kThreads) k_relabel(
       relabel_one(u, v, valid, n, root, bits, key[i], keep);
       keepmask |= (keep ? 1u : 0u) << i;
     }
-    (void)vec;
+#pragma unroll
+    for (int i = 0; i < kRelItems; ++i) {
+      if (keepmask & (1u << i)) {
+        uint32_t slot = (uint32_t)key_mix(key[i]) & (kRelCache - 1);
+        if (cache[slot] != key[i]) {
+          cache[slot] = key[i];
+          emitmask |= 1u << i;
+        }
+      }
+    }
     // warp-level compaction offsets, then one block scan over warp totals
-    uint32_t mine = __popc(keepmask);
+    uint32_t mine = __popc(emitmask);
     uint32_t incl = mine;
+    uint32_t kept = __popc(keepmask);
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       uint32_t y = __shfl_up_sync(kFull, incl, o);
       if (lane >= (unsigned)o) incl += y;
+      kept += __shfl_xor_sync(kFull, kept, o);
     }
     if (lane == 31) ws[w] = incl;
+    if (lane == 0) wk[w] = kept;
     __syncthreads();
     if (tid == 0) {
-      uint32_t run = 0;
+      uint32_t run = 0, kall = 0;
       for (int k = 0; k < kThreads / 32; ++k) {
         uint32_t c = ws[k];
         ws[k] = run;
         run += c;
+        kall += wk[k];
       }
-      s_base = run ? atomicAdd(count, (unsigned long long)run) : 0ull;
+      if (kall) atomicAdd(mprime, (unsigned long long)kall);
+      s_base = run ? atomicAdd(emitted, (unsigned long long)run) : 0ull;
     }
     __syncthreads();
     uint64_t pos = s_base + ws[w] + (incl - mine);
 #pragma unroll
     for (int i = 0; i < kRelItems; ++i)
-      if (keepmask & (1u << i)) keys_out[pos++] = key[i];
+      if (emitmask & (1u << i)) keys_out[pos++] = key[i];
     __syncthreads();
   }
 }
@@ -233,7 +277,7 @@ void init_keys(unsigned long long* minkey, uint32_t* mo, uint32_t n, uint64_t rk
 
 void edge_min(const uint32_t* src, const uint32_t* dst, const uint64_t* packed, uint64_t m,
               uint32_t n, uint64_t rk, unsigned long long* minkey, unsigned* err,
-              const Launch& L) {
+              uint64_t window_bytes, const Launch& L) {
   if (m == 0) return;
   if (packed != nullptr) {
     KScope ks(L, kKEdgeMinPacked);
@@ -241,9 +285,17 @@ void edge_min(const uint32_t* src, const uint32_t* dst, const uint64_t* packed, 
                                                                                    minkey);
   } else {
     int vec = ((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst)) & 15) == 0;
-    KScope ks(L, kKEdgeMinSoa);
-    k_edge_min_soa<<<grid_for((m + 3) / 4, kThreads, L), kThreads, 0, L.stream>>>(
-        src, dst, m, n, rk, minkey, err, vec);
+    // vertex windows whose minkey slices fit the L2 budget; one pass each
+    uint64_t wv = std::max<uint64_t>(1, window_bytes / 8);
+    uint32_t passes = (uint32_t)std::max<uint64_t>(1, (n + wv - 1) / wv);
+    uint64_t span = ((uint64_t)n + passes - 1) / passes;
+    for (uint32_t p = 0; p < passes; ++p) {
+      uint64_t lo = (uint64_t)p * span;
+      uint64_t sp = std::min<uint64_t>(span, n - lo);
+      KScope ks(L, kKEdgeMinSoa);
+      k_edge_min_soa<<<grid_for((m + 3) / 4, kThreads, L), kThreads, 0, L.stream>>>(
+          src, dst, m, n, rk, minkey, err, vec, (uint32_t)lo, (uint32_t)sp, p == 0);
+    }
   }
 }
 
@@ -255,17 +307,17 @@ void jump(unsigned long long* minkey, uint32_t* root, uint32_t* mo, uint32_t n, 
 
 void relabel(const uint32_t* src, const uint32_t* dst, const uint64_t* packed, uint64_t m,
              uint32_t n, const uint32_t* root, int bits, uint64_t* keys_out,
-             unsigned long long* count, const Launch& L) {
+             unsigned long long* mprime, unsigned long long* emitted, const Launch& L) {
   if (m == 0) return;
   int grid = grid_for(m, kThreads * kRelItems, L, 4);
   if (packed != nullptr) {
     KScope ks(L, kKRelabelPacked);
     k_relabel<true><<<grid, kThreads, 0, L.stream>>>(nullptr, nullptr, packed, m, n, root, bits,
-                                                     keys_out, count, 0);
+                                                     keys_out, mprime, emitted);
   } else {
     KScope ks(L, kKRelabelSoa);
     k_relabel<false><<<grid, kThreads, 0, L.stream>>>(src, dst, nullptr, m, n, root, bits,
-                                                      keys_out, count, 0);
+                                                      keys_out, mprime, emitted);
   }
 }
 

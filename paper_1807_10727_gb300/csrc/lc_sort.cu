@@ -299,9 +299,26 @@ __global__ void k_bucket_bounds(const uint64_t* __restrict__ keys,
 constexpr int kTableSlots = 4096;  // per-bucket shared-memory hash set (32 KB)
 constexpr uint64_t kEmpty = ~0ull;  // never a key: keys are (a << bits | b) with a < b
 
+__device__ __forceinline__ void set_insert(uint64_t* table, uint64_t key, int* over) {
+  uint32_t slot = (uint32_t)key_mix(key) & (kTableSlots - 1);
+  int probe = 0;
+  for (; probe < kTableSlots; ++probe) {
+    uint64_t cur = *(volatile uint64_t*)&table[slot];
+    if (cur == key) return;
+    if (cur == kEmpty) {
+      uint64_t prev = atomicCAS((unsigned long long*)&table[slot], kEmpty, key);
+      if (prev == kEmpty || prev == key) return;
+    }
+    slot = (slot + 1) & (kTableSlots - 1);
+  }
+  *over = 1;
+}
+
 // One bucket per iteration (claimed by ticket): insert its keys into a
-// shared-memory open-addressing set, then append the distinct keys to `out`
-// (one atomicAdd per bucket) and mark both endpoints of each in `flags`.
+// shared-memory open-addressing set (eight independent loads in flight per
+// thread), then append the distinct keys to `out` (one atomicAdd per bucket)
+// and mark both endpoints of each in `flags`.  Thread t owns table slots
+// t, t + 256, ... when collecting, so the scan is free of bank conflicts.
 __global__ void __launch_bounds__(kSortThreads) k_bucket_dedup(
     const uint64_t* __restrict__ keys, const uint32_t* __restrict__ bounds, uint32_t nb,
     uint64_t* __restrict__ out, unsigned long long* m_next, uint8_t* flags, int half_bits,
@@ -313,6 +330,7 @@ __global__ void __launch_bounds__(kSortThreads) k_bucket_dedup(
   __shared__ int s_over;
   const unsigned tid = threadIdx.x;
   constexpr int kPer = kTableSlots / kSortThreads;
+  constexpr int kIlp = 8;
   for (int i = tid; i < kTableSlots; i += kSortThreads) table[i] = kEmpty;
   if (tid == 0) s_over = 0;
   const uint64_t half_mask = (1ull << half_bits) - 1;
@@ -322,25 +340,21 @@ __global__ void __launch_bounds__(kSortThreads) k_bucket_dedup(
     const uint32_t b = s_b;
     if (b >= nb) break;
     const uint32_t lo = bounds[b], hi = bounds[b + 1];
-    for (uint32_t i = lo + tid; i < hi; i += kSortThreads) {
-      const uint64_t key = __ldcs(keys + i);
-      uint32_t slot = (uint32_t)key_mix(key) & (kTableSlots - 1);
-      int probe = 0;
-      for (; probe < kTableSlots; ++probe) {
-        uint64_t cur = *(volatile uint64_t*)&table[slot];
-        if (cur == key) break;
-        if (cur == kEmpty) {
-          uint64_t prev = atomicCAS((unsigned long long*)&table[slot], kEmpty, key);
-          if (prev == kEmpty || prev == key) break;
-        }
-        slot = (slot + 1) & (kTableSlots - 1);
+    for (uint32_t i0 = lo; i0 < hi; i0 += kSortThreads * kIlp) {
+      uint64_t kk[kIlp];
+#pragma unroll
+      for (int j = 0; j < kIlp; ++j) {
+        uint32_t i = i0 + j * kSortThreads + tid;
+        kk[j] = i < hi ? __ldcs(keys + i) : kEmpty;
       }
-      if (probe == kTableSlots) s_over = 1;
+#pragma unroll
+      for (int j = 0; j < kIlp; ++j)
+        if (kk[j] != kEmpty) set_insert(table, kk[j], &s_over);
     }
     __syncthreads();
     uint32_t cnt = 0;
 #pragma unroll
-    for (int s = 0; s < kPer; ++s) cnt += table[tid * kPer + s] != kEmpty;
+    for (int s = 0; s < kPer; ++s) cnt += table[s * kSortThreads + tid] != kEmpty;
     uint32_t total;
     uint32_t excl = block_exclusive_scan(cnt, ws, &total);
     if (tid == 0) {
@@ -354,12 +368,12 @@ __global__ void __launch_bounds__(kSortThreads) k_bucket_dedup(
     uint64_t pos = s_base + excl;
 #pragma unroll
     for (int s = 0; s < kPer; ++s) {
-      uint64_t v = table[tid * kPer + s];
+      uint64_t v = table[s * kSortThreads + tid];
       if (v != kEmpty) {
         out[pos++] = v;
         flags[v >> half_bits] = 1;
         flags[v & half_mask] = 1;
-        table[tid * kPer + s] = kEmpty;
+        table[s * kSortThreads + tid] = kEmpty;
       }
     }
     // the next iteration's barrier orders these clears before new inserts

@@ -23,7 +23,7 @@ LC_VARIANT_FOREST, LC_VARIANT_TWO_HOP, LC_VARIANT_TREE = 0, 1, 2
 
 # every symbol include/lc.h declares (checked by the CPU test suite)
 LC_DEDUP_HASH, LC_DEDUP_SORT = 0, 1
-EXPORTED = ("lc_create", "lc_configure", "lc_set_dedup", "lc_run", "lc_run_host", "lc_last_stats", "lc_profile",
+EXPORTED = ("lc_create", "lc_configure", "lc_set_dedup", "lc_set_param", "lc_run", "lc_run_host", "lc_last_stats", "lc_profile",
             "lc_kernel_stats", "lc_destroy", "lc_status_str", "lc_rank_probe")
 
 _lib = None
@@ -49,6 +49,7 @@ def load(path: str | None = None):
     lib.lc_create.argtypes = [u32, p, p, u64, u64, p, ctypes.POINTER(p)]
     lib.lc_configure.argtypes = [p, i32, u64]
     lib.lc_set_dedup.argtypes = [p, i32]
+    lib.lc_set_param.argtypes = [p, ctypes.c_char_p, u64]
     lib.lc_run.argtypes = [p, p, pu32, pu64, pu64, u32]
     lib.lc_run_host.argtypes = [p, p, p, p, pu32, pu64, pu64, u32]
     lib.lc_last_stats.argtypes = [p, pu32, pu64, u32]
@@ -106,6 +107,10 @@ def lc_configure(ctx: int, variant: int, finish_edges: int = 0) -> None:
 
 def lc_set_dedup(ctx: int, mode: int) -> None:
     _check(load().lc_set_dedup(ctx, mode), "lc_set_dedup")
+
+
+def lc_set_param(ctx: int, name: str, value: int) -> None:
+    _check(load().lc_set_param(ctx, name.encode(), value), "lc_set_param")
 
 
 def lc_run(ctx: int, d_labels: int, cap: int = 1024):
@@ -222,6 +227,9 @@ class LocalContraction:
 
     def mprime(self) -> list[int]:
         return lc_last_stats(self.ctx)
+
+    def set_param(self, name: str, value: int) -> None:
+        lc_set_param(self.ctx, name, value)
 
     def profile(self, on: bool) -> None:
         lc_profile(self.ctx, on)
