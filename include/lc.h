@@ -100,7 +100,11 @@ lc_status lc_set_dedup(lc_ctx* ctx, lc_dedup mode);
  *   "window_bytes"  L2 budget (bytes, >= 1 MiB) of one pass of the phase-0
  *                   closed-neighbourhood minimum: vertices are processed in
  *                   windows of window_bytes / 8 ids, one pass over the input
- *                   edges per window (default 128 MiB).
+ *                   edges per window (default 192 MiB).
+ *   "relabel_window_bytes"  when the phase-0 root array (4 bytes per vertex)
+ *                   is larger than this, phase 0 relabels the input edges in
+ *                   two passes, each gathering roots from one half of the
+ *                   array (default 160 MiB; needs n < 2^31).
  * Unknown names or out-of-range values give LC_ERR_INVALID. */
 lc_status lc_set_param(lc_ctx* ctx, const char* name, uint64_t value);
 

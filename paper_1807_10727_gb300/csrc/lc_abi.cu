@@ -14,11 +14,13 @@ using namespace lc;
 namespace lc {
 
 const char* kernel_name(int id) {
-  static const char* names[kNumKernels] = {
+  static const char* names[] = {
       "init_keys",   "edge_min_soa", "edge_min_packed", "jump",          "relabel_soa",
-      "relabel_packed", "sort_hist", "hist_scan",       "sort_pass",     "scan_flags",
+      "relabel_packed", "relabel_split", "sort_hist", "hist_scan",     "sort_pass",
+      "scan_flags",
       "unique_rename", "propagate",  "bucket_bounds",   "bucket_dedup",  "rename",
-      "identity",      "rank_probe"};
+      "unmix",         "identity",   "rank_probe"};
+  static_assert(sizeof(names) / sizeof(names[0]) == kNumKernels, "one name per kernel");
   return (id >= 0 && id < kNumKernels) ? names[id] : "unknown";
 }
 
@@ -163,7 +165,8 @@ struct lc_ctx {
   uint32_t* bounds = nullptr;  // bucket boundaries of the hashed dedup
   uint64_t fallbacks = 0;      // phases that needed the full-sort dedup
   bool dedup_sort = false;     // deduplicate by a full radix sort every phase
-  uint64_t window_bytes = 128ull << 20;  // L2 budget of one phase-0 minimum pass
+  uint64_t window_bytes = 192ull << 20;  // L2 budget of one phase-0 minimum pass
+  uint64_t relabel_window_bytes = 160ull << 20;  // root-array size above which relabel splits
 
   uint32_t last_rounds = 0;
   std::vector<uint64_t> last_mp;
@@ -213,7 +216,7 @@ static lc_status alloc_ctx(lc_ctx* c) {
   c->sort.status_words = std::max(sort_status_words(m), sort_status_words(n));
   LC_TRY(cudaMalloc(&c->sort.status, c->sort.status_words * 8));
   LC_TRY(cudaMemset(c->sort.status, 0, c->sort.status_words * 8));
-  LC_TRY(cudaMalloc(&c->sort.hist, sizeof(uint32_t) * kMaxPasses * kRadix));
+  LC_TRY(cudaMalloc(&c->sort.hist, sizeof(uint32_t) * kMaxPasses * kRadixMax));
   LC_TRY(cudaMalloc(&c->sort.tickets, sizeof(unsigned) * 16));
   LC_TRY(cudaMalloc(&c->bounds, sizeof(uint32_t) * ((1ull << hash_bits_for(m)) + 1)));
   // first arena chunk: 3 arrays per level for levels whose sizes sum to 2n,
@@ -323,13 +326,18 @@ static lc_status run_loop(lc_ctx* c, uint32_t* d_labels, uint32_t* rounds, uint6
     LC_TRY(cudaMemsetAsync(c->flags, 0, ni, c->stream));
     uint64_t* keys = (packed == c->ebuf[0]) ? c->ebuf[1] : c->ebuf[0];
     uint64_t* alt = (keys == c->ebuf[0]) ? c->ebuf[1] : c->ebuf[0];
+    PassPlan hplan{};
+    const int hb = hash_plan(mi, &hplan);
+    if (!c->dedup_sort) hist_reset(c->sort, L);
     relabel(i == 0 ? c->src : nullptr, i == 0 ? c->dst : nullptr, packed, mi, ni, lv.root, bits,
-            keys, &c->ctr->mprime, &c->ctr->emitted, L);
+            keys, &c->ctr->mprime, &c->ctr->emitted, !c->dedup_sort,
+            c->dedup_sort ? nullptr : &hplan, c->sort.hist, i == 0 ? alt : nullptr,
+            c->relabel_window_bytes, L);
     uint64_t* next = alt;
     bool by_sort = c->dedup_sort;
     if (!by_sort) {
-      int which = hash_dedup(keys, alt, &c->ctr->emitted, mi, bits, c->flags, c->bounds,
-                             &c->ctr->m_next, c->sort, err, L);
+      int which = hash_dedup(keys, alt, &c->ctr->emitted, mi, hplan, hb, true, bits, c->flags,
+                             c->bounds, &c->ctr->m_next, c->sort, err, L);
       uint64_t* part = which ? alt : keys;
       next = which ? keys : alt;
       scan_flags(c->flags, lv.scan, ni, lv.mo, mo_next, &c->ctr->n_next, c->sort, err, L);
@@ -348,6 +356,7 @@ static lc_status run_loop(lc_ctx* c, uint32_t* d_labels, uint32_t* rounds, uint6
         by_sort = true;
         keys = part;
         alt = next;
+        unmix_keys(keys, &c->ctr->emitted, mi, L);
         LC_TRY(cudaMemsetAsync(&c->ctr->m_next, 0, 2 * sizeof(unsigned long long), c->stream));
         LC_TRY(cudaMemsetAsync(&c->ctr->err, 0, sizeof(unsigned), c->stream));
         LC_TRY(cudaMemsetAsync(c->flags, 0, ni, c->stream));
@@ -454,6 +463,10 @@ extern "C" lc_status lc_set_param(lc_ctx* c, const char* name, uint64_t value) {
   if (std::strcmp(name, "window_bytes") == 0) {
     if (value < (1u << 20)) return LC_ERR_INVALID;
     c->window_bytes = value;
+    return LC_OK;
+  }
+  if (std::strcmp(name, "relabel_window_bytes") == 0) {
+    c->relabel_window_bytes = value;
     return LC_OK;
   }
   return LC_ERR_INVALID;

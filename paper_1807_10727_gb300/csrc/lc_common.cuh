@@ -34,21 +34,44 @@ enum : uint32_t {
   kErrOverflow = 4u,   // a dedup bucket held more distinct keys than its table
 };
 
-// Mixer of an edge key for bucketing and hash-set slots (xorshift-multiply
-// rounds; any well-mixing bijection serves, the result never reaches the
-// output).
-__device__ __forceinline__ uint64_t key_mix(uint64_t k) {
+// Bijective mixer of an edge key (xorshift-multiply rounds).  The hashed
+// dedup stores keys in mixed form: equal keys stay equal, the top bits pick
+// the bucket and the low bits the hash-set slot, and key_unmix restores the
+// key.  Any well-mixing bijection serves; the mixed form never reaches the
+// output.
+constexpr uint64_t kMixMul = 0xD6E8FEB86659FD93ull;
+constexpr uint64_t kMixMulInv = 0xCFEE444D8B59A89Bull;  // kMixMul^-1 mod 2^64
+static_assert(kMixMul * kMixMulInv == 1ull, "mix inverse");
+
+__host__ __device__ __forceinline__ constexpr uint64_t key_mix(uint64_t k) {
   k ^= k >> 32;
-  k *= 0xD6E8FEB86659FD93ull;
+  k *= kMixMul;
   k ^= k >> 32;
-  k *= 0xD6E8FEB86659FD93ull;
+  k *= kMixMul;
   k ^= k >> 32;
   return k;
 }
 
-// Bucket of a key: the top hb bits of its mix (0 when hb == 0).
-__device__ __forceinline__ uint64_t bucket_hash(uint64_t k, int hb) {
-  return hb ? key_mix(k) >> (64 - hb) : 0ull;
+// x ^= x >> 32 is its own inverse; the multiplications undo with kMixMulInv.
+__host__ __device__ __forceinline__ constexpr uint64_t key_unmix(uint64_t y) {
+  y ^= y >> 32;
+  y *= kMixMulInv;
+  y ^= y >> 32;
+  y *= kMixMulInv;
+  y ^= y >> 32;
+  return y;
+}
+
+// ~0 marks an empty hash-set slot.  It is never a mixed key: its preimage
+// has a high half above its low half (not a < b for 32-bit halves) and is
+// >= 2^62 (too wide for narrower halves).
+static_assert((key_unmix(~0ull) >> 32) > (key_unmix(~0ull) & 0xFFFFFFFFull) &&
+                  key_unmix(~0ull) >= (1ull << 62),
+              "empty-slot sentinel collides with a key");
+
+// Bucket of a mixed key: its top hb bits (0 when hb == 0).
+__device__ __forceinline__ uint64_t bucket_of(uint64_t y, int hb) {
+  return hb ? y >> (64 - hb) : 0ull;
 }
 
 // Iteration limit of every spin-wait on another block's status word.

@@ -17,6 +17,7 @@ enum KernelId : int {
   kKJump,
   kKRelabelSoa,
   kKRelabelPacked,
+  kKRelabelSplit,
   kKSortHist,
   kKHistScan,
   kKSortPass,
@@ -26,6 +27,7 @@ enum KernelId : int {
   kKBucketBounds,
   kKBucketDedup,
   kKRename,
+  kKUnmix,
   kKIdentity,
   kKRankProbe,
   kNumKernels
@@ -81,11 +83,36 @@ struct KScope {
 constexpr int kSortThreads = 256;
 constexpr int kSortItems = 16;
 constexpr int kSortTile = kSortThreads * kSortItems;  // 4096 keys per tile
-constexpr int kRadixBits = 8;
+constexpr int kRadixBits = 8;        // digit width of the full-key sort
 constexpr int kRadix = 1 << kRadixBits;
+constexpr int kRadixBitsMax = 8;     // widest digit of a hashed partition pass
+constexpr int kRadixMax = 1 << kRadixBitsMax;
+static_assert(kRadixMax % 256 == 0, "scan kernels assume whole digits per thread");
 constexpr int kMaxPasses = 8;
 constexpr int kBucketTarget = 2048;  // average keys per dedup bucket
 constexpr int kMaxHashBits = 24;
+
+// Digit of a key in one pass: bits [shift, shift + bits).
+struct DigitFn {
+  int shift;
+  uint32_t mask;
+  __device__ __forceinline__ uint32_t operator()(uint64_t k) const {
+    return (uint32_t)(k >> shift) & mask;
+  }
+};
+
+// The digits of an LSD sort or partition, least significant pass first.
+struct PassPlan {
+  int passes;
+  int shift[kMaxPasses];
+  int bits[kMaxPasses];
+  __host__ __device__ DigitFn digit_fn(int p) const {
+    return DigitFn{shift[p], (1u << bits[p]) - 1u};
+  }
+  __device__ __forceinline__ uint32_t digit(int p, uint64_t k) const {
+    return (uint32_t)(k >> shift[p]) & ((1u << bits[p]) - 1u);
+  }
+};
 
 // Scratch of the onesweep sort and the single-pass scans.  `status` holds one
 // 64-bit look-back word per (tile, digit); epochs make stale words invalid so
@@ -93,7 +120,7 @@ constexpr int kMaxHashBits = 24;
 struct SortScratch {
   uint64_t* status = nullptr;     // [status_words]
   uint64_t status_words = 0;
-  uint32_t* hist = nullptr;       // [kMaxPasses * kRadix] global digit counts / offsets
+  uint32_t* hist = nullptr;       // [kMaxPasses * kRadixMax] global digit counts / offsets
   unsigned* tickets = nullptr;    // [16] dynamic tile counters
   uint32_t epoch = 0;             // last epoch used (1..2^30-1)
 };
@@ -118,24 +145,39 @@ int radix_sort_u64(uint64_t* keys, uint64_t* alt, const unsigned long long* d_co
 // Bucket-hash bits used for max_count keys (0 when one bucket suffices).
 int hash_bits_for(uint64_t max_count);
 
-// Duplicate removal without a full sort: a stable LSD partition of
-// keys[0, *d_count) by an hb-bit hash of each key (hb = hash_bits_for(max_count),
-// at most 3 passes), so all copies of a key share one bucket of about
-// kBucketTarget keys; then one block per bucket keeps the distinct keys with a
-// shared-memory hash set, appends them (in no particular order) to the other
-// buffer, counts them in *m_next and marks both endpoints in flags.  Returns
+// Partition plan over the top hb = hash_bits_for(max_count) bits of the mixed
+// keys (digits of at most kRadixBitsMax bits, two passes up to 18 bits).
+// Returns hb.
+int hash_plan(uint64_t max_count, PassPlan* plan);
+
+// Zero the digit counts of s.hist (before a producer accumulates them).
+void hist_reset(SortScratch& s, const Launch& L);
+
+// Duplicate removal without a full sort, on mixed keys (key_mix of
+// a << half_bits | b): a stable LSD partition of keys[0, *d_count) by their
+// top hb bits following `plan` (from hash_plan; with hist_ready the digit
+// counts are already in s.hist), so all copies
+// of a key share one bucket of about kBucketTarget keys; then one block per
+// bucket keeps the distinct keys with a shared-memory hash set, appends them
+// (mixed, in no particular order) to the other buffer, counts them in *m_next
+// and marks both endpoints in flags.  Returns
 // which buffer holds the partitioned keys (0 = keys, 1 = alt); the distinct
 // keys are in the other one.  A bucket whose distinct keys overflow the set
 // raises kErrOverflow (the caller then falls back to radix_sort_u64).
 // `bounds` holds (1 << hb) + 1 words.
 int hash_dedup(uint64_t* keys, uint64_t* alt, const unsigned long long* d_count,
-               uint64_t max_count, int half_bits, uint8_t* flags, uint32_t* bounds,
-               unsigned long long* m_next, SortScratch& s, unsigned* err, const Launch& L);
+               uint64_t max_count, const PassPlan& plan, int hb, bool hist_ready,
+               int half_bits, uint8_t* flags, uint32_t* bounds, unsigned long long* m_next,
+               SortScratch& s, unsigned* err, const Launch& L);
 
-// e[j] = (newid[a] << 32 | newid[b]) for each key e[j] = (a << half_bits | b),
-// j < *d_count.
+// e[j] = (newid[a] << 32 | newid[b]) for each mixed key
+// e[j] = key_mix(a << half_bits | b), j < *d_count.
 void rename_edges(uint64_t* e, const unsigned long long* d_count, uint64_t max_count,
                   int half_bits, const uint32_t* newid, const Launch& L);
+
+// In place: e[j] = key_unmix(e[j]) for j < *d_count.
+void unmix_keys(uint64_t* e, const unsigned long long* d_count, uint64_t max_count,
+                const Launch& L);
 
 // In-place exclusive scan of flags[0, n) (values 0/1 as uint8) into
 // out[0, n] (uint32, out[n] = total); for every kept r (flag set) also copies
@@ -173,12 +215,19 @@ void edge_min(const uint32_t* src, const uint32_t* dst, const uint64_t* packed, 
 void jump(unsigned long long* minkey, uint32_t* root, uint32_t* mo, uint32_t n, const Launch& L);
 
 // Relabel every edge through root, drop self-loops, emit (min << bits | max)
-// keys compacted to keys_out.  *mprime gets the number of non-loop edges;
+// keys (mixed with key_mix when `mix`) compacted to keys_out.  With `plan`
+// non-null the digit counts of the written keys under that plan are added to
+// ghist (the partition histogram, so the dedup needs no extra read).  For
+// uint32 input with n * 4 > window_bytes (and n < 2^31) the relabel runs in
+// two passes, each gathering from one L2-sized half of root, with `tmp`
+// (8 bytes per edge) holding the half-resolved edges in between.  *mprime gets the number of non-loop edges;
 // *emitted the number of keys written, which omits repeats of a key that the
 // same block has already written (the written keys hold every distinct key).
 void relabel(const uint32_t* src, const uint32_t* dst, const uint64_t* packed, uint64_t m,
              uint32_t n, const uint32_t* root, int bits, uint64_t* keys_out,
-             unsigned long long* mprime, unsigned long long* emitted, const Launch& L);
+             unsigned long long* mprime, unsigned long long* emitted, bool mix,
+             const PassPlan* plan, uint32_t* ghist, uint64_t* tmp, uint64_t window_bytes,
+             const Launch& L);
 
 // labels_out[v] = kept(root[v]) ? labels_up[scan[root[v]]] : mo[root[v]], with
 // kept(r) = scan[r+1] > scan[r].  labels_out may alias root.

@@ -38,19 +38,11 @@ __global__ void k_rank_probe(uint64_t rk, uint32_t v0, uint32_t count, uint32_t*
 
 // ---------------------------------------------------- closed-N minimum
 
-__device__ __forceinline__ void min_edge(uint32_t u, uint32_t v, uint32_t n, uint64_t rk,
-                                         unsigned long long* minkey, unsigned* err) {
-  if (u >= n || v >= n) {
-    atomicOr(err, kErrBadVertex);
-    return;
-  }
-  if (u == v) return;  // v is in its own closed neighbourhood already
-  atomicMin(&minkey[u], (unsigned long long)phase_key(rk, v));
-  atomicMin(&minkey[v], (unsigned long long)phase_key(rk, u));
-}
-
-// Window form of min_edge: only endpoints in [lo, lo + span) are updated, so
-// the updates of one pass over the edges touch an L2-sized slice of minkey.
+// Window form of the edge update: keys are distinct, so of key(u) and key(v)
+// only the larger endpoint's minimum can drop, to the other endpoint's key;
+// the edge needs one atomic, applied when that endpoint lies in
+// [lo, lo + span) (so one pass over the edges touches an L2-sized slice of
+// minkey).
 __device__ __forceinline__ void min_edge_window(uint32_t u, uint32_t v, uint32_t n, uint64_t rk,
                                                 unsigned long long* minkey, unsigned* err,
                                                 uint32_t lo, uint32_t span, bool check) {
@@ -59,8 +51,9 @@ __device__ __forceinline__ void min_edge_window(uint32_t u, uint32_t v, uint32_t
     return;
   }
   if (u == v) return;
-  if (u - lo < span) atomicMin(&minkey[u], (unsigned long long)phase_key(rk, v));
-  if (v - lo < span) atomicMin(&minkey[v], (unsigned long long)phase_key(rk, u));
+  const uint64_t ku = phase_key(rk, u), kv = phase_key(rk, v);
+  const uint32_t hi = ku < kv ? v : u;
+  if (hi - lo < span) atomicMin(&minkey[hi], (unsigned long long)(ku < kv ? ku : kv));
 }
 
 // Input edges as two uint32 arrays; `vec` = both arrays 16-byte aligned.
@@ -89,6 +82,16 @@ __global__ void __launch_bounds__(kThreads) k_edge_min_soa(
     min_edge_window(__ldcs(src + j), __ldcs(dst + j), n, rk, minkey, err, lo, span, check);
 }
 
+// One atomic per edge, at the endpoint with the larger key (see
+// min_edge_window).
+__device__ __forceinline__ void min_edge_packed(uint64_t x, uint64_t rk,
+                                                unsigned long long* minkey) {
+  const uint32_t a = (uint32_t)(x >> 32), b = (uint32_t)x;
+  const uint64_t ka = phase_key(rk, a), kb = phase_key(rk, b);
+  if (ka < kb) atomicMin(&minkey[b], (unsigned long long)ka);
+  else atomicMin(&minkey[a], (unsigned long long)kb);
+}
+
 // Packed edges (a << 32 | b), two per 128-bit load.
 __global__ void __launch_bounds__(kThreads) k_edge_min_packed(
     const uint64_t* __restrict__ e, uint64_t m, uint64_t rk, unsigned long long* minkey) {
@@ -98,19 +101,10 @@ __global__ void __launch_bounds__(kThreads) k_edge_min_packed(
   const uint64_t gt = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   for (uint64_t q = gt; q < npair; q += stride) {
     ulonglong2 p = __ldcs(e2 + q);
-    uint32_t a0 = (uint32_t)(p.x >> 32), b0 = (uint32_t)p.x;
-    uint32_t a1 = (uint32_t)(p.y >> 32), b1 = (uint32_t)p.y;
-    atomicMin(&minkey[a0], (unsigned long long)phase_key(rk, b0));
-    atomicMin(&minkey[b0], (unsigned long long)phase_key(rk, a0));
-    atomicMin(&minkey[a1], (unsigned long long)phase_key(rk, b1));
-    atomicMin(&minkey[b1], (unsigned long long)phase_key(rk, a1));
+    min_edge_packed(p.x, rk, minkey);
+    min_edge_packed(p.y, rk, minkey);
   }
-  if ((m & 1) && gt == 0) {
-    uint64_t x = e[m - 1];
-    uint32_t a = (uint32_t)(x >> 32), b = (uint32_t)x;
-    atomicMin(&minkey[a], (unsigned long long)phase_key(rk, b));
-    atomicMin(&minkey[b], (unsigned long long)phase_key(rk, a));
-  }
+  if ((m & 1) && gt == 0) min_edge_packed(e[m - 1], rk, minkey);
 }
 
 // ------------------------------------------------------- pointer jumping
@@ -162,13 +156,40 @@ constexpr int kRelCache = 4096;  // per-block direct-mapped cache of emitted key
 // repeated keys (pairs of large trees) are thus written about once per block,
 // which keeps the dedup buckets small.  The written keys are compacted with a
 // block scan and appended after one atomicAdd per tile.
-template <bool kPacked>
+// Half-resolved endpoint: the root id with this bit set (ids < 2^31 only).
+constexpr uint32_t kResolved = 0x80000000u;
+
+// First half of a two-pass relabel of the input edges: every endpoint below
+// `split` is replaced by its root and flagged kResolved, the others are kept;
+// out[j] = (a << 32 | b).  Each pass gathers from one half of `root`, which
+// fits in L2.  Ids >= n become a flagged self-loop (dropped later).
+__global__ void __launch_bounds__(kThreads) k_relabel_first_half(
+    const uint32_t* __restrict__ src, const uint32_t* __restrict__ dst, uint64_t m, uint32_t n,
+    uint32_t split, const uint32_t* __restrict__ root, uint64_t* __restrict__ out) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += stride) {
+    uint32_t u = __ldcs(src + j), v = __ldcs(dst + j);
+    uint32_t a, b;
+    if (u >= n || v >= n) {
+      a = b = kResolved;
+    } else {
+      a = u < split ? (__ldg(root + u) | kResolved) : u;
+      b = v < split ? (__ldg(root + v) | kResolved) : v;
+    }
+    __stcs(out + j, ((uint64_t)a << 32) | b);
+  }
+}
+
+// kMode 0: uint32 src/dst; 1: packed (a << 32 | b); 2: packed half-resolved
+// (see k_relabel_first_half).
+template <int kMode>
 __global__ void __launch_bounds__(kThreads) k_relabel(
     const uint32_t* __restrict__ src, const uint32_t* __restrict__ dst,
     const uint64_t* __restrict__ packed, uint64_t m, uint32_t n, const uint32_t* __restrict__ root,
     int bits, uint64_t* __restrict__ keys_out, unsigned long long* mprime,
-    unsigned long long* emitted) {
+    unsigned long long* emitted, int mix, PassPlan plan, uint32_t* __restrict__ ghist) {
   __shared__ uint64_t cache[kRelCache];
+  __shared__ uint32_t hist[3][kRadixMax];
   __shared__ uint32_t ws[kThreads / 32];
   __shared__ uint32_t wk[kThreads / 32];
   __shared__ unsigned long long s_base;
@@ -176,6 +197,7 @@ __global__ void __launch_bounds__(kThreads) k_relabel(
   const uint64_t ntiles = (m + tile_edges - 1) / tile_edges;
   const unsigned tid = threadIdx.x, lane = lane_id(), w = tid >> 5;
   for (int i = tid; i < kRelCache; i += kThreads) cache[i] = ~0ull;
+  for (int i = tid; i < 3 * kRadixMax; i += kThreads) (&hist[0][0])[i] = 0;
   __syncthreads();
   for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
     // thread item i handles edge base + w*32*kRelItems + i*32 + lane (coalesced)
@@ -188,7 +210,7 @@ __global__ void __launch_bounds__(kThreads) k_relabel(
       bool valid = j < m;
       uint32_t u = 0, v = 0;
       if (valid) {
-        if (kPacked) {
+        if (kMode != 0) {
           uint64_t x = __ldcs(packed + j);
           u = (uint32_t)(x >> 32);
           v = (uint32_t)x;
@@ -199,16 +221,28 @@ __global__ void __launch_bounds__(kThreads) k_relabel(
       }
       bool keep;
       key[i] = 0;
-      relabel_one(u, v, valid, n, root, bits, key[i], keep);
+      if (kMode == 2) {
+        uint32_t a = (u & kResolved) ? (u & ~kResolved) : __ldg(root + u);
+        uint32_t b = (v & kResolved) ? (v & ~kResolved) : __ldg(root + v);
+        keep = valid && a != b;
+        if (keep) key[i] = ((uint64_t)min(a, b) << bits) | max(a, b);
+      } else {
+        relabel_one(u, v, valid, n, root, bits, key[i], keep);
+      }
       keepmask |= (keep ? 1u : 0u) << i;
     }
 #pragma unroll
     for (int i = 0; i < kRelItems; ++i) {
       if (keepmask & (1u << i)) {
-        uint32_t slot = (uint32_t)key_mix(key[i]) & (kRelCache - 1);
+        uint64_t y = key_mix(key[i]);
+        uint32_t slot = (uint32_t)y & (kRelCache - 1);
+        if (mix) key[i] = y;
         if (cache[slot] != key[i]) {
           cache[slot] = key[i];
           emitmask |= 1u << i;
+#pragma unroll
+          for (int p = 0; p < 3; ++p)
+            if (p < plan.passes) atomicAdd(&hist[p][plan.digit(p, key[i])], 1u);
         }
       }
     }
@@ -240,8 +274,12 @@ __global__ void __launch_bounds__(kThreads) k_relabel(
     uint64_t pos = s_base + ws[w] + (incl - mine);
 #pragma unroll
     for (int i = 0; i < kRelItems; ++i)
-      if (emitmask & (1u << i)) keys_out[pos++] = key[i];
+      if (emitmask & (1u << i)) __stcs(keys_out + pos++, key[i]);
     __syncthreads();
+  }
+  for (int i = tid; i < plan.passes * kRadixMax; i += kThreads) {
+    uint32_t c = (&hist[0][0])[i];
+    if (c) atomicAdd(&ghist[i], c);
   }
 }
 
@@ -307,17 +345,32 @@ void jump(unsigned long long* minkey, uint32_t* root, uint32_t* mo, uint32_t n, 
 
 void relabel(const uint32_t* src, const uint32_t* dst, const uint64_t* packed, uint64_t m,
              uint32_t n, const uint32_t* root, int bits, uint64_t* keys_out,
-             unsigned long long* mprime, unsigned long long* emitted, const Launch& L) {
+             unsigned long long* mprime, unsigned long long* emitted, bool mix,
+             const PassPlan* plan, uint32_t* ghist, uint64_t* tmp, uint64_t window_bytes,
+             const Launch& L) {
+  PassPlan pl{};
+  if (plan != nullptr) pl = *plan;  // passes == 0: no histogram
   if (m == 0) return;
   int grid = grid_for(m, kThreads * kRelItems, L, 4);
   if (packed != nullptr) {
     KScope ks(L, kKRelabelPacked);
-    k_relabel<true><<<grid, kThreads, 0, L.stream>>>(nullptr, nullptr, packed, m, n, root, bits,
-                                                     keys_out, mprime, emitted);
+    k_relabel<1><<<grid, kThreads, 0, L.stream>>>(nullptr, nullptr, packed, m, n, root, bits,
+                                                  keys_out, mprime, emitted, mix, pl, ghist);
+  } else if (tmp != nullptr && n < kResolved && (uint64_t)n * 4 > window_bytes) {
+    // two passes, each gathering from one half of root (see k_relabel_first_half)
+    const uint32_t split = n / 2;
+    {
+      KScope ks(L, kKRelabelSplit);
+      k_relabel_first_half<<<grid_for(m, kThreads, L), kThreads, 0, L.stream>>>(src, dst, m, n,
+                                                                               split, root, tmp);
+    }
+    KScope ks(L, kKRelabelSoa);
+    k_relabel<2><<<grid, kThreads, 0, L.stream>>>(nullptr, nullptr, tmp, m, n, root, bits,
+                                                  keys_out, mprime, emitted, mix, pl, ghist);
   } else {
     KScope ks(L, kKRelabelSoa);
-    k_relabel<false><<<grid, kThreads, 0, L.stream>>>(src, dst, nullptr, m, n, root, bits,
-                                                      keys_out, mprime, emitted);
+    k_relabel<0><<<grid, kThreads, 0, L.stream>>>(src, dst, nullptr, m, n, root, bits, keys_out,
+                                                  mprime, emitted, mix, pl, ghist);
   }
 }
 

@@ -88,73 +88,126 @@ __device__ __forceinline__ uint32_t look_back(uint64_t* status, uint32_t tile, u
 
 // ------------------------------------------------------------- histogram
 
-// Digit of a key in one pass: bits [shift, shift + bits) of the key itself
-// (plain sort) or of its hb-bit bucket hash (hash partition).
-struct DigitFn {
-  int shift;
-  uint32_t mask;
-  int hb;
-  __device__ __forceinline__ uint32_t operator()(uint64_t k) const {
-    uint64_t x = hb ? bucket_hash(k, hb) : k;
-    return (uint32_t)(x >> shift) & mask;
-  }
-};
-
-struct PassPlan {
-  int passes;
-  int hb;
-  int shift[kMaxPasses];
-  int bits[kMaxPasses];
-  __host__ __device__ DigitFn digit(int p) const {
-    return DigitFn{shift[p], (1u << bits[p]) - 1u, hb};
-  }
-};
-
 __global__ void __launch_bounds__(kSortThreads) k_sort_hist(const uint64_t* __restrict__ keys,
                                                             const unsigned long long* d_count,
                                                             PassPlan plan, uint32_t* ghist) {
-  __shared__ uint32_t h[kMaxPasses][kRadix];
-  for (int i = threadIdx.x; i < kMaxPasses * kRadix; i += blockDim.x) (&h[0][0])[i] = 0;
+  __shared__ uint32_t h[kMaxPasses][kRadixMax];
+  for (int i = threadIdx.x; i < kMaxPasses * kRadixMax; i += blockDim.x) (&h[0][0])[i] = 0;
   __syncthreads();
   const uint64_t count = *d_count;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride) {
-    uint64_t k = __ldcs(keys + i);
-    uint64_t x = plan.hb ? bucket_hash(k, plan.hb) : k;
+    uint64_t x = __ldcs(keys + i);
 #pragma unroll
     for (int p = 0; p < kMaxPasses; ++p)
-      if (p < plan.passes)
-        atomicAdd(&h[p][(uint32_t)(x >> plan.shift[p]) & ((1u << plan.bits[p]) - 1u)], 1u);
+      if (p < plan.passes) atomicAdd(&h[p][plan.digit(p, x)], 1u);
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < plan.passes * kRadix; i += blockDim.x) {
+  for (int i = threadIdx.x; i < plan.passes * kRadixMax; i += blockDim.x) {
     uint32_t c = (&h[0][0])[i];
     if (c) atomicAdd(&ghist[i], c);
   }
 }
 
-// In-place exclusive scan of each pass's kRadix counts (one block per pass).
-__global__ void __launch_bounds__(kRadix) k_hist_scan(uint32_t* ghist) {
+// In-place exclusive scan of each pass's kRadixMax counts (one block per pass,
+// kRadixMax / kSortThreads consecutive counts per thread).
+__global__ void __launch_bounds__(kSortThreads) k_hist_scan(uint32_t* ghist) {
+  constexpr int kPer = kRadixMax / kSortThreads;
   __shared__ uint32_t ws[kWarps];
-  uint32_t* h = ghist + blockIdx.x * kRadix;
-  uint32_t v = h[threadIdx.x], total;
-  uint32_t e = block_exclusive_scan(v, ws, &total);
-  h[threadIdx.x] = e;
+  uint32_t* h = ghist + blockIdx.x * kRadixMax + threadIdx.x * kPer;
+  uint32_t c[kPer], sum = 0;
+#pragma unroll
+  for (int q = 0; q < kPer; ++q) {
+    c[q] = h[q];
+    sum += c[q];
+  }
+  uint32_t total;
+  uint32_t e = block_exclusive_scan(sum, ws, &total);
+#pragma unroll
+  for (int q = 0; q < kPer; ++q) {
+    h[q] = e;
+    e += c[q];
+  }
 }
 
 // ------------------------------------------------------------ one pass
 
-// One stable counting pass over a 4096-key tile.  Lanes holding the same
-// digit are found by slicing the digit into bits and intersecting ballots
-// (one vote per digit bit), so ranking needs no match instruction; each warp
-// counts its digits in its own shared-memory row.
+// Digit-parallel look-back for the digits this thread owns: publish each
+// digit's tile count as an aggregate, walk back over the preceding tiles until
+// an inclusive prefix is found (all owned digits advance together, one load
+// each per step), publish the inclusive prefixes.  Returns false if a bounded
+// wait gave up.
+template <int kPer>
+__device__ __forceinline__ bool look_back_digits(uint64_t* status, uint32_t tile, int stride,
+                                                 const uint32_t* dig, const uint32_t* cnt,
+                                                 uint32_t* prefix, uint32_t epoch) {
+#pragma unroll
+  for (int q = 0; q < kPer; ++q) {
+    prefix[q] = 0;
+    store_status(status + (uint64_t)tile * stride + dig[q],
+                 pack_status(epoch, tile == 0 ? kFlagPrefix : kFlagAgg, cnt[q]));
+  }
+  if (tile == 0) return true;
+  uint32_t j[kPer];
+  bool done[kPer];
+#pragma unroll
+  for (int q = 0; q < kPer; ++q) {
+    j[q] = tile - 1;
+    done[q] = false;
+  }
+  bool ok = true;
+  uint32_t spins = 0;
+  for (;;) {
+    bool all = true;
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+      if (done[q]) continue;
+      uint64_t wd = load_status(status + (uint64_t)j[q] * stride + dig[q]);
+      if ((uint32_t)(wd >> 34) == epoch) {
+        uint32_t flag = (uint32_t)(wd >> 32) & 3u;
+        if (flag == kFlagPrefix) {
+          prefix[q] += (uint32_t)wd;
+          done[q] = true;
+          continue;
+        }
+        if (flag == kFlagAgg) {
+          prefix[q] += (uint32_t)wd;
+          --j[q];  // tile 0 always publishes a prefix, so j never wraps
+          spins = 0;
+        }
+      }
+      all = false;
+    }
+    if (all) break;
+    if (++spins > kSpinLimit) {
+      ok = false;
+      break;
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < kPer; ++q)
+    store_status(status + (uint64_t)tile * stride + dig[q],
+                 pack_status(epoch, kFlagPrefix, prefix[q] + cnt[q]));
+  return ok;
+}
+
+// One stable counting pass over a 4096-key tile with 2^kRB digit values.
+// Lanes holding the same digit are found by slicing the digit into bits and
+// intersecting ballots (one vote per digit bit), so ranking needs no match
+// instruction; each warp counts its digits in its own shared-memory row.
+// Thread t owns digits t*kPer .. t*kPer+kPer-1 for the tile totals,
+// look-back and scan.
+template <int kRB>
 __global__ void __launch_bounds__(kSortThreads, 3) k_sort_pass(
     const uint64_t* __restrict__ in, uint64_t* __restrict__ out, const unsigned long long* d_count,
     DigitFn dg, int bits, const uint32_t* __restrict__ digit_offset, uint64_t* status,
     uint32_t epoch, unsigned* ticket, unsigned* err, uint8_t* mark_flags, int half_bits) {
-  __shared__ uint64_t sk[kSortTile];
-  __shared__ uint32_t whist[kWarps][kRadix];
-  __shared__ uint32_t gofs[kRadix];
+  constexpr int kR = 1 << kRB;
+  constexpr int kPer = kR / kSortThreads;
+  extern __shared__ __align__(16) uint64_t sort_smem[];
+  uint64_t* sk = sort_smem;                                              // [kSortTile]
+  uint32_t(*whist)[kR] = reinterpret_cast<uint32_t(*)[kR]>(sk + kSortTile);  // [kWarps][kR]
+  uint32_t* gofs = reinterpret_cast<uint32_t*>(whist + kWarps);            // [kR]
   __shared__ uint32_t ws[kWarps];
   __shared__ uint32_t s_tile;
   __shared__ int s_bad;
@@ -164,7 +217,7 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_sort_pass(
     s_tile = atomicAdd(ticket, 1u);
     s_bad = 0;
   }
-  for (int i = tid; i < kWarps * kRadix; i += kSortThreads) (&whist[0][0])[i] = 0;
+  for (int i = tid; i < kWarps * kR; i += kSortThreads) (&whist[0][0])[i] = 0;
   __syncthreads();
   const uint32_t tile = s_tile;
   const uint64_t count = *d_count;
@@ -190,68 +243,51 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_sort_pass(
     const uint32_t d = dg(k[i]);
     unsigned peers = __ballot_sync(kFull, valid);
 #pragma unroll
-    for (int b = 0; b < kRadixBits; ++b) {
+    for (int b = 0; b < kRB; ++b) {
       if (b < bits) {
         unsigned v = __ballot_sync(kFull, (d >> b) & 1u);
         peers &= ((d >> b) & 1u) ? v : ~v;
       }
     }
     uint32_t r = __popc(peers & lt);
-    uint32_t cnt = valid ? whist[w][d] : 0u;
+    int leader = valid ? __ffs(peers) - 1 : (int)lane;
+    uint32_t cnt = (valid && r == 0) ? whist[w][d] : 0u;
+    cnt = __shfl_sync(kFull, cnt, leader);
     off[i] = cnt + r;
-    __syncwarp();
     if (valid && r == 0) whist[w][d] = cnt + __popc(peers);
     __syncwarp();
   }
   __syncthreads();
 
-  // per digit (one per thread): prefix over warps, tile count, look-back
-  const uint32_t d = tid;
-  uint32_t run = 0;
+  // per owned digit: prefix over warps, tile count, look-back
+  uint32_t dig[kPer], tcount[kPer], prefix[kPer];
+  uint32_t mine = 0;
 #pragma unroll
-  for (int ww = 0; ww < kWarps; ++ww) {
-    uint32_t t = whist[ww][d];
-    whist[ww][d] = run;
-    run += t;
-  }
-  const uint32_t tcount = run;
-  uint32_t prefix = 0;
-  {
-    uint64_t* st = status + (uint64_t)tile * kRadix + d;
-    if (tile == 0) {
-      store_status(st, pack_status(epoch, kFlagPrefix, tcount));
-    } else {
-      store_status(st, pack_status(epoch, kFlagAgg, tcount));
-      uint32_t j = tile - 1, spins = 0;
-      for (;;) {
-        uint64_t wd = load_status(status + (uint64_t)j * kRadix + d);
-        if ((uint32_t)(wd >> 34) == epoch) {
-          uint32_t flag = (uint32_t)(wd >> 32) & 3u;
-          if (flag == kFlagPrefix) {
-            prefix += (uint32_t)wd;
-            break;
-          }
-          if (flag == kFlagAgg) {
-            prefix += (uint32_t)wd;
-            --j;
-            spins = 0;
-            continue;
-          }
-        }
-        if (++spins > kSpinLimit) {
-          atomicOr(err, kErrTimeout);
-          s_bad = 1;
-          break;
-        }
-      }
-      store_status(st, pack_status(epoch, kFlagPrefix, prefix + tcount));
+  for (int q = 0; q < kPer; ++q) {
+    dig[q] = tid * kPer + q;
+    uint32_t run = 0;
+#pragma unroll
+    for (int ww = 0; ww < kWarps; ++ww) {
+      uint32_t t = whist[ww][dig[q]];
+      whist[ww][dig[q]] = run;
+      run += t;
     }
+    tcount[q] = run;
+    mine += run;
+  }
+  if (!look_back_digits<kPer>(status, tile, kR, dig, tcount, prefix, epoch)) {
+    atomicOr(err, kErrTimeout);
+    s_bad = 1;
   }
   uint32_t total;
-  const uint32_t tstart = block_exclusive_scan(tcount, ws, &total);
+  uint32_t tstart = block_exclusive_scan(mine, ws, &total);
 #pragma unroll
-  for (int ww = 0; ww < kWarps; ++ww) whist[ww][d] += tstart;
-  gofs[d] = digit_offset[d] + prefix - tstart;
+  for (int q = 0; q < kPer; ++q) {
+#pragma unroll
+    for (int ww = 0; ww < kWarps; ++ww) whist[ww][dig[q]] += tstart;
+    gofs[dig[q]] = digit_offset[dig[q]] + prefix[q] - tstart;
+    tstart += tcount[q];
+  }
   __syncthreads();
   if (s_bad) return;  // offsets unknown: write nothing (the host sees kErrTimeout)
 
@@ -268,7 +304,7 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_sort_pass(
   for (uint32_t j = tid; j < nvalid; j += kSortThreads) {
     uint64_t key = sk[j];
     uint64_t gpos = (uint64_t)gofs[dg(key)] + j;
-    if (gpos < count) out[gpos] = key;
+    if (gpos < count) __stcs(out + gpos, key);
     if (mark_flags != nullptr && (j == 0 || sk[j - 1] != key)) {
       mark_flags[key >> half_bits] = 1;
       mark_flags[key & half_mask] = 1;
@@ -278,8 +314,8 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_sort_pass(
 
 // --------------------------------------------- hashed buckets and dedup
 
-// bounds[b] = first position whose bucket hash is >= b, for b in [0, nb];
-// the keys are partitioned in ascending order of their bucket hash.
+// bounds[b] = first position whose bucket is >= b, for b in [0, nb]; the
+// mixed keys are partitioned in ascending order of their bucket (top hb bits).
 __global__ void k_bucket_bounds(const uint64_t* __restrict__ keys,
                                 const unsigned long long* d_count, int hb, uint32_t nb,
                                 uint32_t* __restrict__ bounds) {
@@ -289,18 +325,18 @@ __global__ void k_bucket_bounds(const uint64_t* __restrict__ keys,
     uint64_t lo = 0, hi = count;
     while (lo < hi) {
       uint64_t mid = (lo + hi) >> 1;
-      if (bucket_hash(keys[mid], hb) < b) lo = mid + 1;
+      if (bucket_of(keys[mid], hb) < b) lo = mid + 1;
       else hi = mid;
     }
     bounds[b] = (uint32_t)lo;
   }
 }
 
-constexpr int kTableSlots = 4096;  // per-bucket shared-memory hash set (32 KB)
-constexpr uint64_t kEmpty = ~0ull;  // never a key: keys are (a << bits | b) with a < b
+constexpr int kTableSlots = 2 * kBucketTarget;  // per-bucket shared-memory hash set (32 KB)
+constexpr uint64_t kEmpty = ~0ull;  // never a mixed key (static_assert in lc_common.cuh)
 
 __device__ __forceinline__ void set_insert(uint64_t* table, uint64_t key, int* over) {
-  uint32_t slot = (uint32_t)key_mix(key) & (kTableSlots - 1);
+  uint32_t slot = (uint32_t)key & (kTableSlots - 1);  // low bits of the mixed key
   int probe = 0;
   for (; probe < kTableSlots; ++probe) {
     uint64_t cur = *(volatile uint64_t*)&table[slot];
@@ -323,7 +359,7 @@ __global__ void __launch_bounds__(kSortThreads) k_bucket_dedup(
     const uint64_t* __restrict__ keys, const uint32_t* __restrict__ bounds, uint32_t nb,
     uint64_t* __restrict__ out, unsigned long long* m_next, uint8_t* flags, int half_bits,
     unsigned* ticket, unsigned* err) {
-  __shared__ uint64_t table[kTableSlots];
+  extern __shared__ __align__(16) uint64_t table[];  // [kTableSlots]
   __shared__ uint32_t ws[kWarps];
   __shared__ uint32_t s_b;
   __shared__ unsigned long long s_base;
@@ -371,8 +407,9 @@ __global__ void __launch_bounds__(kSortThreads) k_bucket_dedup(
       uint64_t v = table[s * kSortThreads + tid];
       if (v != kEmpty) {
         out[pos++] = v;
-        flags[v >> half_bits] = 1;
-        flags[v & half_mask] = 1;
+        uint64_t k = key_unmix(v);
+        flags[k >> half_bits] = 1;
+        flags[k & half_mask] = 1;
         table[s * kSortThreads + tid] = kEmpty;
       }
     }
@@ -380,16 +417,24 @@ __global__ void __launch_bounds__(kSortThreads) k_bucket_dedup(
   }
 }
 
-// e[j] = (newid[a] << 32 | newid[b]) for e[j] = (a << half_bits | b).
+// e[j] = (newid[a] << 32 | newid[b]) for e[j] = key_mix(a << half_bits | b).
 __global__ void k_rename(uint64_t* __restrict__ e, const unsigned long long* d_count,
                          int half_bits, const uint32_t* __restrict__ newid) {
   const uint64_t count = *d_count;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   const uint64_t half_mask = (1ull << half_bits) - 1;
   for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < count; j += stride) {
-    uint64_t k = e[j];
+    uint64_t k = key_unmix(e[j]);
     e[j] = ((uint64_t)newid[k >> half_bits] << 32) | newid[k & half_mask];
   }
+}
+
+// In place: e[j] = key_unmix(e[j]) (before the full-sort fallback).
+__global__ void k_unmix(uint64_t* __restrict__ e, const unsigned long long* d_count) {
+  const uint64_t count = *d_count;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < count; j += stride)
+    e[j] = key_unmix(e[j]);
 }
 
 // ------------------------------------------------------------- scans
@@ -512,7 +557,7 @@ __global__ void __launch_bounds__(kSortThreads) k_unique_rename(
 
 uint64_t sort_status_words(uint64_t max_keys) {
   uint64_t tiles = (max_keys + kSortTile - 1) / kSortTile;
-  uint64_t w = tiles * kRadix;
+  uint64_t w = tiles * kRadixMax;
   return std::max<uint64_t>(w, 1024);
 }
 
@@ -524,21 +569,43 @@ uint32_t next_epoch(SortScratch& s, const Launch& L) {
   return ++s.epoch;
 }
 
+static size_t sort_pass_smem(int rb) {
+  return (size_t)kSortTile * 8 + (size_t)kWarps * (1u << rb) * 4 + (size_t)(1u << rb) * 4;
+}
+
+static size_t dedup_smem() { return (size_t)kTableSlots * 8; }
+
+// Opt in to more than 48 KB of dynamic shared memory (a cheap host call,
+// repeated before each use so every device the library runs on sees it).
+static void set_smem_limits() {
+  cudaFuncSetAttribute(k_sort_pass<kRadixBitsMax>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)sort_pass_smem(kRadixBitsMax));
+  cudaFuncSetAttribute(k_bucket_dedup, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)dedup_smem());
+}
+
+void hist_reset(SortScratch& s, const Launch& L) {
+  cudaMemsetAsync(s.hist, 0, sizeof(uint32_t) * kMaxPasses * kRadixMax, L.stream);
+}
+
+// hist_ready: s.hist already holds the plan's digit counts (accumulated by the
+// producer of the keys); otherwise a histogram pass reads the keys first.
 static int run_passes(uint64_t* keys, uint64_t* alt, const unsigned long long* d_count,
-                      uint64_t max_count, const PassPlan& plan, SortScratch& s, unsigned* err,
-                      uint8_t* mark_flags, int half_bits, const Launch& L) {
+                      uint64_t max_count, const PassPlan& plan, bool hist_ready, SortScratch& s,
+                      unsigned* err, uint8_t* mark_flags, int half_bits, const Launch& L) {
   if (max_count == 0 || plan.passes == 0) return 0;
-  cudaMemsetAsync(s.hist, 0, sizeof(uint32_t) * kMaxPasses * kRadix, L.stream);
+  set_smem_limits();
   cudaMemsetAsync(s.tickets, 0, sizeof(unsigned) * 8, L.stream);
   uint64_t tiles = (max_count + kSortTile - 1) / kSortTile;
-  int hgrid = (int)std::min<uint64_t>(tiles, (uint64_t)L.sms * 4);
-  {
+  if (!hist_ready) {
+    hist_reset(s, L);
+    int hgrid = (int)std::min<uint64_t>(tiles, (uint64_t)L.sms * 4);
     KScope ks(L, kKSortHist);
     k_sort_hist<<<hgrid, kSortThreads, 0, L.stream>>>(keys, d_count, plan, s.hist);
   }
   {
     KScope ks(L, kKHistScan);
-    k_hist_scan<<<plan.passes, kRadix, 0, L.stream>>>(s.hist);
+    k_hist_scan<<<plan.passes, kSortThreads, 0, L.stream>>>(s.hist);
   }
   uint64_t* src = keys;
   uint64_t* dst = alt;
@@ -546,9 +613,10 @@ static int run_passes(uint64_t* keys, uint64_t* alt, const unsigned long long* d
     uint32_t epoch = next_epoch(s, L);
     bool last = p == plan.passes - 1;
     KScope ks(L, kKSortPass);
-    k_sort_pass<<<(unsigned)tiles, kSortThreads, 0, L.stream>>>(
-        src, dst, d_count, plan.digit(p), plan.bits[p], s.hist + p * kRadix, s.status, epoch,
-        s.tickets + p, err, last ? mark_flags : nullptr, half_bits);
+    k_sort_pass<kRadixBitsMax><<<(unsigned)tiles, kSortThreads, sort_pass_smem(kRadixBitsMax),
+                                 L.stream>>>(
+        src, dst, d_count, plan.digit_fn(p), plan.bits[p], s.hist + p * kRadixMax, s.status,
+        epoch, s.tickets + p, err, last ? mark_flags : nullptr, half_bits);
     std::swap(src, dst);
   }
   return plan.passes & 1;
@@ -558,13 +626,12 @@ int radix_sort_u64(uint64_t* keys, uint64_t* alt, const unsigned long long* d_co
                    uint64_t max_count, int key_bits, SortScratch& s, unsigned* err,
                    uint8_t* mark_flags, int half_bits, const Launch& L) {
   PassPlan plan{};
-  plan.hb = 0;
   plan.passes = (std::max(key_bits, 1) + kRadixBits - 1) / kRadixBits;
   for (int p = 0; p < plan.passes; ++p) {
     plan.shift[p] = kRadixBits * p;
     plan.bits[p] = kRadixBits;
   }
-  return run_passes(keys, alt, d_count, max_count, plan, s, err, mark_flags, half_bits, L);
+  return run_passes(keys, alt, d_count, max_count, plan, false, s, err, mark_flags, half_bits, L);
 }
 
 int hash_bits_for(uint64_t max_count) {
@@ -573,22 +640,27 @@ int hash_bits_for(uint64_t max_count) {
   return b;
 }
 
-int hash_dedup(uint64_t* keys, uint64_t* alt, const unsigned long long* d_count,
-               uint64_t max_count, int half_bits, uint8_t* flags, uint32_t* bounds,
-               unsigned long long* m_next, SortScratch& s, unsigned* err, const Launch& L) {
-  if (max_count == 0) return 0;
+int hash_plan(uint64_t max_count, PassPlan* plan) {
   const int hb = hash_bits_for(max_count);
-  PassPlan plan{};
-  plan.hb = hb;
-  plan.passes = (hb + kRadixBits - 1) / kRadixBits;
-  int shift = 0;
-  for (int p = 0; p < plan.passes; ++p) {
-    int w = hb / plan.passes + (p < hb % plan.passes ? 1 : 0);
-    plan.shift[p] = shift;
-    plan.bits[p] = w;
+  *plan = PassPlan{};
+  plan->passes = (hb + kRadixBitsMax - 1) / kRadixBitsMax;
+  int shift = 64 - hb;  // the bucket is the top hb bits of the mixed key
+  for (int p = 0; p < plan->passes; ++p) {
+    int w = hb / plan->passes + (p < hb % plan->passes ? 1 : 0);
+    plan->shift[p] = shift;
+    plan->bits[p] = w;
     shift += w;
   }
-  int which = run_passes(keys, alt, d_count, max_count, plan, s, err, nullptr, half_bits, L);
+  return hb;
+}
+
+int hash_dedup(uint64_t* keys, uint64_t* alt, const unsigned long long* d_count,
+               uint64_t max_count, const PassPlan& plan, int hb, bool hist_ready,
+               int half_bits, uint8_t* flags, uint32_t* bounds, unsigned long long* m_next,
+               SortScratch& s, unsigned* err, const Launch& L) {
+  if (max_count == 0) return 0;
+  int which =
+      run_passes(keys, alt, d_count, max_count, plan, hist_ready, s, err, nullptr, half_bits, L);
   uint64_t* part = which ? alt : keys;
   uint64_t* out = which ? keys : alt;
   const uint32_t nb = 1u << hb;
@@ -600,11 +672,21 @@ int hash_dedup(uint64_t* keys, uint64_t* alt, const unsigned long long* d_count,
   cudaMemsetAsync(s.tickets + 10, 0, sizeof(unsigned), L.stream);
   {
     KScope ks(L, kKBucketDedup);
+    set_smem_limits();
     int g = (int)std::min<uint64_t>(nb, (uint64_t)L.sms * 6);
-    k_bucket_dedup<<<g, kSortThreads, 0, L.stream>>>(part, bounds, nb, out, m_next, flags,
-                                                     half_bits, s.tickets + 10, err);
+    k_bucket_dedup<<<g, kSortThreads, dedup_smem(), L.stream>>>(part, bounds, nb, out, m_next,
+                                                                flags, half_bits, s.tickets + 10,
+                                                                err);
   }
   return which;  // keys partitioned in `part` (0: keys, 1: alt); distinct keys in the other
+}
+
+void unmix_keys(uint64_t* e, const unsigned long long* d_count, uint64_t max_count,
+                const Launch& L) {
+  if (max_count == 0) return;
+  KScope ks(L, kKUnmix);
+  int g = (int)std::min<uint64_t>((max_count + 255) / 256, (uint64_t)L.sms * 8);
+  k_unmix<<<g, 256, 0, L.stream>>>(e, d_count);
 }
 
 void rename_edges(uint64_t* e, const unsigned long long* d_count, uint64_t max_count,
