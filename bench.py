@@ -37,6 +37,9 @@ if REPO not in sys.path:
     sys.path.insert(0, REPO)
 
 METRIC = "input edges/sec to final labels (1 GB300), HBM roofline %"
+# DRAM bytes / algorithmic bytes per launch from the committed ncu capture
+# (profiles/traffic_rmat23.md); valid while the kernel is unchanged.
+TRAFFIC_RATIO = {"sort_pass": 1.007, "relabel_soa": 0.98, "bucket_dedup": 0.93}
 UNIT = "edges/s"
 CPU_SAMPLE_EDGES = 1 << 24
 
@@ -51,11 +54,14 @@ def peaks():
         return 6800.0, "fallback"
 
 
-# Algorithmic bytes of one launch of each kernel, from the phase sizes
-# (n_i vertices, m_i edges, mp_i keys after relabel, m_{i+1} unique edges).
-# Random-gather sector amplification and the repeated sort passes beyond one
-# read+write of the keys are not algorithmic and are not counted.
-def algorithmic_bytes(n_i, m_i, mp_i, passes_i):
+# Algorithmic bytes of each kernel over one run, from the phase sizes (n_i
+# vertices, m_i edges, mp_i non-loop keys after relabel, em_i keys the relabel
+# wrote, m_{i+1} distinct edges): one read of every input a launch must
+# consume and one write of every output it must produce.  Random-gather
+# sector amplification is not algorithmic and is not counted; a phase-0
+# minimum window pass or a relabel half-pass reads all edges, so each such
+# launch counts that read.
+def algorithmic_bytes(n_i, m_i, mp_i, em_i, window_passes, relabel_split):
     per = {}
 
     def add(k, b):
@@ -63,20 +69,35 @@ def algorithmic_bytes(n_i, m_i, mp_i, passes_i):
 
     R = len(n_i)
     for i in range(R):
-        n, m, mp = n_i[i], m_i[i], mp_i[i]
+        n, m, em = n_i[i], m_i[i], em_i[i]
         m_next = m_i[i + 1] if i + 1 < R else 0
-        edge_bytes = 8 * m
         add("init_keys", 8 * n + (4 * n if i == 0 else 0))
-        add("edge_min_soa" if i == 0 else "edge_min_packed", edge_bytes + 8 * n)
+        if i == 0:
+            add("edge_min_soa", window_passes * 8 * m + 8 * n)
+            if relabel_split:
+                add("relabel_split", 8 * m + 8 * m + 4 * n)
+                add("relabel_soa", 8 * m + 8 * em + 4 * n)
+            else:
+                add("relabel_soa", 8 * m + 8 * em + 4 * n)
+        else:
+            add("edge_min_packed", 8 * m + 8 * n)
+            add("relabel_packed", 8 * m + 8 * em + 4 * n)
         add("jump", 8 * n + 4 * n + 4 * n)
-        add("relabel_soa" if i == 0 else "relabel_packed", edge_bytes + 4 * n + 8 * mp)
-        if mp:
-            add("sort_hist", 8 * mp)
-            add("sort_pass", 16 * mp * passes_i[i])
-            add("unique_rename", 8 * mp + 8 * m_next)
-        add("scan_flags", n + 4 * n + 4 * n)
-        add("propagate", 4 * n + 4 * n)
+        add("sort_pass", 16 * em * hash_passes(m))
+        add("bucket_dedup", 8 * em + 8 * m_next + 2 * n)
+        add("rename", 16 * m_next + 4 * n)
+        add("scan_flags", n + 4 * n + 8 * (m_next and n))
+        add("propagate", 4 * n + 4 * n + 4 * n)
     return per
+
+
+def hash_passes(m):
+    """Partition passes of the hashed dedup for m edges (digits <= 8 bits over
+    the bucket bits, 2048 keys per bucket)."""
+    hb = 0
+    while hb < 24 and (2048 << hb) < m:
+        hb += 1
+    return (hb + 7) // 8
 
 
 def path_bytes(n_i, m_i, mp_i):
@@ -92,13 +113,6 @@ def path_bytes(n_i, m_i, mp_i):
         total += n * (8 + 4 + 8 + 4 + 4)
     total += sum(8 * n for n in n_i) + 8 * (n_i[0] if n_i else 0)
     return total
-
-
-def sort_passes(n):
-    bits = 1
-    while bits < 32 and (1 << bits) < n:
-        bits += 1
-    return (2 * bits + 7) // 8
 
 
 class ClockSampler:
@@ -254,7 +268,7 @@ def main():
 
     for _ in range(max(3, args.warmup)):
         _, res = ctx.run(labels)
-    mp = ctx.mprime()
+    mp, em = lc.lc_last_stats(ctx.ctx)
 
     clocks = ClockSampler(gpu_id_for(local))
     ctx.profile(not args.no_profile)
@@ -282,16 +296,21 @@ def main():
 
     # dominant kernel and its roofline
     peak, peak_kind = peaks()
-    passes = [sort_passes(n) for n in res.n_i]
-    alg = algorithmic_bytes(res.n_i, res.m_i, mp, passes)
+    wpass = max(1, -(-8 * g.n // (192 << 20)))
+    split = g.n < (1 << 31) and 4 * g.n > (160 << 20)
+    alg = algorithmic_bytes(res.n_i, res.m_i, mp, em, wpass, split)
     top = max(kstats.items(), key=lambda kv: kv[1][1])
     top_name, (top_launches, top_ms) = top
     roof = None
     if top_ms > 0:
         achieved = alg.get(top_name, 0) * args.steps / (top_ms / 1e3) / 1e9
+        per_launch = alg.get(top_name, 0) * args.steps / max(1, top_launches)
+        ratio = TRAFFIC_RATIO.get(top_name)
         roof = {"bound": "hbm", "kernel": top_name, "achieved": achieved, "peak": peak,
                 "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind,
-                "traffic": None, "launches_per_step": top_launches / args.steps,
+                "traffic": ratio * per_launch if ratio else None,
+                "algorithmic_bytes_per_launch": per_launch,
+                "launches_per_step": top_launches / args.steps,
                 "share_of_step": top_ms / args.steps / ms}
     pb = path_bytes(res.n_i, res.m_i, mp)
     path_roof = {"bytes_per_step": pb, "achieved": pb / (ms / 1e3) / 1e9, "peak": peak,
@@ -341,7 +360,8 @@ def main():
             "roofline": roof, "path_roofline": path_roof,
             "e2e": e2e, "cpu_baseline": cpu, "gpu_launches": launches,
             "clocks": clk, "kernels": kernels,
-            "sizes": [[int(a), int(b), int(c)] for a, b, c in zip(res.n_i, res.m_i, mp)],
+            "sizes": [[int(a), int(b), int(c), int(d)]
+                      for a, b, c, d in zip(res.n_i, res.m_i, mp, em)],
         }
         print(json.dumps(line))
     if world > 1:

@@ -131,8 +131,11 @@ lc_status lc_run_host(lc_ctx* ctx, const uint32_t* h_src, const uint32_t* h_dst,
 
 /* Diagnostics of the last successful run, host uint64[cap] each (NULL to skip):
  * mp_i = edges of phase i left after relabelling and loop removal, before
- * deduplication.  Returns the phase count in *rounds. */
-lc_status lc_last_stats(const lc_ctx* ctx, uint32_t* rounds, uint64_t* mp_i, uint32_t cap);
+ * deduplication (m'_i); emitted_i = how many of those the relabel step wrote
+ * out (it skips repeats of a key it has just written, so the deduplication
+ * reads fewer keys; emitted_i <= mp_i).  Returns the phase count in *rounds. */
+lc_status lc_last_stats(const lc_ctx* ctx, uint32_t* rounds, uint64_t* mp_i, uint64_t* emitted_i,
+                        uint32_t cap);
 
 /* Per-kernel instrumentation (no counterpart in the paper; used to measure
  * the kernels against the HBM roofline).  Launch counts of every kernel are

@@ -170,6 +170,7 @@ struct lc_ctx {
 
   uint32_t last_rounds = 0;
   std::vector<uint64_t> last_mp;
+  std::vector<uint64_t> last_emitted;
 };
 
 #define LC_TRY(call)                                  \
@@ -284,6 +285,7 @@ static lc_status run_loop(lc_ctx* c, uint32_t* d_labels, uint32_t* rounds, uint6
   const Launch& L = c->L;
   c->last_rounds = 0;
   c->last_mp.clear();
+  c->last_emitted.clear();
   if (rounds) *rounds = 0;
   if (c->n == 0) return LC_OK;
   if (c->m == 0) {
@@ -383,6 +385,7 @@ static lc_status run_loop(lc_ctx* c, uint32_t* d_labels, uint32_t* rounds, uint6
     hn.push_back(ni);
     hm.push_back(mi);
     c->last_mp.push_back(c->h_ctr->mprime);
+    c->last_emitted.push_back(c->h_ctr->emitted);
     c->levels.push_back(lv);
     ni = (uint32_t)c->h_ctr->n_next;
     mi = c->h_ctr->m_next;
@@ -442,12 +445,13 @@ extern "C" lc_status lc_run_host(lc_ctx* c, const uint32_t* h_src, const uint32_
 }
 
 extern "C" lc_status lc_last_stats(const lc_ctx* c, uint32_t* rounds, uint64_t* mp_i,
-                                   uint32_t cap) {
+                                   uint64_t* emitted_i, uint32_t cap) {
   if (!c) return LC_ERR_INVALID;
   if (rounds) *rounds = c->last_rounds;
-  if (mp_i)
-    for (uint32_t i = 0; i < std::min<uint32_t>(cap, (uint32_t)c->last_mp.size()); ++i)
-      mp_i[i] = c->last_mp[i];
+  for (uint32_t i = 0; i < std::min<uint32_t>(cap, (uint32_t)c->last_mp.size()); ++i) {
+    if (mp_i) mp_i[i] = c->last_mp[i];
+    if (emitted_i) emitted_i[i] = c->last_emitted[i];
+  }
   return LC_OK;
 }
 

@@ -52,7 +52,7 @@ def load(path: str | None = None):
     lib.lc_set_param.argtypes = [p, ctypes.c_char_p, u64]
     lib.lc_run.argtypes = [p, p, pu32, pu64, pu64, u32]
     lib.lc_run_host.argtypes = [p, p, p, p, pu32, pu64, pu64, u32]
-    lib.lc_last_stats.argtypes = [p, pu32, pu64, u32]
+    lib.lc_last_stats.argtypes = [p, pu32, pu64, pu64, u32]
     lib.lc_profile.argtypes = [p, i32]
     lib.lc_kernel_stats.argtypes = [p, u32, ctypes.POINTER(ctypes.c_char_p), pu64,
                                     ctypes.POINTER(ctypes.c_double)]
@@ -133,11 +133,14 @@ def lc_run_host(ctx: int, h_src: np.ndarray, h_dst: np.ndarray, h_labels: np.nda
     return r, list(n_i[:r]), list(m_i[:r])
 
 
-def lc_last_stats(ctx: int, cap: int = 1024) -> list[int]:
+def lc_last_stats(ctx: int, cap: int = 1024) -> tuple[list[int], list[int]]:
+    """(m'_i, emitted_i) of the last run."""
     R = ctypes.c_uint32(0)
     mp = (ctypes.c_uint64 * cap)()
-    _check(load().lc_last_stats(ctx, ctypes.byref(R), mp, cap), "lc_last_stats")
-    return list(mp[:min(R.value, cap)])
+    em = (ctypes.c_uint64 * cap)()
+    _check(load().lc_last_stats(ctx, ctypes.byref(R), mp, em, cap), "lc_last_stats")
+    r = min(R.value, cap)
+    return list(mp[:r]), list(em[:r])
 
 
 def lc_profile(ctx: int, on: bool) -> None:
@@ -226,7 +229,10 @@ class LocalContraction:
         return h_labels, Result(r, n_i, m_i)
 
     def mprime(self) -> list[int]:
-        return lc_last_stats(self.ctx)
+        return lc_last_stats(self.ctx)[0]
+
+    def emitted(self) -> list[int]:
+        return lc_last_stats(self.ctx)[1]
 
     def set_param(self, name: str, value: int) -> None:
         lc_set_param(self.ctx, name, value)
