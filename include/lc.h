@@ -155,6 +155,39 @@ lc_status lc_kernel_stats(const lc_ctx* ctx, uint32_t k, const char** name, uint
  * synchronisation of the context's stream).  NULL is accepted. */
 lc_status lc_destroy(lc_ctx* ctx);
 
+/* Allocation-free connected components for small graphs.  (The paper has no
+ * counterpart; this entry point serves callers that must not allocate device
+ * memory: code running under another framework's allocator that already holds
+ * the device memory, plug-ins or callbacks that may not touch the allocator,
+ * and latency-critical loops that avoid cudaMalloc because it can synchronise
+ * the device.)
+ *
+ * Same computation, outputs and errors as lc_create + lc_run + lc_destroy
+ * with the default settings, for n <= LC_STATIC_MAX_N vertices and
+ * m <= LC_STATIC_MAX_M edges.  Inputs (d_src, d_dst: device uint32[m]) and
+ * outputs (d_labels: device uint32[n]; rounds, n_i, m_i: host, as in lc_run)
+ * are the caller's.  All scratch lives in one static device array of
+ * LC_STATIC_SCRATCH_BYTES bytes inside this library, which every GPU that loads
+ * the library holds until the process exits; the call performs no device or
+ * pinned-host allocation (cudaMalloc, cudaFree, cudaMallocHost or any
+ * allocating library routine).
+ *   - Larger n or m: LC_ERR_INVALID, before any device work.
+ *   - The first call on a device looks up the array's device address with that
+ *     device current (once per device); make that first call before any
+ *     stream capture.
+ *   - Every call on a device shares the array, which keeps the last call's
+ *     contents (each call clears what it needs zeroed).  Calls whose GPU work
+ *     overlaps (other streams, other host threads) race on it and give
+ *     undefined results: serialise them.
+ *   - Phase sequences that shrink very slowly can exceed the static per-phase
+ *     storage (16 words per vertex): LC_ERR_OOM, labels not written. */
+#define LC_STATIC_MAX_N 131072u
+#define LC_STATIC_MAX_M 524288u
+#define LC_STATIC_SCRATCH_BYTES (20u << 20)
+lc_status lc_run_static(uint32_t n, const uint32_t* d_src, const uint32_t* d_dst, uint64_t m,
+                        uint64_t seed, void* stream, uint32_t* d_labels, uint32_t* rounds,
+                        uint64_t* n_i, uint64_t* m_i, uint32_t cap);
+
 /* Static text for a status code. */
 const char* lc_status_str(lc_status s);
 

@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -78,6 +79,7 @@ struct Arena {
   std::vector<std::pair<uint32_t*, uint64_t>> chunks;  // (base, words)
   size_t cur = 0;
   uint64_t used = 0;
+  bool fixed = false;  // never grow: running out is an allocation failure
   cudaError_t init(uint64_t words) {
     uint32_t* p = nullptr;
     cudaError_t e = cudaMalloc(&p, std::max<uint64_t>(words, 1024) * 4);
@@ -96,6 +98,10 @@ struct Arena {
       }
       ++cur;
       used = 0;
+    }
+    if (fixed) {
+      *err = cudaErrorMemoryAllocation;
+      return nullptr;
     }
     uint64_t sz = std::max<uint64_t>(words, chunks.empty() ? words : chunks.back().second);
     uint32_t* p = nullptr;
@@ -525,4 +531,107 @@ extern "C" lc_status lc_rank_probe(uint64_t seed, uint32_t i, uint32_t v0, uint3
   rank_probe(phase_seed(seed, i), v0, count, d_out, L);
   LC_TRY(cudaGetLastError());
   return LC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free entry point.
+//
+// Some callers cannot call cudaMalloc: code running under another
+// framework's caching allocator that already holds the device memory, plug-ins
+// and callbacks that must not touch the allocator, and latency-critical loops
+// that avoid cudaMalloc because it can synchronise the device.  lc_run_static
+// runs the same phase loop as lc_run for small graphs with every scratch
+// buffer carved out of one file-scope device array.  Every GPU that loads
+// the library holds that array until the process exits.
+
+static __device__ __align__(256) unsigned char g_static_scratch[LC_STATIC_SCRATCH_BYTES];
+
+namespace {
+
+// Layout of the static array (byte offsets, 256-byte aligned pieces).
+constexpr uint64_t align256(uint64_t x) { return (x + 255) & ~255ull; }
+constexpr uint64_t kSN = LC_STATIC_MAX_N, kSM = LC_STATIC_MAX_M;
+constexpr uint64_t kOffMinkey = 0;
+constexpr uint64_t kOffFlags = align256(kOffMinkey + 8 * kSN);
+constexpr uint64_t kOffEbuf0 = align256(kOffFlags + kSN + 16);
+constexpr uint64_t kOffEbuf1 = align256(kOffEbuf0 + 8 * kSM);
+constexpr uint64_t kOffCtr = align256(kOffEbuf1 + 8 * kSM);
+constexpr uint64_t kStatusWords = (kSM + kSortTile - 1) / kSortTile * kRadixMax + 1024;
+constexpr uint64_t kOffStatus = align256(kOffCtr + sizeof(Counters));
+constexpr uint64_t kOffHist = align256(kOffStatus + 8 * kStatusWords);
+constexpr uint64_t kOffTickets = align256(kOffHist + 4ull * kMaxPasses * kRadixMax);
+constexpr uint64_t kBoundsWords = (1ull << 8) + 1;  // hash_bits_for(LC_STATIC_MAX_M) == 8
+constexpr uint64_t kOffBounds = align256(kOffTickets + 4 * 16);
+constexpr uint64_t kOffArena = align256(kOffBounds + 4 * kBoundsWords);
+constexpr uint64_t kArenaWords = (LC_STATIC_SCRATCH_BYTES - kOffArena) / 4;
+static_assert(kOffArena < LC_STATIC_SCRATCH_BYTES, "static scratch too small");
+static_assert(kArenaWords >= 16 * kSN, "static level arena below 16 words per vertex");
+
+constexpr int kMaxStaticDevices = 64;
+unsigned char* g_static_base[kMaxStaticDevices];  // device address, per device
+std::mutex g_static_mu;
+
+// Device address of the static array for the current device.  In host code
+// the array's name is only a host-side stand-in, so the address is looked
+// up once per device with that device current.
+lc_status static_scratch(int dev, unsigned char** out) {
+  if (dev < 0 || dev >= kMaxStaticDevices) return LC_ERR_INVALID;
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  if (g_static_base[dev] == nullptr) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess) return status_of(e);
+    g_static_base[dev] = static_cast<unsigned char*>(p);
+  }
+  *out = g_static_base[dev];
+  return LC_OK;
+}
+
+}  // namespace
+
+extern "C" lc_status lc_run_static(uint32_t n, const uint32_t* d_src, const uint32_t* d_dst,
+                                   uint64_t m, uint64_t seed, void* stream, uint32_t* d_labels,
+                                   uint32_t* rounds, uint64_t* n_i, uint64_t* m_i, uint32_t cap) {
+  if (n > LC_STATIC_MAX_N || m > LC_STATIC_MAX_M) return LC_ERR_INVALID;  // too large
+  if ((1ull << hash_bits_for(m)) + 1 > kBoundsWords) return LC_ERR_INVALID;
+  if (n == 0 && m > 0) return LC_ERR_INVALID;
+  if (m > 0 && (d_src == nullptr || d_dst == nullptr)) return LC_ERR_INVALID;
+  if (n > 0 && d_labels == nullptr) return LC_ERR_INVALID;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return LC_ERR_CUDA;
+  unsigned char* base = nullptr;
+  lc_status st = static_scratch(dev, &base);
+  if (st != LC_OK) return st;
+  lc_ctx c;  // host-side bookkeeping only; every device buffer points into base
+  c.n = n;
+  c.m = m;
+  c.seed = seed;
+  c.stream = (cudaStream_t)stream;
+  c.device = dev;
+  if (cudaDeviceGetAttribute(&c.L.sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return LC_ERR_CUDA;
+  c.L.stream = c.stream;
+  c.L.prof = &c.prof;
+  c.src = d_src;
+  c.dst = d_dst;
+  c.minkey = reinterpret_cast<unsigned long long*>(base + kOffMinkey);
+  c.flags = base + kOffFlags;
+  c.ebuf[0] = reinterpret_cast<uint64_t*>(base + kOffEbuf0);
+  c.ebuf[1] = reinterpret_cast<uint64_t*>(base + kOffEbuf1);
+  c.ctr = reinterpret_cast<Counters*>(base + kOffCtr);
+  Counters host_ctr;
+  c.h_ctr = &host_ctr;
+  c.sort.status = reinterpret_cast<uint64_t*>(base + kOffStatus);
+  c.sort.status_words = kStatusWords;
+  c.sort.hist = reinterpret_cast<uint32_t*>(base + kOffHist);
+  c.sort.tickets = reinterpret_cast<unsigned*>(base + kOffTickets);
+  c.sort.epoch = 0;  // the array keeps the last call's words: clear them on first use
+  c.bounds = reinterpret_cast<uint32_t*>(base + kOffBounds);
+  c.arena.chunks.push_back({reinterpret_cast<uint32_t*>(base + kOffArena), kArenaWords});
+  c.arena.fixed = true;
+  // the run clears the counters, status words, histograms, tickets and
+  // flags it reads before reading them
+  st = run_loop(&c, d_labels, rounds, n_i, m_i, cap);
+  c.arena.chunks.clear();  // nothing to free: all of it is the static array
+  return st;
 }

@@ -23,8 +23,10 @@ LC_VARIANT_FOREST, LC_VARIANT_TWO_HOP, LC_VARIANT_TREE = 0, 1, 2
 
 # every symbol include/lc.h declares (checked by the CPU test suite)
 LC_DEDUP_HASH, LC_DEDUP_SORT = 0, 1
-EXPORTED = ("lc_create", "lc_configure", "lc_set_dedup", "lc_set_param", "lc_run", "lc_run_host", "lc_last_stats", "lc_profile",
-            "lc_kernel_stats", "lc_destroy", "lc_status_str", "lc_rank_probe")
+EXPORTED = ("lc_create", "lc_configure", "lc_set_dedup", "lc_set_param", "lc_run", "lc_run_host",
+            "lc_last_stats", "lc_profile", "lc_kernel_stats", "lc_destroy", "lc_status_str",
+            "lc_rank_probe", "lc_run_static")
+LC_STATIC_MAX_N, LC_STATIC_MAX_M = 131072, 524288
 
 _lib = None
 
@@ -60,6 +62,7 @@ def load(path: str | None = None):
     lib.lc_status_str.argtypes = [i32]
     lib.lc_status_str.restype = ctypes.c_char_p
     lib.lc_rank_probe.argtypes = [u64, u32, u32, u32, p, p]
+    lib.lc_run_static.argtypes = [u32, p, p, u64, u64, p, p, pu32, pu64, pu64, u32]
     for name in EXPORTED:
         if name != "lc_status_str":
             getattr(lib, name).restype = i32
@@ -166,6 +169,19 @@ def lc_kernel_stats(ctx: int) -> dict:
 def lc_destroy(ctx: int) -> None:
     if ctx:
         _check(load().lc_destroy(ctx), "lc_destroy")
+
+
+def lc_run_static(n: int, d_src: int, d_dst: int, m: int, seed: int, stream: int,
+                  d_labels: int, cap: int = 1024):
+    """Allocation-free run for n <= LC_STATIC_MAX_N, m <= LC_STATIC_MAX_M (all
+    scratch in the library's static device array; see include/lc.h)."""
+    R = ctypes.c_uint32(0)
+    n_i = (ctypes.c_uint64 * cap)()
+    m_i = (ctypes.c_uint64 * cap)()
+    _check(load().lc_run_static(n, d_src, d_dst, m, seed, stream, d_labels, ctypes.byref(R), n_i,
+                                m_i, cap), "lc_run_static")
+    r = R.value
+    return r, list(n_i[:r]), list(m_i[:r])
 
 
 def lc_rank_probe(seed: int, i: int, v0: int, count: int, d_out: int, stream: int) -> None:
