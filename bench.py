@@ -189,6 +189,58 @@ def cpu_baseline(g, sample_edges=CPU_SAMPLE_EDGES):
                       % (k, g.m, g.n, dt)}
 
 
+def bench_batch(dev, stream, steps=5, k=4096):
+    """Config 4: 4096 independent graphs (n log-uniform in [2^6, 2^16]; half ER
+    with average degree 4, half R-MAT with average degree 16), one batched
+    context vs one lc_run per graph on the same GPU (contexts created up front
+    in both cases; creation is not timed)."""
+    import torch
+
+    from paper_1807_10727_gb300 import lc, synth
+    b = synth.batch(k=k)
+    src = torch.from_numpy(b.src.view(np.int32)).to(dev)
+    dst = torch.from_numpy(b.dst.view(np.int32)).to(dev)
+    total = int(b.n.astype(np.int64).sum())
+    labels = torch.empty(total, dtype=torch.int32, device=dev)
+    bl = lc.BatchLocalContraction(b.n, b.eoff, src, dst, b.seeds, stream=stream)
+    for _ in range(2):
+        bl.run(labels)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        _, rounds, _, _ = bl.run(labels)
+    torch.cuda.synchronize(dev)
+    batched_s = (time.perf_counter() - t0) / steps
+    bl.close()
+    # one context and one lc_run per graph
+    voff = np.concatenate([[0], np.cumsum(b.n.astype(np.int64))])
+    ctxs = []
+    for g in range(k):
+        lo, hi = int(b.eoff[g]), int(b.eoff[g + 1])
+        ctxs.append(lc.LocalContraction(int(b.n[g]), src[lo:hi], dst[lo:hi], seed=int(b.seeds[g]),
+                                        stream=stream))
+    for g in range(min(k, 64)):
+        ctxs[g].run(labels[voff[g]:voff[g + 1]])
+    torch.cuda.synchronize(dev)
+    lat = np.empty(k)
+    t0 = time.perf_counter()
+    for g in range(k):
+        t1 = time.perf_counter()
+        ctxs[g].run(labels[voff[g]:voff[g + 1]])
+        lat[g] = time.perf_counter() - t1
+    serial_s = time.perf_counter() - t0
+    for c in ctxs:
+        c.close()
+    return {"workload": "4096 graphs, n log-uniform [2^6, 2^16], ER deg 4 / R-MAT deg 16",
+            "graphs": k, "vertices": total, "edges": int(b.eoff[-1]),
+            "max_rounds": int(rounds.max()),
+            "batched_graphs_per_s": k / batched_s, "batched_ms": batched_s * 1e3,
+            "per_graph_graphs_per_s": k / serial_s, "per_graph_ms_total": serial_s * 1e3,
+            "per_graph_latency_ms_p50": float(np.percentile(lat, 50) * 1e3),
+            "per_graph_latency_ms_p99": float(np.percentile(lat, 99) * 1e3),
+            "speedup": serial_s / batched_s}
+
+
 def dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -236,6 +288,7 @@ def main():
     ap.add_argument("--workload", default="rmat26")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched (config 4) leg")
     ap.add_argument("--no-profile", action="store_true",
                     help="skip the per-kernel event timing (roofline) of the timed steps")
     args = ap.parse_args()
@@ -347,6 +400,10 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(g)
+    batched = None
+    if rank == 0 and not args.no_batch:
+        torch.cuda.empty_cache()
+        batched = bench_batch(dev, stream)
 
     if rank == 0:
         line = {
@@ -358,7 +415,7 @@ def main():
                        "rounds": res.rounds, "parallelism": "replicas" if world > 1 else "single",
                        "l2": "inputs (8 B/edge) larger than L2; no flush"},
             "roofline": roof, "path_roofline": path_roof,
-            "e2e": e2e, "cpu_baseline": cpu, "gpu_launches": launches,
+            "e2e": e2e, "cpu_baseline": cpu, "gpu_launches": launches, "batched": batched,
             "clocks": clk, "kernels": kernels,
             "sizes": [[int(a), int(b), int(c), int(d)]
                       for a, b, c, d in zip(res.n_i, res.m_i, mp, em)],

@@ -129,6 +129,32 @@ lc_status lc_run_host(lc_ctx* ctx, const uint32_t* h_src, const uint32_t* h_dst,
                       uint32_t* h_labels, uint32_t* rounds, uint64_t* n_i, uint64_t* m_i,
                       uint32_t cap);
 
+/* Batched form: k independent graphs in one context, run together (each
+ * phase's kernels cover every graph still holding edges), with results equal
+ * to k separate lc_create/lc_run calls.
+ *   h_n      host uint32[k]: vertices of graph g (local ids 0..h_n[g]-1).
+ *   h_eoff   host uint64[k+1]: graph g's edges are d_src/d_dst[h_eoff[g],
+ *            h_eoff[g+1]); h_eoff[0] = 0, non-decreasing.
+ *   d_src, d_dst  device uint32[h_eoff[k]], local ids, caller-owned, read-only.
+ *   h_seeds  host uint64[k]: rank seed of graph g (as lc_create's seed).
+ * sum(h_n) and h_eoff[k] must be <= 2^32 - 1.  Local ids are validated during
+ * lc_batch_run (LC_ERR_INVALID).  Destroy with lc_destroy. */
+lc_status lc_batch_create(uint32_t k, const uint32_t* h_n, const uint64_t* h_eoff,
+                          const uint32_t* d_src, const uint32_t* d_dst, const uint64_t* h_seeds,
+                          void* stream, lc_ctx** out);
+
+/* Run a batch context.
+ *   d_labels  device uint32[sum h_n]: graph g's labels at offset
+ *             sum_{h<g} h_n[h], local (smallest local id of the component).
+ *   rounds    host uint32[k]: phases of graph g.
+ *   n_i, m_i  host uint64[k * cap], graph-major: n_i[g * cap + i] is the
+ *             vertex count of graph g's phase i, for i < min(rounds[g], cap).
+ *   cap       phases stored per graph; a graph with more gives LC_ERR_INVALID
+ *             after everything else has been filled.
+ * Any of rounds / n_i / m_i may be NULL. */
+lc_status lc_batch_run(lc_ctx* ctx, uint32_t* d_labels, uint32_t* rounds, uint64_t* n_i,
+                       uint64_t* m_i, uint32_t cap);
+
 /* Diagnostics of the last successful run, host uint64[cap] each (NULL to skip):
  * mp_i = edges of phase i left after relabelling and loop removal, before
  * deduplication (m'_i); emitted_i = how many of those the relabel step wrote

@@ -20,7 +20,7 @@ const char* kernel_name(int id) {
       "relabel_packed", "relabel_split", "sort_hist", "hist_scan",     "sort_pass",
       "scan_flags",
       "unique_rename", "propagate",  "bucket_bounds",   "bucket_dedup",  "rename",
-      "unmix",         "identity",   "rank_probe"};
+      "unmix",         "batch",      "identity",        "rank_probe"};
   static_assert(sizeof(names) / sizeof(names[0]) == kNumKernels, "one name per kernel");
   return (id >= 0 && id < kNumKernels) ? names[id] : "unknown";
 }
@@ -142,6 +142,37 @@ struct DeviceGuard {
 
 }  // namespace
 
+// Progress of one run of the phase loop (see run_begin / run_complete).
+struct RunState {
+  enum State { kDone = 0, kPhase, kSortPhase, kLabels } state = kDone;
+  lc_status st = LC_OK;
+  uint32_t* d_labels = nullptr;
+  uint32_t i = 0, ni = 0;
+  uint64_t mi = 0;
+  const uint64_t* packed = nullptr;  // current edges when not the input
+  uint32_t* mo_cur = nullptr;
+  Level lv{};
+  uint32_t* mo_next = nullptr;
+  int bits = 1;
+  uint64_t *keys = nullptr, *alt = nullptr, *part = nullptr, *next = nullptr;
+  std::vector<uint64_t> hn, hm;
+};
+
+// A batch of independent graphs run as one (see BatchKeys in lc_round.cu).
+struct BatchState {
+  uint32_t k = 0;
+  uint64_t* d_seeds = nullptr;  // [k] rank seeds
+  uint32_t* d_voff0 = nullptr;  // [k+1] vertex offsets of the input
+  uint64_t* d_eoff = nullptr;   // [k+1] edge offsets of the input
+  uint64_t* d_rk = nullptr;     // [k] phase seeds of the current phase
+  const uint32_t* user_src = nullptr;  // caller's edges, local ids
+  const uint32_t* user_dst = nullptr;
+  std::vector<uint64_t> h_eoff;
+  std::vector<uint32_t> h_voff0;
+  std::vector<uint32_t*> voff;  // per level: [k+1] offsets (level 0: d_voff0)
+  std::vector<uint32_t*> mcnt;  // per level i >= 1: [k] edges per graph
+};
+
 struct lc_ctx {
   uint32_t n = 0;
   uint64_t m = 0;
@@ -177,6 +208,10 @@ struct lc_ctx {
   uint32_t last_rounds = 0;
   std::vector<uint64_t> last_mp;
   std::vector<uint64_t> last_emitted;
+
+  cudaEvent_t ev = nullptr;  // completion of the work enqueued last (none: sync the stream)
+  RunState rs;
+  BatchState* batch = nullptr;
 };
 
 #define LC_TRY(call)                                  \
@@ -202,6 +237,14 @@ static void free_ctx(lc_ctx* c) {
   cudaFree(c->ebuf[1]);
   cudaFree(c->ctr);
   if (c->h_ctr) cudaFreeHost(c->h_ctr);
+  if (c->ev) cudaEventDestroy(c->ev);
+  if (c->batch) {
+    cudaFree(c->batch->d_seeds);
+    cudaFree(c->batch->d_voff0);
+    cudaFree(c->batch->d_eoff);
+    cudaFree(c->batch->d_rk);
+    delete c->batch;
+  }
   cudaFree(c->sort.status);
   cudaFree(c->sort.hist);
   cudaFree(c->sort.tickets);
@@ -220,6 +263,7 @@ static lc_status alloc_ctx(lc_ctx* c) {
   LC_TRY(cudaMalloc(&c->ctr, sizeof(Counters)));
   LC_TRY(cudaMemset(c->ctr, 0, sizeof(Counters)));
   LC_TRY(cudaMallocHost(&c->h_ctr, sizeof(Counters)));
+  LC_TRY(cudaEventCreateWithFlags(&c->ev, cudaEventDisableTiming));
   c->sort.status_words = std::max(sort_status_words(m), sort_status_words(n));
   LC_TRY(cudaMalloc(&c->sort.status, c->sort.status_words * 8));
   LC_TRY(cudaMemset(c->sort.status, 0, c->sort.status_words * 8));
@@ -286,136 +330,238 @@ extern "C" lc_status lc_configure(lc_ctx* c, lc_variant variant, uint64_t finish
 
 static uint32_t round_cap(uint32_t n) { return 64 + 4 * (uint32_t)bits_for(std::max(n, 2u)); }
 
-static lc_status run_loop(lc_ctx* c, uint32_t* d_labels, uint32_t* rounds, uint64_t* n_i,
-                          uint64_t* m_i, uint32_t cap) {
+// ---------------------------------------------------------------------------
+// The phase loop as a state machine, so that one host thread can drive many
+// contexts: run_begin enqueues phase 0, and each time the work enqueued last
+// has completed (run_wait, or an event query), run_complete reads the phase's
+// counters and enqueues the next phase, the dedup fallback, or the final label
+// composition.
+
+static lc_status record(lc_ctx* c) {
+  LC_TRY(cudaGetLastError());
+  if (c->ev) LC_TRY(cudaEventRecord(c->ev, c->stream));
+  return LC_OK;
+}
+
+static lc_status enqueue_sort_dedup(lc_ctx* c);
+
+static lc_status fail(lc_ctx* c, lc_status st) {
+  c->rs.st = st;
+  c->rs.state = RunState::kDone;
+  return st;
+}
+
+// Enqueue phase rs.i on (rs.ni, rs.mi): steps (a)-(d) and the copy of the
+// phase counters to the host.
+static lc_status enqueue_phase(lc_ctx* c) {
+  RunState& r = c->rs;
   const Launch& L = c->L;
-  c->last_rounds = 0;
-  c->last_mp.clear();
-  c->last_emitted.clear();
-  if (rounds) *rounds = 0;
-  if (c->n == 0) return LC_OK;
-  if (c->m == 0) {
-    identity_labels(d_labels, c->n, L);
-    LC_TRY(cudaGetLastError());
-    LC_TRY(cudaStreamSynchronize(c->stream));
-    c->prof.resolve();
-    return LC_OK;
-  }
-  c->arena.reset();
-  c->levels.clear();
-  LC_TRY(cudaMemsetAsync(c->ctr, 0, sizeof(Counters), c->stream));
   cudaError_t aerr = cudaSuccess;
-  uint32_t ni = c->n;
-  uint64_t mi = c->m;
-  const uint64_t* packed = nullptr;  // current edges when not the input
-  uint32_t* mo_cur = c->arena.alloc(ni, &aerr);
-  LC_TRY(aerr);
-  std::vector<uint64_t> hn, hm;
-  const uint32_t cap_rounds = round_cap(c->n);
+  const uint32_t i = r.i, ni = r.ni;
+  const uint64_t mi = r.mi;
+  r.lv = Level{ni, c->arena.alloc(ni, &aerr), r.mo_cur, nullptr};
+  if (aerr != cudaSuccess) return fail(c, status_of(aerr));
+  r.lv.scan = c->arena.alloc((uint64_t)ni + 1, &aerr);
+  if (aerr != cudaSuccess) return fail(c, status_of(aerr));
+  r.mo_next = c->arena.alloc(ni, &aerr);
+  if (aerr != cudaSuccess) return fail(c, status_of(aerr));
+  const uint64_t rk = phase_seed(c->seed, i);
+  r.bits = bits_for(ni);
   unsigned* err = &c->ctr->err;
-  for (uint32_t i = 0; mi > 0; ++i) {
-    if (i >= cap_rounds) return LC_ERR_NO_CONVERGENCE;
-    Level lv{ni, c->arena.alloc(ni, &aerr), mo_cur, nullptr};
-    LC_TRY(aerr);
-    lv.scan = c->arena.alloc((uint64_t)ni + 1, &aerr);
-    LC_TRY(aerr);
-    uint32_t* mo_next = c->arena.alloc(ni, &aerr);
-    LC_TRY(aerr);
-    const uint64_t rk = phase_seed(c->seed, i);
-    const int bits = bits_for(ni);
-    // (a) + (b): ranks and closed-neighbourhood minimum
-    init_keys(c->minkey, i == 0 ? lv.mo : nullptr, ni, rk, L);
-    edge_min(i == 0 ? c->src : nullptr, i == 0 ? c->dst : nullptr, packed, mi, ni, rk, c->minkey,
-             err, c->window_bytes, L);
-    // (c): roots of the parent arborescences
-    jump(c->minkey, lv.root, lv.mo, ni, L);
-    // (d): relabel, drop loops, deduplicate, compact
-    LC_TRY(cudaMemsetAsync(c->ctr, 0, 4 * sizeof(unsigned long long), c->stream));
-    LC_TRY(cudaMemsetAsync(c->flags, 0, ni, c->stream));
-    uint64_t* keys = (packed == c->ebuf[0]) ? c->ebuf[1] : c->ebuf[0];
-    uint64_t* alt = (keys == c->ebuf[0]) ? c->ebuf[1] : c->ebuf[0];
-    PassPlan hplan{};
-    const int hb = hash_plan(mi, &hplan);
-    if (!c->dedup_sort) hist_reset(c->sort, L);
-    relabel(i == 0 ? c->src : nullptr, i == 0 ? c->dst : nullptr, packed, mi, ni, lv.root, bits,
-            keys, &c->ctr->mprime, &c->ctr->emitted, !c->dedup_sort,
-            c->dedup_sort ? nullptr : &hplan, c->sort.hist, i == 0 ? alt : nullptr,
-            c->relabel_window_bytes, L);
-    uint64_t* next = alt;
-    bool by_sort = c->dedup_sort;
-    if (!by_sort) {
-      int which = hash_dedup(keys, alt, &c->ctr->emitted, mi, hplan, hb, true, bits, c->flags,
-                             c->bounds, &c->ctr->m_next, c->sort, err, L);
-      uint64_t* part = which ? alt : keys;
-      next = which ? keys : alt;
-      scan_flags(c->flags, lv.scan, ni, lv.mo, mo_next, &c->ctr->n_next, c->sort, err, L);
-      rename_edges(next, &c->ctr->m_next, mi, bits, lv.scan, L);
-      LC_TRY(cudaGetLastError());
-      LC_TRY(
-          cudaMemcpyAsync(c->h_ctr, c->ctr, sizeof(Counters), cudaMemcpyDeviceToHost, c->stream));
-      LC_TRY(cudaStreamSynchronize(c->stream));
-      c->prof.resolve();
-      if (c->h_ctr->err & kErrBadVertex) return LC_ERR_INVALID;
-      if (c->h_ctr->err & kErrTimeout) return LC_ERR_TIMEOUT;
-      if (c->h_ctr->err & kErrOverflow) {
-        // a bucket held more distinct keys than its shared-memory set: redo
-        // this phase's deduplication by a full sort of the intact keys
-        ++c->fallbacks;
-        by_sort = true;
-        keys = part;
-        alt = next;
-        unmix_keys(keys, &c->ctr->emitted, mi, L);
-        LC_TRY(cudaMemsetAsync(&c->ctr->m_next, 0, 2 * sizeof(unsigned long long), c->stream));
-        LC_TRY(cudaMemsetAsync(&c->ctr->err, 0, sizeof(unsigned), c->stream));
-        LC_TRY(cudaMemsetAsync(c->flags, 0, ni, c->stream));
-      }
+  BatchView bv{};
+  if (BatchState* b = c->batch) {
+    if (i > 0) {
+      // per-graph offsets and edge counts of this level, from the last level
+      uint32_t* voff = c->arena.alloc(b->k + 1, &aerr);
+      if (aerr != cudaSuccess) return fail(c, status_of(aerr));
+      uint32_t* mcnt = c->arena.alloc(b->k, &aerr);
+      if (aerr != cudaSuccess) return fail(c, status_of(aerr));
+      batch_next_level(b->voff.back(), c->levels.back().scan, b->k, voff, r.packed, mi, mcnt, L);
+      b->voff.push_back(voff);
+      b->mcnt.push_back(mcnt);
     }
-    if (by_sort) {
-      // sort all key bits, mark endpoints of distinct keys, keep the first of
-      // each run renamed (output sorted)
-      int w2 = radix_sort_u64(keys, alt, &c->ctr->emitted, mi, 2 * bits, c->sort, err, c->flags,
-                              bits, L);
-      uint64_t* sorted = w2 ? alt : keys;
-      next = w2 ? keys : alt;
-      scan_flags(c->flags, lv.scan, ni, lv.mo, mo_next, &c->ctr->n_next, c->sort, err, L);
-      unique_rename(sorted, &c->ctr->emitted, mi, bits, lv.scan, next, &c->ctr->m_next, c->sort,
-                    err, L);
-      LC_TRY(cudaGetLastError());
-      LC_TRY(
-          cudaMemcpyAsync(c->h_ctr, c->ctr, sizeof(Counters), cudaMemcpyDeviceToHost, c->stream));
-      LC_TRY(cudaStreamSynchronize(c->stream));
-      c->prof.resolve();
-      if (c->h_ctr->err & kErrBadVertex) return LC_ERR_INVALID;
-      if (c->h_ctr->err & kErrTimeout) return LC_ERR_TIMEOUT;
-    }
-    hn.push_back(ni);
-    hm.push_back(mi);
-    c->last_mp.push_back(c->h_ctr->mprime);
-    c->last_emitted.push_back(c->h_ctr->emitted);
-    c->levels.push_back(lv);
-    ni = (uint32_t)c->h_ctr->n_next;
-    mi = c->h_ctr->m_next;
-    packed = next;
-    mo_cur = mo_next;
+    batch_phase_seeds(b->d_seeds, b->k, i, b->d_rk, L);
+    bv = BatchView{b->d_rk, b->voff.back(), b->k};
   }
+  const BatchView* bp = c->batch ? &bv : nullptr;
+  // (a) + (b): ranks and closed-neighbourhood minimum
+  init_keys(c->minkey, i == 0 ? r.lv.mo : nullptr, ni, rk, bp, L);
+  edge_min(i == 0 ? c->src : nullptr, i == 0 ? c->dst : nullptr, r.packed, mi, ni, rk, c->minkey,
+           err, c->window_bytes, bp, L);
+  // (c): roots of the parent arborescences
+  jump(c->minkey, r.lv.root, r.lv.mo, ni, L);
+  // (d): relabel, drop loops, deduplicate, compact
+  if (cudaMemsetAsync(c->ctr, 0, 4 * sizeof(unsigned long long), c->stream) != cudaSuccess ||
+      cudaMemsetAsync(c->flags, 0, ni, c->stream) != cudaSuccess)
+    return fail(c, LC_ERR_CUDA);
+  r.keys = (r.packed == c->ebuf[0]) ? c->ebuf[1] : c->ebuf[0];
+  r.alt = (r.keys == c->ebuf[0]) ? c->ebuf[1] : c->ebuf[0];
+  PassPlan hplan{};
+  const int hb = hash_plan(mi, &hplan);
+  if (!c->dedup_sort) hist_reset(c->sort, L);
+  relabel(i == 0 ? c->src : nullptr, i == 0 ? c->dst : nullptr, r.packed, mi, ni, r.lv.root,
+          r.bits, r.keys, &c->ctr->mprime, &c->ctr->emitted, !c->dedup_sort,
+          c->dedup_sort ? nullptr : &hplan, c->sort.hist, i == 0 ? r.alt : nullptr,
+          c->relabel_window_bytes, L);
+  if (!c->dedup_sort) {
+    int which = hash_dedup(r.keys, r.alt, &c->ctr->emitted, mi, hplan, hb, true, r.bits, c->flags,
+                           c->bounds, &c->ctr->m_next, c->sort, err, L);
+    r.part = which ? r.alt : r.keys;
+    r.next = which ? r.keys : r.alt;
+    scan_flags(c->flags, r.lv.scan, ni, r.lv.mo, r.mo_next, &c->ctr->n_next, c->sort, err, L);
+    rename_edges(r.next, &c->ctr->m_next, mi, r.bits, r.lv.scan, L);
+    r.state = RunState::kPhase;
+  } else {
+    r.part = r.keys;
+    r.next = r.alt;
+    r.state = RunState::kSortPhase;
+    lc_status st = enqueue_sort_dedup(c);
+    if (st != LC_OK) return st;
+  }
+  if (cudaMemcpyAsync(c->h_ctr, c->ctr, sizeof(Counters), cudaMemcpyDeviceToHost, c->stream) !=
+      cudaSuccess)
+    return fail(c, LC_ERR_CUDA);
+  lc_status st = record(c);
+  return st == LC_OK ? st : fail(c, st);
+}
+
+// Deduplicate the keys in rs.part by a full sort of all key bits, mark the
+// endpoints of distinct keys, keep the first of each run renamed (output
+// sorted, in rs.next).
+static lc_status enqueue_sort_dedup(lc_ctx* c) {
+  RunState& r = c->rs;
+  const Launch& L = c->L;
+  unsigned* err = &c->ctr->err;
+  int w2 = radix_sort_u64(r.part, r.next, &c->ctr->emitted, r.mi, 2 * r.bits, c->sort, err,
+                          c->flags, r.bits, L);
+  uint64_t* sorted = w2 ? r.next : r.part;
+  r.next = w2 ? r.part : r.next;
+  scan_flags(c->flags, r.lv.scan, r.ni, r.lv.mo, r.mo_next, &c->ctr->n_next, c->sort, err, L);
+  unique_rename(sorted, &c->ctr->emitted, r.mi, r.bits, r.lv.scan, r.next, &c->ctr->m_next,
+                c->sort, err, L);
+  return LC_OK;
+}
+
+// (e): compose the phase maps top-down; level i's labels overwrite its root
+// array in place (level 0 writes the caller's labels).
+static lc_status enqueue_labels(lc_ctx* c) {
   const uint32_t R = (uint32_t)c->levels.size();
-  // (e): compose the phase maps top-down; level i's labels overwrite its root
-  // array in place (level 0 writes the caller's labels)
   for (int i = (int)R - 1; i >= 0; --i) {
     const Level& lv = c->levels[i];
     const uint32_t* up = (i + 1 < (int)R) ? c->levels[i + 1].root : nullptr;
-    uint32_t* out = i == 0 ? d_labels : lv.root;
-    propagate(lv.root, lv.scan, lv.mo, up, out, lv.n, L);
+    uint32_t* out = i == 0 ? c->rs.d_labels : lv.root;
+    propagate(lv.root, lv.scan, lv.mo, up, out, lv.n, c->L);
   }
-  LC_TRY(cudaGetLastError());
-  LC_TRY(cudaStreamSynchronize(c->stream));
+  if (c->batch) batch_localize(c->rs.d_labels, c->n, c->batch->d_voff0, c->batch->k, c->L);
+  c->rs.state = RunState::kLabels;
+  lc_status st = record(c);
+  return st == LC_OK ? st : fail(c, st);
+}
+
+static lc_status run_begin(lc_ctx* c, uint32_t* d_labels) {
+  RunState& r = c->rs;
+  r = RunState{};
+  r.d_labels = d_labels;
+  c->last_rounds = 0;
+  c->last_mp.clear();
+  c->last_emitted.clear();
+  c->levels.clear();
+  c->arena.reset();
+  if (c->n == 0) {
+    r.state = RunState::kDone;
+    return LC_OK;
+  }
+  if (c->m == 0) {
+    identity_labels(d_labels, c->n, c->L);
+    if (c->batch) batch_localize(d_labels, c->n, c->batch->d_voff0, c->batch->k, c->L);
+    r.state = RunState::kLabels;
+    lc_status st = record(c);
+    return st == LC_OK ? st : fail(c, st);
+  }
+  if (cudaMemsetAsync(c->ctr, 0, sizeof(Counters), c->stream) != cudaSuccess)
+    return fail(c, LC_ERR_CUDA);
+  if (BatchState* b = c->batch) {
+    b->voff.assign(1, b->d_voff0);
+    b->mcnt.clear();
+    batch_globalize(b->user_src, b->user_dst, b->d_eoff, b->d_voff0, b->k, c->m, c->own_src,
+                    c->own_dst, &c->ctr->err, c->L);
+  }
+  cudaError_t aerr = cudaSuccess;
+  r.ni = c->n;
+  r.mi = c->m;
+  r.packed = nullptr;
+  r.mo_cur = c->arena.alloc(r.ni, &aerr);
+  if (aerr != cudaSuccess) return fail(c, status_of(aerr));
+  r.i = 0;
+  return enqueue_phase(c);
+}
+
+static lc_status run_wait(lc_ctx* c) {
+  cudaError_t e = c->ev ? cudaEventSynchronize(c->ev) : cudaStreamSynchronize(c->stream);
+  return status_of(e);
+}
+
+// Called once the work enqueued last has completed.
+static lc_status run_complete(lc_ctx* c) {
+  RunState& r = c->rs;
   c->prof.resolve();
-  c->last_rounds = R;
+  if (r.state == RunState::kLabels) {
+    c->last_rounds = (uint32_t)c->levels.size();
+    r.state = RunState::kDone;
+    return LC_OK;
+  }
+  if (r.state != RunState::kPhase && r.state != RunState::kSortPhase) return r.st;
+  const Counters& h = *c->h_ctr;
+  if (h.err & kErrBadVertex) return fail(c, LC_ERR_INVALID);
+  if (h.err & kErrTimeout) return fail(c, LC_ERR_TIMEOUT);
+  if (r.state == RunState::kPhase && (h.err & kErrOverflow)) {
+    // a bucket held more distinct keys than its shared-memory set: redo this
+    // phase's deduplication by a full sort of the intact keys
+    ++c->fallbacks;
+    unmix_keys(r.part, &c->ctr->emitted, r.mi, c->L);
+    if (cudaMemsetAsync(&c->ctr->m_next, 0, 2 * sizeof(unsigned long long), c->stream) !=
+            cudaSuccess ||
+        cudaMemsetAsync(&c->ctr->err, 0, sizeof(unsigned), c->stream) != cudaSuccess ||
+        cudaMemsetAsync(c->flags, 0, r.ni, c->stream) != cudaSuccess)
+      return fail(c, LC_ERR_CUDA);
+    r.state = RunState::kSortPhase;
+    lc_status st = enqueue_sort_dedup(c);
+    if (st != LC_OK) return st;
+    if (cudaMemcpyAsync(c->h_ctr, c->ctr, sizeof(Counters), cudaMemcpyDeviceToHost, c->stream) !=
+        cudaSuccess)
+      return fail(c, LC_ERR_CUDA);
+    st = record(c);
+    return st == LC_OK ? st : fail(c, st);
+  }
+  r.hn.push_back(r.ni);
+  r.hm.push_back(r.mi);
+  c->last_mp.push_back(h.mprime);
+  c->last_emitted.push_back(h.emitted);
+  c->levels.push_back(r.lv);
+  r.ni = (uint32_t)h.n_next;
+  r.mi = h.m_next;
+  r.packed = r.next;
+  r.mo_cur = r.mo_next;
+  if (r.mi == 0) return enqueue_labels(c);
+  if (++r.i >= round_cap(c->n)) return fail(c, LC_ERR_NO_CONVERGENCE);
+  return enqueue_phase(c);
+}
+
+static lc_status run_loop(lc_ctx* c, uint32_t* d_labels, uint32_t* rounds, uint64_t* n_i,
+                          uint64_t* m_i, uint32_t cap) {
+  if (rounds) *rounds = 0;
+  lc_status st = run_begin(c, d_labels);
+  while (st == LC_OK && c->rs.state != RunState::kDone) {
+    st = run_wait(c);
+    if (st == LC_OK) st = run_complete(c);
+  }
+  if (st != LC_OK) return st;
+  const uint32_t R = c->last_rounds;
   if (rounds) *rounds = R;
   if (n_i || m_i) {
     for (uint32_t i = 0; i < std::min(R, cap); ++i) {
-      if (n_i) n_i[i] = hn[i];
-      if (m_i) m_i[i] = hm[i];
+      if (n_i) n_i[i] = c->rs.hn[i];
+      if (m_i) m_i[i] = c->rs.hm[i];
     }
     if (R > cap) return LC_ERR_INVALID;
   }
@@ -448,6 +594,95 @@ extern "C" lc_status lc_run_host(lc_ctx* c, const uint32_t* h_src, const uint32_
     LC_TRY(cudaStreamSynchronize(c->stream));
   }
   return st;
+}
+
+extern "C" lc_status lc_batch_create(uint32_t k, const uint32_t* h_n, const uint64_t* h_eoff,
+                                     const uint32_t* d_src, const uint32_t* d_dst,
+                                     const uint64_t* h_seeds, void* stream, lc_ctx** out) {
+  if (!out) return LC_ERR_INVALID;
+  *out = nullptr;
+  if (k == 0 || !h_n || !h_eoff || !h_seeds) return LC_ERR_INVALID;
+  if (h_eoff[0] != 0) return LC_ERR_INVALID;
+  std::vector<uint32_t> voff(k + 1, 0);
+  uint64_t tot = 0;
+  for (uint32_t g = 0; g < k; ++g) {
+    if (h_eoff[g + 1] < h_eoff[g]) return LC_ERR_INVALID;
+    if (h_eoff[g + 1] > h_eoff[g] && h_n[g] == 0) return LC_ERR_INVALID;
+    tot += h_n[g];
+    if (tot > 0xFFFFFFFFull) return LC_ERR_INVALID;
+    voff[g + 1] = (uint32_t)tot;
+  }
+  const uint64_t m = h_eoff[k];
+  if (m > 0xFFFFFFFFull || (m > 0 && (!d_src || !d_dst))) return LC_ERR_INVALID;
+  // the context owns the global-id copy of the edges (filled at every run)
+  lc_ctx* c = nullptr;
+  lc_status st = lc_create((uint32_t)tot, nullptr, nullptr, m, 0, stream, &c);
+  if (st != LC_OK) return st;
+  BatchState* b = new (std::nothrow) BatchState();
+  if (!b) {
+    lc_destroy(c);
+    return LC_ERR_OOM;
+  }
+  c->batch = b;
+  b->k = k;
+  b->user_src = d_src;
+  b->user_dst = d_dst;
+  b->h_eoff.assign(h_eoff, h_eoff + k + 1);
+  b->h_voff0 = voff;
+  cudaError_t e = cudaMalloc(&b->d_seeds, 8ull * k);
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_voff0, 4ull * (k + 1));
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_eoff, 8ull * (k + 1));
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_rk, 8ull * k);
+  if (e == cudaSuccess) e = cudaMemcpy(b->d_seeds, h_seeds, 8ull * k, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(b->d_voff0, voff.data(), 4ull * (k + 1), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(b->d_eoff, h_eoff, 8ull * (k + 1), cudaMemcpyHostToDevice);
+  // level arrays of a batch: offsets and edge counts per graph per level
+  if (e == cudaSuccess) e = c->arena.init(64ull * (2 * k + 2));
+  if (e != cudaSuccess) {
+    lc_destroy(c);
+    return status_of(e);
+  }
+  *out = c;
+  return LC_OK;
+}
+
+extern "C" lc_status lc_batch_run(lc_ctx* c, uint32_t* d_labels, uint32_t* rounds,
+                                  uint64_t* n_i, uint64_t* m_i, uint32_t cap) {
+  if (!c || !c->batch || (!d_labels && c->n > 0)) return LC_ERR_INVALID;
+  DeviceGuard g(c->device);
+  BatchState* b = c->batch;
+  lc_status st = run_loop(c, d_labels, nullptr, nullptr, nullptr, 0);
+  if (st != LC_OK) return st;
+  const uint32_t k = b->k, R = c->last_rounds;
+  // per-level per-graph sizes: level 0 from the input, later levels from the
+  // device arrays written during the run
+  std::vector<uint32_t> voff(k + 1), mcnt(k);
+  std::vector<uint32_t> Rg(k, 0);
+  bool over = false;
+  for (uint32_t i = 0; i < R; ++i) {
+    if (i == 0) {
+      voff = b->h_voff0;
+      for (uint32_t gi = 0; gi < k; ++gi) mcnt[gi] = (uint32_t)(b->h_eoff[gi + 1] - b->h_eoff[gi]);
+    } else {
+      LC_TRY(cudaMemcpy(voff.data(), b->voff[i], 4ull * (k + 1), cudaMemcpyDeviceToHost));
+      LC_TRY(cudaMemcpy(mcnt.data(), b->mcnt[i - 1], 4ull * k, cudaMemcpyDeviceToHost));
+    }
+    for (uint32_t gi = 0; gi < k; ++gi) {
+      if (mcnt[gi] == 0) continue;  // graph finished before this phase
+      if (Rg[gi] != i) continue;     // (cannot happen: a finished graph stays finished)
+      if (i < cap) {
+        if (n_i) n_i[(uint64_t)gi * cap + i] = voff[gi + 1] - voff[gi];
+        if (m_i) m_i[(uint64_t)gi * cap + i] = mcnt[gi];
+      } else {
+        over = true;
+      }
+      Rg[gi] = i + 1;
+    }
+  }
+  if (rounds)
+    for (uint32_t gi = 0; gi < k; ++gi) rounds[gi] = Rg[gi];
+  return over ? LC_ERR_INVALID : LC_OK;
 }
 
 extern "C" lc_status lc_last_stats(const lc_ctx* c, uint32_t* rounds, uint64_t* mp_i,

@@ -28,6 +28,7 @@ enum KernelId : int {
   kKBucketDedup,
   kKRename,
   kKUnmix,
+  kKBatch,
   kKIdentity,
   kKRankProbe,
   kNumKernels
@@ -194,9 +195,18 @@ void unique_rename(const uint64_t* keys, const unsigned long long* d_count, uint
                    unsigned long long* m_next, SortScratch& s, unsigned* err, const Launch& L);
 
 // ---------------------------------------------------------- phase steps
+// A batch of independent graphs in one id space (device pointers): graph g
+// owns ids [voff[g], voff[g+1]) and uses phase seed rk[g].
+struct BatchView {
+  const uint64_t* rk;
+  const uint32_t* voff;
+  uint32_t k;
+};
+
 // minkey[v] = key(v) for v < n; when mo is non-null also mo[v] = v (phase 0).
+// With a batch, each vertex is keyed by its own graph's seed and local id.
 void init_keys(unsigned long long* minkey, uint32_t* mo, uint32_t n, uint64_t rk,
-               const Launch& L);
+               const BatchView* batch, const Launch& L);
 
 // Closed-neighbourhood minimum: minkey[u] = min(minkey[u], key(v)) and
 // minkey[v] = min(minkey[v], key(u)) for every edge.  Edges are either two
@@ -207,7 +217,21 @@ void init_keys(unsigned long long* minkey, uint32_t* mo, uint32_t n, uint64_t rk
 // each pass's atomics stay inside an L2-sized slice of minkey.
 void edge_min(const uint32_t* src, const uint32_t* dst, const uint64_t* packed, uint64_t m,
               uint32_t n, uint64_t rk, unsigned long long* minkey, unsigned* err,
-              uint64_t window_bytes, const Launch& L);
+              uint64_t window_bytes, const BatchView* batch, const Launch& L);
+
+// Batches: phase seeds rk[g] for phase i; local -> global edge ids (ids
+// validated per graph); next level offsets voff_next[g] = scan[voff[g]] and
+// per-graph edge counts of the next level's packed edges e[0, m); global ->
+// local labels.
+void batch_phase_seeds(const uint64_t* seeds, uint32_t k, uint32_t i, uint64_t* rk,
+                       const Launch& L);
+void batch_globalize(const uint32_t* src, const uint32_t* dst, const uint64_t* eoff,
+                     const uint32_t* voff, uint32_t k, uint64_t m, uint32_t* gsrc, uint32_t* gdst,
+                     unsigned* err, const Launch& L);
+void batch_next_level(const uint32_t* voff, const uint32_t* scan, uint32_t k, uint32_t* voff_next,
+                      const uint64_t* e, uint64_t m, uint32_t* mcnt, const Launch& L);
+void batch_localize(uint32_t* labels, uint32_t n, const uint32_t* voff, uint32_t k,
+                    const Launch& L);
 
 // root[v] = root of v's arborescence (follows the parent stored in the low
 // half of minkey, compressing as it goes); mo[root] = min over the tree of

@@ -21,11 +21,53 @@ inline int grid_for(uint64_t work, int per_block, const Launch& L, int blocks_pe
 
 // ------------------------------------------------------------ ranking
 
+// Keys of one phase of a single graph: the phase's stream seed and the id.
+struct GraphKeys {
+  uint64_t rk;
+  __device__ __forceinline__ uint64_t key(uint32_t v) const { return phase_key(rk, v); }
+  __device__ __forceinline__ void pair(uint32_t u, uint32_t v, uint64_t& ku, uint64_t& kv) const {
+    ku = phase_key(rk, u);
+    kv = phase_key(rk, v);
+  }
+};
+
+// Keys of one phase of a batch of independent graphs sharing one id space:
+// graph g owns ids [voff[g], voff[g+1]) and ranks its vertex v with its own
+// phase seed rk[g] and its local id v - voff[g], exactly as a run on graph g
+// alone would.  The low half keeps the global id (the order inside a graph is
+// the same) so that it can index the per-vertex arrays.  Edges never cross
+// graphs, so both endpoints of an edge share one lookup.
+struct BatchKeys {
+  const uint64_t* rk;
+  const uint32_t* voff;
+  uint32_t k;
+  __device__ __forceinline__ uint32_t graph_of(uint32_t v) const {
+    uint32_t lo = 0, hi = k - 1;  // last g with voff[g] <= v
+    while (lo < hi) {
+      uint32_t mid = (lo + hi + 1) >> 1;
+      if (__ldg(voff + mid) <= v) lo = mid;
+      else hi = mid - 1;
+    }
+    return lo;
+  }
+  __device__ __forceinline__ uint64_t key_in(uint32_t g, uint32_t v) const {
+    const uint64_t local = v - __ldg(voff + g);
+    return (splitmix_mix(__ldg(rk + g) + (local + 1ull) * kGamma) & 0xFFFFFFFF00000000ull) | v;
+  }
+  __device__ __forceinline__ uint64_t key(uint32_t v) const { return key_in(graph_of(v), v); }
+  __device__ __forceinline__ void pair(uint32_t u, uint32_t v, uint64_t& ku, uint64_t& kv) const {
+    const uint32_t g = graph_of(u);
+    ku = key_in(g, u);
+    kv = key_in(g, v);
+  }
+};
+
+template <class K>
 __global__ void k_init_keys(unsigned long long* __restrict__ minkey, uint32_t* __restrict__ mo,
-                            uint32_t n, uint64_t rk) {
+                            uint32_t n, K keys) {
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
-    minkey[v] = phase_key(rk, (uint32_t)v);
+    minkey[v] = keys.key((uint32_t)v);
     if (mo != nullptr) mo[v] = (uint32_t)v;
   }
 }
@@ -43,7 +85,8 @@ __global__ void k_rank_probe(uint64_t rk, uint32_t v0, uint32_t count, uint32_t*
 // the edge needs one atomic, applied when that endpoint lies in
 // [lo, lo + span) (so one pass over the edges touches an L2-sized slice of
 // minkey).
-__device__ __forceinline__ void min_edge_window(uint32_t u, uint32_t v, uint32_t n, uint64_t rk,
+template <class K>
+__device__ __forceinline__ void min_edge_window(uint32_t u, uint32_t v, uint32_t n, const K& keys,
                                                 unsigned long long* minkey, unsigned* err,
                                                 uint32_t lo, uint32_t span, bool check) {
   if (check && (u >= n || v >= n)) {
@@ -51,16 +94,18 @@ __device__ __forceinline__ void min_edge_window(uint32_t u, uint32_t v, uint32_t
     return;
   }
   if (u == v) return;
-  const uint64_t ku = phase_key(rk, u), kv = phase_key(rk, v);
+  uint64_t ku, kv;
+  keys.pair(u, v, ku, kv);
   const uint32_t hi = ku < kv ? v : u;
   if (hi - lo < span) atomicMin(&minkey[hi], (unsigned long long)(ku < kv ? ku : kv));
 }
 
 // Input edges as two uint32 arrays; `vec` = both arrays 16-byte aligned.
 // Updates only vertices in [lo, lo + span); ids are validated when `check`.
+template <class K>
 __global__ void __launch_bounds__(kThreads) k_edge_min_soa(
     const uint32_t* __restrict__ src, const uint32_t* __restrict__ dst, uint64_t m, uint32_t n,
-    uint64_t rk, unsigned long long* minkey, unsigned* err, int vec, uint32_t lo, uint32_t span,
+    K keys, unsigned long long* minkey, unsigned* err, int vec, uint32_t lo, uint32_t span,
     int check) {
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   const uint64_t gt = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -71,40 +116,108 @@ __global__ void __launch_bounds__(kThreads) k_edge_min_soa(
     const uint4* d4 = reinterpret_cast<const uint4*>(dst);
     for (uint64_t q = gt; q < nq; q += stride) {
       uint4 s = __ldcs(s4 + q), d = __ldcs(d4 + q);
-      min_edge_window(s.x, d.x, n, rk, minkey, err, lo, span, check);
-      min_edge_window(s.y, d.y, n, rk, minkey, err, lo, span, check);
-      min_edge_window(s.z, d.z, n, rk, minkey, err, lo, span, check);
-      min_edge_window(s.w, d.w, n, rk, minkey, err, lo, span, check);
+      min_edge_window(s.x, d.x, n, keys, minkey, err, lo, span, check);
+      min_edge_window(s.y, d.y, n, keys, minkey, err, lo, span, check);
+      min_edge_window(s.z, d.z, n, keys, minkey, err, lo, span, check);
+      min_edge_window(s.w, d.w, n, keys, minkey, err, lo, span, check);
     }
     done = nq * 4;
   }
   for (uint64_t j = done + gt; j < m; j += stride)
-    min_edge_window(__ldcs(src + j), __ldcs(dst + j), n, rk, minkey, err, lo, span, check);
+    min_edge_window(__ldcs(src + j), __ldcs(dst + j), n, keys, minkey, err, lo, span, check);
 }
 
 // One atomic per edge, at the endpoint with the larger key (see
 // min_edge_window).
-__device__ __forceinline__ void min_edge_packed(uint64_t x, uint64_t rk,
+template <class K>
+__device__ __forceinline__ void min_edge_packed(uint64_t x, const K& keys,
                                                 unsigned long long* minkey) {
   const uint32_t a = (uint32_t)(x >> 32), b = (uint32_t)x;
-  const uint64_t ka = phase_key(rk, a), kb = phase_key(rk, b);
+  uint64_t ka, kb;
+  keys.pair(a, b, ka, kb);
   if (ka < kb) atomicMin(&minkey[b], (unsigned long long)ka);
   else atomicMin(&minkey[a], (unsigned long long)kb);
 }
 
 // Packed edges (a << 32 | b), two per 128-bit load.
+template <class K>
 __global__ void __launch_bounds__(kThreads) k_edge_min_packed(
-    const uint64_t* __restrict__ e, uint64_t m, uint64_t rk, unsigned long long* minkey) {
+    const uint64_t* __restrict__ e, uint64_t m, K keys, unsigned long long* minkey) {
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   const uint64_t npair = m / 2;
   const ulonglong2* e2 = reinterpret_cast<const ulonglong2*>(e);
   const uint64_t gt = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   for (uint64_t q = gt; q < npair; q += stride) {
     ulonglong2 p = __ldcs(e2 + q);
-    min_edge_packed(p.x, rk, minkey);
-    min_edge_packed(p.y, rk, minkey);
+    min_edge_packed(p.x, keys, minkey);
+    min_edge_packed(p.y, keys, minkey);
   }
-  if ((m & 1) && gt == 0) min_edge_packed(e[m - 1], rk, minkey);
+  if ((m & 1) && gt == 0) min_edge_packed(e[m - 1], keys, minkey);
+}
+
+// ------------------------------------------------------- batches
+
+// rk[g] = stream seed of phase i for graph g.
+__global__ void k_batch_phase_seeds(const uint64_t* __restrict__ seeds, uint32_t k, uint32_t i,
+                                    uint64_t* __restrict__ rk) {
+  for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < k; g += gridDim.x * blockDim.x)
+    rk[g] = splitmix_mix(seeds[g] + (uint64_t)(i + 1) * kGamma);
+}
+
+// Local edge ids -> global ids: edge j of graph g (eoff[g] <= j < eoff[g+1])
+// gets voff[g] added to both endpoints; local ids >= n_g set kErrBadVertex
+// and become a self-loop on the graph's first vertex.
+__global__ void k_batch_globalize(const uint32_t* __restrict__ src, const uint32_t* __restrict__ dst,
+                                  const uint64_t* __restrict__ eoff,
+                                  const uint32_t* __restrict__ voff, uint32_t k, uint64_t m,
+                                  uint32_t* __restrict__ gsrc, uint32_t* __restrict__ gdst,
+                                  unsigned* err) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += stride) {
+    uint32_t lo = 0, hi = k - 1;  // last g with eoff[g] <= j
+    while (lo < hi) {
+      uint32_t mid = (lo + hi + 1) >> 1;
+      if (__ldg(eoff + mid) <= j) lo = mid;
+      else hi = mid - 1;
+    }
+    const uint32_t base = __ldg(voff + lo), ng = __ldg(voff + lo + 1) - base;
+    uint32_t u = src[j], v = dst[j];
+    if (u >= ng || v >= ng) {
+      atomicOr(err, kErrBadVertex);
+      u = v = 0;
+    }
+    gsrc[j] = base + u;
+    gdst[j] = base + v;
+  }
+}
+
+// Offsets of the next level: graph g's surviving nodes are the scan values of
+// its range, so voff_next[g] = scan[voff[g]] (g <= k).
+__global__ void k_batch_next_offsets(const uint32_t* __restrict__ voff,
+                                     const uint32_t* __restrict__ scan, uint32_t k,
+                                     uint32_t* __restrict__ voff_next) {
+  for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g <= k; g += gridDim.x * blockDim.x)
+    voff_next[g] = scan[voff[g]];
+}
+
+// mcnt[g] += number of packed edges (a << 32 | b) whose endpoint a lies in
+// graph g's range of voff.
+__global__ void k_batch_count_edges(const uint64_t* __restrict__ e, uint64_t m,
+                                    const uint32_t* __restrict__ voff, uint32_t k,
+                                    uint32_t* __restrict__ mcnt) {
+  BatchKeys b{nullptr, voff, k};
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += stride)
+    atomicAdd(&mcnt[b.graph_of((uint32_t)(e[j] >> 32))], 1u);
+}
+
+// labels[v] -= voff[graph of v]: global labels to per-graph local labels.
+__global__ void k_batch_localize(uint32_t* __restrict__ labels, uint32_t n,
+                                 const uint32_t* __restrict__ voff, uint32_t k) {
+  BatchKeys b{nullptr, voff, k};
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride)
+    labels[v] -= __ldg(voff + b.graph_of((uint32_t)v));
 }
 
 // ------------------------------------------------------- pointer jumping
@@ -307,20 +420,24 @@ __global__ void k_identity(uint32_t* labels, uint32_t n) {
 }  // namespace
 
 void init_keys(unsigned long long* minkey, uint32_t* mo, uint32_t n, uint64_t rk,
-               const Launch& L) {
+               const BatchView* batch, const Launch& L) {
   if (n == 0) return;
   KScope ks(L, kKInitKeys);
-  k_init_keys<<<grid_for(n, kThreads, L), kThreads, 0, L.stream>>>(minkey, mo, n, rk);
+  if (batch)
+    k_init_keys<<<grid_for(n, kThreads, L), kThreads, 0, L.stream>>>(
+        minkey, mo, n, BatchKeys{batch->rk, batch->voff, batch->k});
+  else
+    k_init_keys<<<grid_for(n, kThreads, L), kThreads, 0, L.stream>>>(minkey, mo, n, GraphKeys{rk});
 }
 
-void edge_min(const uint32_t* src, const uint32_t* dst, const uint64_t* packed, uint64_t m,
-              uint32_t n, uint64_t rk, unsigned long long* minkey, unsigned* err,
-              uint64_t window_bytes, const Launch& L) {
-  if (m == 0) return;
+template <class K>
+static void edge_min_impl(const uint32_t* src, const uint32_t* dst, const uint64_t* packed,
+                          uint64_t m, uint32_t n, K keys, unsigned long long* minkey,
+                          unsigned* err, uint64_t window_bytes, const Launch& L) {
   if (packed != nullptr) {
     KScope ks(L, kKEdgeMinPacked);
-    k_edge_min_packed<<<grid_for(m / 2 + 1, kThreads, L), kThreads, 0, L.stream>>>(packed, m, rk,
-                                                                                   minkey);
+    k_edge_min_packed<<<grid_for(m / 2 + 1, kThreads, L), kThreads, 0, L.stream>>>(packed, m,
+                                                                                   keys, minkey);
   } else {
     int vec = ((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst)) & 15) == 0;
     // vertex windows whose minkey slices fit the L2 budget; one pass each
@@ -332,9 +449,53 @@ void edge_min(const uint32_t* src, const uint32_t* dst, const uint64_t* packed, 
       uint64_t sp = std::min<uint64_t>(span, n - lo);
       KScope ks(L, kKEdgeMinSoa);
       k_edge_min_soa<<<grid_for((m + 3) / 4, kThreads, L), kThreads, 0, L.stream>>>(
-          src, dst, m, n, rk, minkey, err, vec, (uint32_t)lo, (uint32_t)sp, p == 0);
+          src, dst, m, n, keys, minkey, err, vec, (uint32_t)lo, (uint32_t)sp, p == 0);
     }
   }
+}
+
+void edge_min(const uint32_t* src, const uint32_t* dst, const uint64_t* packed, uint64_t m,
+              uint32_t n, uint64_t rk, unsigned long long* minkey, unsigned* err,
+              uint64_t window_bytes, const BatchView* batch, const Launch& L) {
+  if (m == 0) return;
+  if (batch)
+    edge_min_impl(src, dst, packed, m, n, BatchKeys{batch->rk, batch->voff, batch->k}, minkey,
+                  err, window_bytes, L);
+  else
+    edge_min_impl(src, dst, packed, m, n, GraphKeys{rk}, minkey, err, window_bytes, L);
+}
+
+void batch_phase_seeds(const uint64_t* seeds, uint32_t k, uint32_t i, uint64_t* rk,
+                       const Launch& L) {
+  KScope ks(L, kKBatch);
+  k_batch_phase_seeds<<<grid_for(k, kThreads, L), kThreads, 0, L.stream>>>(seeds, k, i, rk);
+}
+
+void batch_globalize(const uint32_t* src, const uint32_t* dst, const uint64_t* eoff,
+                     const uint32_t* voff, uint32_t k, uint64_t m, uint32_t* gsrc, uint32_t* gdst,
+                     unsigned* err, const Launch& L) {
+  if (m == 0) return;
+  KScope ks(L, kKBatch);
+  k_batch_globalize<<<grid_for(m, kThreads, L), kThreads, 0, L.stream>>>(src, dst, eoff, voff, k,
+                                                                         m, gsrc, gdst, err);
+}
+
+void batch_next_level(const uint32_t* voff, const uint32_t* scan, uint32_t k, uint32_t* voff_next,
+                      const uint64_t* e, uint64_t m, uint32_t* mcnt, const Launch& L) {
+  KScope ks(L, kKBatch);
+  k_batch_next_offsets<<<grid_for(k + 1, kThreads, L), kThreads, 0, L.stream>>>(voff, scan, k,
+                                                                                voff_next);
+  cudaMemsetAsync(mcnt, 0, sizeof(uint32_t) * k, L.stream);
+  if (m)
+    k_batch_count_edges<<<grid_for(m, kThreads, L), kThreads, 0, L.stream>>>(e, m, voff_next, k,
+                                                                             mcnt);
+}
+
+void batch_localize(uint32_t* labels, uint32_t n, const uint32_t* voff, uint32_t k,
+                    const Launch& L) {
+  if (n == 0) return;
+  KScope ks(L, kKBatch);
+  k_batch_localize<<<grid_for(n, kThreads, L), kThreads, 0, L.stream>>>(labels, n, voff, k);
 }
 
 void jump(unsigned long long* minkey, uint32_t* root, uint32_t* mo, uint32_t n, const Launch& L) {

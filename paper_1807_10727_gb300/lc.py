@@ -25,7 +25,7 @@ LC_VARIANT_FOREST, LC_VARIANT_TWO_HOP, LC_VARIANT_TREE = 0, 1, 2
 LC_DEDUP_HASH, LC_DEDUP_SORT = 0, 1
 EXPORTED = ("lc_create", "lc_configure", "lc_set_dedup", "lc_set_param", "lc_run", "lc_run_host",
             "lc_last_stats", "lc_profile", "lc_kernel_stats", "lc_destroy", "lc_status_str",
-            "lc_rank_probe", "lc_run_static")
+            "lc_rank_probe", "lc_run_static", "lc_batch_create", "lc_batch_run")
 LC_STATIC_MAX_N, LC_STATIC_MAX_M = 131072, 524288
 
 _lib = None
@@ -63,6 +63,8 @@ def load(path: str | None = None):
     lib.lc_status_str.restype = ctypes.c_char_p
     lib.lc_rank_probe.argtypes = [u64, u32, u32, u32, p, p]
     lib.lc_run_static.argtypes = [u32, p, p, u64, u64, p, p, pu32, pu64, pu64, u32]
+    lib.lc_batch_create.argtypes = [u32, p, p, p, p, p, p, ctypes.POINTER(p)]
+    lib.lc_batch_run.argtypes = [p, p, p, p, p, u32]
     for name in EXPORTED:
         if name != "lc_status_str":
             getattr(lib, name).restype = i32
@@ -184,6 +186,28 @@ def lc_run_static(n: int, d_src: int, d_dst: int, m: int, seed: int, stream: int
     return r, list(n_i[:r]), list(m_i[:r])
 
 
+def lc_batch_create(k: int, h_n: np.ndarray, h_eoff: np.ndarray, d_src: int, d_dst: int,
+                    h_seeds: np.ndarray, stream: int) -> int:
+    h_n = np.ascontiguousarray(h_n, dtype=np.uint32)
+    h_eoff = np.ascontiguousarray(h_eoff, dtype=np.uint64)
+    h_seeds = np.ascontiguousarray(h_seeds, dtype=np.uint64)
+    out = ctypes.c_void_p()
+    _check(load().lc_batch_create(k, h_n.ctypes.data, h_eoff.ctypes.data, d_src, d_dst,
+                                  h_seeds.ctypes.data, stream, ctypes.byref(out)),
+           "lc_batch_create")
+    return out.value
+
+
+def lc_batch_run(ctx: int, k: int, d_labels: int, cap: int = 256):
+    """Returns (rounds[k], n_i[k, cap], m_i[k, cap]) as numpy arrays."""
+    rounds = np.zeros(k, dtype=np.uint32)
+    n_i = np.zeros((k, cap), dtype=np.uint64)
+    m_i = np.zeros((k, cap), dtype=np.uint64)
+    _check(load().lc_batch_run(ctx, d_labels, rounds.ctypes.data, n_i.ctypes.data,
+                               m_i.ctypes.data, cap), "lc_batch_run")
+    return rounds, n_i, m_i
+
+
 def lc_rank_probe(seed: int, i: int, v0: int, count: int, d_out: int, stream: int) -> None:
     _check(load().lc_rank_probe(seed, i, v0, count, d_out, stream), "lc_rank_probe")
 
@@ -258,6 +282,46 @@ class LocalContraction:
 
     def kernel_stats(self) -> dict:
         return lc_kernel_stats(self.ctx)
+
+    def close(self) -> None:
+        if getattr(self, "ctx", None):
+            lc_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class BatchLocalContraction:
+    """k independent graphs run together; results equal k separate runs.
+
+    n: uint32[k] vertex counts; eoff: uint64[k+1] edge offsets into the CUDA
+    32-bit tensors src/dst (local ids); seeds: uint64[k] rank seeds.
+    """
+
+    def __init__(self, n, eoff, src, dst, seeds, stream=None):
+        self.n = np.ascontiguousarray(n, dtype=np.uint32)
+        self.k = int(self.n.shape[0])
+        self.eoff = np.ascontiguousarray(eoff, dtype=np.uint64)
+        self.voff = np.zeros(self.k + 1, dtype=np.int64)
+        np.cumsum(self.n, out=self.voff[1:])
+        m = int(self.eoff[-1])
+        self._src, self._dst = src, dst
+        self.ctx = lc_batch_create(self.k, self.n, self.eoff, _dev_ptr(src, m, "src") if m else 0,
+                                   _dev_ptr(dst, m, "dst") if m else 0, seeds,
+                                   _stream_handle(stream))
+
+    def run(self, labels=None, cap: int = 256):
+        import torch
+        total = int(self.voff[-1])
+        if labels is None:
+            dev = self._src.device if self._src is not None else torch.device("cuda")
+            labels = torch.empty(max(total, 1), dtype=torch.int32, device=dev)
+        rounds, n_i, m_i = lc_batch_run(self.ctx, self.k, _dev_ptr(labels, total, "labels"), cap)
+        return labels, rounds, n_i, m_i
 
     def close(self) -> None:
         if getattr(self, "ctx", None):
