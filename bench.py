@@ -241,6 +241,85 @@ def bench_batch(dev, stream, steps=5, k=4096):
             "speedup": serial_s / batched_s}
 
 
+def bench_serving(rates=(300.0, 1000.0, 3000.0), count=160, slots=32):
+    """Config 5: Poisson arrivals of CC requests (ER / R-MAT / permuted grid,
+    n log-uniform in [2^10, 2^22], average degree 4-32), served by the
+    continuous-batching loop vs the serial plain path (one request at a time,
+    lc_run_host, in arrival order).  Latency = arrival to labels on the host.
+    The same requests are replayed at every rate."""
+    import threading
+
+    from paper_1807_10727_gb300 import lc, synth
+    reqs = synth.serving_stream(1000.0, count)
+    log("serving: %d requests generated" % count)
+    base = np.array([r.arrival_s for r in reqs])
+    edges = int(sum(r.graph.m for r in reqs))
+
+    def summarize(lat, t_first, t_last):
+        lat = np.asarray(lat)
+        return {"graphs_per_s": len(lat) / (t_last - t_first),
+                "latency_ms_p50": float(np.percentile(lat, 50) * 1e3),
+                "latency_ms_p99": float(np.percentile(lat, 99) * 1e3)}
+
+    out = {"workload": "%d requests, ER/R-MAT/grid, n in [2^10, 2^22], degree 4-32, %d edges"
+                       % (count, edges), "slots": slots, "rates": []}
+    srv = lc.Server(slots=slots)
+    warm = [srv.submit(r.graph.n, r.graph.src, r.graph.dst, r.graph.seed) for r in reqs[:8]]
+    for j in warm:
+        srv.wait(j)
+    for rate in rates:
+        arr = base * (1000.0 / rate)
+        ids = [None] * count
+        ready = threading.Semaphore(0)
+        t0 = time.perf_counter() + 0.05
+
+        def producer():
+            for k, r in enumerate(reqs):
+                d = t0 + arr[k] - time.perf_counter()
+                if d > 0:
+                    time.sleep(d)
+                ids[k] = srv.submit(r.graph.n, r.graph.src, r.graph.dst, r.graph.seed)
+                ready.release()
+
+        th = threading.Thread(target=producer)
+        th.start()
+        lat, t_last = [], t0
+        for k in range(count):
+            if not ready.acquire(timeout=120):
+                raise RuntimeError("serving: request %d was not submitted within 120 s" % k)
+            _, _, l = srv.wait(ids[k], timeout_s=120.0)
+            lat.append(l)
+            t_last = max(t_last, t0 + arr[k] + l)
+        th.join()
+        row = summarize(lat, t0, t_last)
+        row["rate_req_s"] = rate
+        out["rates"].append(row)
+        log("serving: rate %g done" % rate)
+    out["peak_active"] = srv.stats()["peak_active"]
+    srv.close()
+    # serial plain path at the middle rate
+    rate = rates[len(rates) // 2]
+    arr = base * (1000.0 / rate)
+    lat = []
+    t0 = time.perf_counter() + 0.05
+    for k, r in enumerate(reqs):
+        d = t0 + arr[k] - time.perf_counter()
+        if d > 0:
+            time.sleep(d)
+        c = lc.LocalContraction(r.graph.n, m=r.graph.m, seed=r.graph.seed)
+        c.run_host(r.graph.src, r.graph.dst)
+        c.close()
+        lat.append(time.perf_counter() - (t0 + arr[k]))
+    row = summarize(lat, t0, time.perf_counter())
+    row["rate_req_s"] = rate
+    out["serial"] = row
+    return out
+
+
+def log(msg):
+    print("[bench] " + msg, file=sys.stderr, flush=True)
+
+
 def dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -289,6 +368,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched (config 4) leg")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving (config 5) leg")
     ap.add_argument("--no-profile", action="store_true",
                     help="skip the per-kernel event timing (roofline) of the timed steps")
     args = ap.parse_args()
@@ -337,6 +417,7 @@ def main():
     torch.cuda.synchronize(dev)
     barrier()
     clk = clocks.stop()
+    log("timed steps done")
     ms = e0.elapsed_time(e1) / args.steps
     kstats = ctx.kernel_stats()
     ctx.profile(False)
@@ -404,6 +485,12 @@ def main():
     if rank == 0 and not args.no_batch:
         torch.cuda.empty_cache()
         batched = bench_batch(dev, stream)
+        log("batched leg done")
+    serving = None
+    if rank == 0 and not args.no_serving:
+        torch.cuda.empty_cache()
+        serving = bench_serving()
+        log("serving leg done")
 
     if rank == 0:
         line = {
@@ -416,6 +503,7 @@ def main():
                        "l2": "inputs (8 B/edge) larger than L2; no flush"},
             "roofline": roof, "path_roofline": path_roof,
             "e2e": e2e, "cpu_baseline": cpu, "gpu_launches": launches, "batched": batched,
+            "serving": serving,
             "clocks": clk, "kernels": kernels,
             "sizes": [[int(a), int(b), int(c), int(d)]
                       for a, b, c, d in zip(res.n_i, res.m_i, mp, em)],

@@ -45,7 +45,9 @@ typedef enum {
   LC_ERR_OOM = 2,            /* a device allocation failed */
   LC_ERR_CUDA = 3,           /* a CUDA runtime call failed */
   LC_ERR_NO_CONVERGENCE = 4, /* more phases than the round cap (64 + 4*ceil(log2 n)) */
-  LC_ERR_TIMEOUT = 5         /* a bounded device-side wait gave up */
+  LC_ERR_TIMEOUT = 5,        /* a bounded device-side wait gave up */
+  LC_ERR_INTERNAL = 6        /* an internal index check failed (corrupted state; the
+                                offending access was skipped and reported on stderr) */
 } lc_status;
 
 typedef enum {
@@ -180,6 +182,39 @@ lc_status lc_kernel_stats(const lc_ctx* ctx, uint32_t k, const char** name, uint
 /* Release the context and all its device memory (stream-ordered frees after a
  * synchronisation of the context's stream).  NULL is accepted. */
 lc_status lc_destroy(lc_ctx* ctx);
+
+/* Serving: a request loop with continuous batching (no counterpart in the
+ * paper; it runs many independent LocalContraction jobs on one GPU).
+ * A worker thread admits submitted jobs in arrival order while a slot and the
+ * device-memory budget allow, keeps each job's contracted graph on the device
+ * between phases, and enqueues each job's next phase as soon as its previous
+ * one completes, so phases of different jobs interleave and overlap on the
+ * device (one CUDA stream per slot).  Idle contexts are kept and re-used for
+ * later jobs of equal or smaller size.
+ *   lc_server_create: budget_bytes = device bytes the server may hold
+ *     (0: 80% of the free memory now); slots = jobs running at once (1..1024).
+ *     Uses the current device.
+ *   lc_server_submit: n, host h_src/h_dst uint32[m], seed as in lc_create;
+ *     h_labels host uint32[n] receives the labels.  All three host arrays
+ *     must stay valid until lc_server_wait returns (pinned memory lets the
+ *     copies overlap).  *job receives an id.  LC_ERR_OOM if the job alone
+ *     exceeds the budget.
+ *   lc_server_wait: blocks until the job is done (or timeout_s seconds have
+ *     passed, if timeout_s > 0: LC_ERR_TIMEOUT, the job stays pending);
+ *     returns its status, its phase count and its latency (submission to
+ *     labels on the host) in seconds; then forgets the job.
+ *   lc_server_stats: jobs completed, the most jobs that ran at once, device
+ *     bytes held.
+ *   lc_server_destroy: finishes submitted jobs, then frees everything. */
+typedef struct lc_server lc_server;
+lc_status lc_server_create(uint64_t budget_bytes, uint32_t slots, lc_server** out);
+lc_status lc_server_submit(lc_server* s, uint32_t n, const uint32_t* h_src, const uint32_t* h_dst,
+                           uint64_t m, uint64_t seed, uint32_t* h_labels, uint64_t* job);
+lc_status lc_server_wait(lc_server* s, uint64_t job, double timeout_s, uint32_t* rounds,
+                         double* latency_s);
+lc_status lc_server_stats(lc_server* s, uint64_t* completed, uint64_t* peak_active,
+                          uint64_t* bytes_in_use);
+lc_status lc_server_destroy(lc_server* s);
 
 /* Allocation-free connected components for small graphs.  (The paper has no
  * counterpart; this entry point serves callers that must not allocate device

@@ -3,9 +3,14 @@
 // stream, one device synchronisation per phase to read the phase's sizes.
 #include <algorithm>
 #include <cstdio>
+#include <chrono>
+#include <condition_variable>
 #include <cstring>
+#include <deque>
 #include <mutex>
 #include <new>
+#include <thread>
+#include <unordered_map>
 #include <vector>
 
 #include "lc_internal.cuh"
@@ -212,6 +217,9 @@ struct lc_ctx {
   cudaEvent_t ev = nullptr;  // completion of the work enqueued last (none: sync the stream)
   RunState rs;
   BatchState* batch = nullptr;
+  uint64_t tag = 0;    // last value stamped into the device counters
+  uint32_t n_cap = 0;  // sizes the buffers were allocated for (a context may be
+  uint64_t m_cap = 0;  // re-bound to any smaller graph, see ctx_rebind)
 };
 
 #define LC_TRY(call)                                  \
@@ -256,17 +264,21 @@ static void free_ctx(lc_ctx* c) {
 
 static lc_status alloc_ctx(lc_ctx* c) {
   const uint64_t n = c->n, m = c->m;
+  c->n_cap = c->n;
+  c->m_cap = c->m;
   LC_TRY(cudaMalloc(&c->minkey, std::max<uint64_t>(n, 1) * 8));
   LC_TRY(cudaMalloc(&c->flags, ((n + 15) & ~15ull) + 16));
   LC_TRY(cudaMalloc(&c->ebuf[0], std::max<uint64_t>(m, 2) * 8));
   LC_TRY(cudaMalloc(&c->ebuf[1], std::max<uint64_t>(m, 2) * 8));
   LC_TRY(cudaMalloc(&c->ctr, sizeof(Counters)));
-  LC_TRY(cudaMemset(c->ctr, 0, sizeof(Counters)));
+  // initialisation is ordered on the context's stream, and lc_create waits
+  // for it, so the context may then be used from any stream
+  LC_TRY(cudaMemsetAsync(c->ctr, 0, sizeof(Counters), c->stream));
   LC_TRY(cudaMallocHost(&c->h_ctr, sizeof(Counters)));
   LC_TRY(cudaEventCreateWithFlags(&c->ev, cudaEventDisableTiming));
   c->sort.status_words = std::max(sort_status_words(m), sort_status_words(n));
   LC_TRY(cudaMalloc(&c->sort.status, c->sort.status_words * 8));
-  LC_TRY(cudaMemset(c->sort.status, 0, c->sort.status_words * 8));
+  LC_TRY(cudaMemsetAsync(c->sort.status, 0, c->sort.status_words * 8, c->stream));
   LC_TRY(cudaMalloc(&c->sort.hist, sizeof(uint32_t) * kMaxPasses * kRadixMax));
   LC_TRY(cudaMalloc(&c->sort.tickets, sizeof(unsigned) * 16));
   LC_TRY(cudaMalloc(&c->bounds, sizeof(uint32_t) * ((1ull << hash_bits_for(m)) + 1)));
@@ -310,6 +322,7 @@ extern "C" lc_status lc_create(uint32_t n, const uint32_t* d_src, const uint32_t
     c->src = c->own_src;
     c->dst = c->own_dst;
   }
+  if (st == LC_OK) st = status_of(cudaStreamSynchronize(c->stream));
   if (st != LC_OK) {
     free_ctx(c);
     cudaGetLastError();
@@ -389,7 +402,7 @@ static lc_status enqueue_phase(lc_ctx* c) {
   edge_min(i == 0 ? c->src : nullptr, i == 0 ? c->dst : nullptr, r.packed, mi, ni, rk, c->minkey,
            err, c->window_bytes, bp, L);
   // (c): roots of the parent arborescences
-  jump(c->minkey, r.lv.root, r.lv.mo, ni, L);
+  jump(c->minkey, r.lv.root, r.lv.mo, ni, err, L);
   // (d): relabel, drop loops, deduplicate, compact
   if (cudaMemsetAsync(c->ctr, 0, 4 * sizeof(unsigned long long), c->stream) != cudaSuccess ||
       cudaMemsetAsync(c->flags, 0, ni, c->stream) != cudaSuccess)
@@ -402,14 +415,14 @@ static lc_status enqueue_phase(lc_ctx* c) {
   relabel(i == 0 ? c->src : nullptr, i == 0 ? c->dst : nullptr, r.packed, mi, ni, r.lv.root,
           r.bits, r.keys, &c->ctr->mprime, &c->ctr->emitted, !c->dedup_sort,
           c->dedup_sort ? nullptr : &hplan, c->sort.hist, i == 0 ? r.alt : nullptr,
-          c->relabel_window_bytes, L);
+          c->relabel_window_bytes, err, L);
   if (!c->dedup_sort) {
     int which = hash_dedup(r.keys, r.alt, &c->ctr->emitted, mi, hplan, hb, true, r.bits, c->flags,
-                           c->bounds, &c->ctr->m_next, c->sort, err, L);
+                           ni, c->bounds, &c->ctr->m_next, c->sort, err, L);
     r.part = which ? r.alt : r.keys;
     r.next = which ? r.keys : r.alt;
     scan_flags(c->flags, r.lv.scan, ni, r.lv.mo, r.mo_next, &c->ctr->n_next, c->sort, err, L);
-    rename_edges(r.next, &c->ctr->m_next, mi, r.bits, r.lv.scan, L);
+    rename_edges(r.next, &c->ctr->m_next, mi, r.bits, r.lv.scan, ni, err, L);
     r.state = RunState::kPhase;
   } else {
     r.part = r.keys;
@@ -418,6 +431,7 @@ static lc_status enqueue_phase(lc_ctx* c) {
     lc_status st = enqueue_sort_dedup(c);
     if (st != LC_OK) return st;
   }
+  stamp_counters(c->ctr, ++c->tag, L);
   if (cudaMemcpyAsync(c->h_ctr, c->ctr, sizeof(Counters), cudaMemcpyDeviceToHost, c->stream) !=
       cudaSuccess)
     return fail(c, LC_ERR_CUDA);
@@ -437,8 +451,8 @@ static lc_status enqueue_sort_dedup(lc_ctx* c) {
   uint64_t* sorted = w2 ? r.next : r.part;
   r.next = w2 ? r.part : r.next;
   scan_flags(c->flags, r.lv.scan, r.ni, r.lv.mo, r.mo_next, &c->ctr->n_next, c->sort, err, L);
-  unique_rename(sorted, &c->ctr->emitted, r.mi, r.bits, r.lv.scan, r.next, &c->ctr->m_next,
-                c->sort, err, L);
+  unique_rename(sorted, &c->ctr->emitted, r.mi, r.bits, r.lv.scan, r.ni, r.next,
+                &c->ctr->m_next, c->sort, err, L);
   return LC_OK;
 }
 
@@ -449,10 +463,15 @@ static lc_status enqueue_labels(lc_ctx* c) {
   for (int i = (int)R - 1; i >= 0; --i) {
     const Level& lv = c->levels[i];
     const uint32_t* up = (i + 1 < (int)R) ? c->levels[i + 1].root : nullptr;
+    const uint32_t n_up = (i + 1 < (int)R) ? c->levels[i + 1].n : 0;
     uint32_t* out = i == 0 ? c->rs.d_labels : lv.root;
-    propagate(lv.root, lv.scan, lv.mo, up, out, lv.n, c->L);
+    propagate(lv.root, lv.scan, lv.mo, up, out, lv.n, n_up, &c->ctr->err, c->L);
   }
   if (c->batch) batch_localize(c->rs.d_labels, c->n, c->batch->d_voff0, c->batch->k, c->L);
+  stamp_counters(c->ctr, ++c->tag, c->L);
+  if (cudaMemcpyAsync(c->h_ctr, c->ctr, sizeof(Counters), cudaMemcpyDeviceToHost, c->stream) !=
+      cudaSuccess)
+    return fail(c, LC_ERR_CUDA);
   c->rs.state = RunState::kLabels;
   lc_status st = record(c);
   return st == LC_OK ? st : fail(c, st);
@@ -474,6 +493,7 @@ static lc_status run_begin(lc_ctx* c, uint32_t* d_labels) {
   if (c->m == 0) {
     identity_labels(d_labels, c->n, c->L);
     if (c->batch) batch_localize(d_labels, c->n, c->batch->d_voff0, c->batch->k, c->L);
+    c->h_ctr->err = 0;  // nothing below reads the device counters
     r.state = RunState::kLabels;
     lc_status st = record(c);
     return st == LC_OK ? st : fail(c, st);
@@ -502,16 +522,38 @@ static lc_status run_wait(lc_ctx* c) {
 }
 
 // Called once the work enqueued last has completed.
+static lc_status report_internal(lc_ctx* c, const char* what) {
+  const Counters& h = *c->h_ctr;
+  std::fprintf(stderr,
+               "liblc: %s: kernel %s index %llu limit %llu; phase %u of a graph with n = %u, "
+               "m = %llu; phase n_i %u m_i %llu; counters m' %llu emitted %llu m_next %llu "
+               "n_next %llu err %u tag %llu (expected %llu)\n",
+               what, h.bad_kernel ? kernel_name((int)h.bad_kernel - 1) : "-",
+               (unsigned long long)h.bad_index, (unsigned long long)h.bad_limit, c->rs.i, c->n,
+               (unsigned long long)c->m, c->rs.ni, (unsigned long long)c->rs.mi, h.mprime,
+               h.emitted, h.m_next, h.n_next, h.err, h.tag, (unsigned long long)c->tag);
+  return fail(c, LC_ERR_INTERNAL);
+}
+
+static lc_status report_corrupt(lc_ctx* c) {
+  return report_internal(c, "internal index check failed");
+}
+
 static lc_status run_complete(lc_ctx* c) {
   RunState& r = c->rs;
   c->prof.resolve();
   if (r.state == RunState::kLabels) {
+    // the label kernels report index failures through the device error word
+    if (c->h_ctr->tag != c->tag && c->m > 0) return report_internal(c, "stale counters");
+    if (c->h_ctr->err & kErrCorrupt) return report_corrupt(c);
     c->last_rounds = (uint32_t)c->levels.size();
     r.state = RunState::kDone;
     return LC_OK;
   }
   if (r.state != RunState::kPhase && r.state != RunState::kSortPhase) return r.st;
   const Counters& h = *c->h_ctr;
+  if (h.tag != c->tag) return report_internal(c, "stale counters");
+  if (h.err & kErrCorrupt) return report_corrupt(c);
   if (h.err & kErrBadVertex) return fail(c, LC_ERR_INVALID);
   if (h.err & kErrTimeout) return fail(c, LC_ERR_TIMEOUT);
   if (r.state == RunState::kPhase && (h.err & kErrOverflow)) {
@@ -527,12 +569,15 @@ static lc_status run_complete(lc_ctx* c) {
     r.state = RunState::kSortPhase;
     lc_status st = enqueue_sort_dedup(c);
     if (st != LC_OK) return st;
+    stamp_counters(c->ctr, ++c->tag, c->L);
     if (cudaMemcpyAsync(c->h_ctr, c->ctr, sizeof(Counters), cudaMemcpyDeviceToHost, c->stream) !=
         cudaSuccess)
       return fail(c, LC_ERR_CUDA);
     st = record(c);
     return st == LC_OK ? st : fail(c, st);
   }
+  if ((h.n_next > 0) != (h.m_next > 0) || h.n_next > r.ni || h.m_next > h.emitted)
+    return report_internal(c, "inconsistent phase counters");
   r.hn.push_back(r.ni);
   r.hm.push_back(r.mi);
   c->last_mp.push_back(h.mprime);
@@ -633,10 +678,14 @@ extern "C" lc_status lc_batch_create(uint32_t k, const uint32_t* h_n, const uint
   if (e == cudaSuccess) e = cudaMalloc(&b->d_voff0, 4ull * (k + 1));
   if (e == cudaSuccess) e = cudaMalloc(&b->d_eoff, 8ull * (k + 1));
   if (e == cudaSuccess) e = cudaMalloc(&b->d_rk, 8ull * k);
-  if (e == cudaSuccess) e = cudaMemcpy(b->d_seeds, h_seeds, 8ull * k, cudaMemcpyHostToDevice);
   if (e == cudaSuccess)
-    e = cudaMemcpy(b->d_voff0, voff.data(), 4ull * (k + 1), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(b->d_eoff, h_eoff, 8ull * (k + 1), cudaMemcpyHostToDevice);
+    e = cudaMemcpyAsync(b->d_seeds, h_seeds, 8ull * k, cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->d_voff0, voff.data(), 4ull * (k + 1), cudaMemcpyHostToDevice,
+                        c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->d_eoff, h_eoff, 8ull * (k + 1), cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   // level arrays of a batch: offsets and edge counts per graph per level
   if (e == cudaSuccess) e = c->arena.init(64ull * (2 * k + 2));
   if (e != cudaSuccess) {
@@ -665,8 +714,11 @@ extern "C" lc_status lc_batch_run(lc_ctx* c, uint32_t* d_labels, uint32_t* round
       voff = b->h_voff0;
       for (uint32_t gi = 0; gi < k; ++gi) mcnt[gi] = (uint32_t)(b->h_eoff[gi + 1] - b->h_eoff[gi]);
     } else {
-      LC_TRY(cudaMemcpy(voff.data(), b->voff[i], 4ull * (k + 1), cudaMemcpyDeviceToHost));
-      LC_TRY(cudaMemcpy(mcnt.data(), b->mcnt[i - 1], 4ull * k, cudaMemcpyDeviceToHost));
+      LC_TRY(cudaMemcpyAsync(voff.data(), b->voff[i], 4ull * (k + 1), cudaMemcpyDeviceToHost,
+                             c->stream));
+      LC_TRY(cudaMemcpyAsync(mcnt.data(), b->mcnt[i - 1], 4ull * k, cudaMemcpyDeviceToHost,
+                             c->stream));
+      LC_TRY(cudaStreamSynchronize(c->stream));
     }
     for (uint32_t gi = 0; gi < k; ++gi) {
       if (mcnt[gi] == 0) continue;  // graph finished before this phase
@@ -752,6 +804,7 @@ extern "C" const char* lc_status_str(lc_status s) {
     case LC_ERR_CUDA: return "CUDA runtime error";
     case LC_ERR_NO_CONVERGENCE: return "phase count exceeded the round cap";
     case LC_ERR_TIMEOUT: return "a bounded device wait gave up";
+    case LC_ERR_INTERNAL: return "internal consistency check failed";
   }
   return "unknown status";
 }
@@ -869,4 +922,346 @@ extern "C" lc_status lc_run_static(uint32_t n, const uint32_t* d_src, const uint
   st = run_loop(&c, d_labels, rounds, n_i, m_i, cap);
   c.arena.chunks.clear();  // nothing to free: all of it is the static array
   return st;
+}
+
+// ---------------------------------------------------------------------------
+// Serving: a request loop with continuous batching (native worker thread).
+//
+// Jobs (one graph each, host edge arrays) are admitted in arrival order while
+// the device-memory budget and the number of slots allow.  Each admitted job
+// gets a context (reused from a pool of idle contexts when one is large
+// enough, so steady-state admission allocates nothing) and its slot's CUDA
+// stream; its contracted graph stays on the device between phases.  The
+// worker polls every running job's last event and enqueues that job's next
+// phase as soon as the previous one completes, so phases of different jobs
+// interleave and overlap on the device, and jobs that arrive while others run
+// are admitted as soon as a slot and memory free up.
+
+namespace {
+
+// Device bytes of a context allocated for (n, m) with its own input buffers
+// (mirrors alloc_ctx and lc_create).
+uint64_t ctx_bytes(uint64_t n, uint64_t m) {
+  const uint64_t status = std::max(sort_status_words(m), sort_status_words(n)) * 8;
+  const uint64_t bounds = 4 * ((1ull << hash_bits_for(m)) + 1);
+  const uint64_t arena = 4 * std::max<uint64_t>(4 * (2 * n + 256), 1024);
+  return 8 * std::max<uint64_t>(n, 1) + n + 32 + 16 * std::max<uint64_t>(m, 2) + status +
+         bounds + arena + 8 * std::max<uint64_t>(m, 1) + 4 * std::max<uint64_t>(n, 1) +
+         sizeof(Counters) + 4096 + 16 * 4 + 4ull * kMaxPasses * kRadixMax + (1u << 16);
+}
+
+struct Job {
+  uint64_t id = 0;
+  uint32_t n = 0;
+  uint64_t m = 0, seed = 0;
+  const uint32_t *h_src = nullptr, *h_dst = nullptr;
+  uint32_t* h_labels = nullptr;
+  enum { kQueued, kRunning, kCopying, kDone } state = kQueued;
+  lc_status status = LC_OK;
+  uint32_t rounds = 0;
+  lc_ctx* ctx = nullptr;
+  int slot = -1;
+  std::chrono::steady_clock::time_point t_submit, t_done;
+};
+
+}  // namespace
+
+struct lc_server {
+  std::vector<lc_ctx*> in_use_ctx;  // contexts held by running jobs (consistency check)
+  int device = 0;
+  uint64_t budget = 0, in_use = 0;
+  std::vector<cudaStream_t> streams;
+  std::vector<int> free_slots;
+  std::vector<lc_ctx*> pool;  // idle contexts
+  std::deque<Job*> queue;
+  std::vector<Job*> active;
+  std::unordered_map<uint64_t, Job*> jobs;
+  uint64_t next_id = 1, completed = 0, peak_active = 0;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  bool stop = false;
+  std::thread worker;
+};
+
+// Re-bind an idle context (allocated with its own inputs for at least n
+// vertices and m edges) to a new graph of that size.
+static void ctx_rebind(lc_ctx* c, uint32_t n, uint64_t m, uint64_t seed, cudaStream_t stream) {
+  c->n = n;
+  c->m = m;
+  c->seed = seed;
+  c->stream = stream;
+  c->L.stream = stream;
+  c->src = c->own_src;
+  c->dst = c->own_dst;
+}
+
+static void finish_job(lc_server* s, Job* j, lc_status st) {
+  j->status = st;
+  j->state = Job::kDone;
+  j->t_done = std::chrono::steady_clock::now();
+  if (j->ctx) {
+    auto it = std::find(s->in_use_ctx.begin(), s->in_use_ctx.end(), j->ctx);
+    if (it != s->in_use_ctx.end()) s->in_use_ctx.erase(it);
+    if (std::find(s->pool.begin(), s->pool.end(), j->ctx) != s->pool.end())
+      std::fprintf(stderr, "liblc: server: context returned to the pool twice\n");
+    if (st == LC_OK || st == LC_ERR_INVALID || st == LC_ERR_NO_CONVERGENCE) {
+      s->pool.push_back(j->ctx);  // the context is intact: keep it for reuse
+    } else {
+      s->in_use -= ctx_bytes(j->ctx->n_cap, j->ctx->m_cap);
+      lc_destroy(j->ctx);
+    }
+    j->ctx = nullptr;
+  }
+  if (j->slot >= 0) s->free_slots.push_back(j->slot);
+  j->slot = -1;
+  ++s->completed;
+}
+
+// Admit queued jobs while a slot is free and their memory fits.  Called with
+// the lock held; returns whether anything was admitted.
+static bool admit(lc_server* s) {
+  bool any = false;
+  while (!s->queue.empty() && !s->free_slots.empty()) {
+    Job* j = s->queue.front();
+    // best-fitting idle context
+    int best = -1;
+    for (size_t q = 0; q < s->pool.size(); ++q) {
+      lc_ctx* c = s->pool[q];
+      if (c->n_cap >= j->n && c->m_cap >= j->m &&
+          (best < 0 || ctx_bytes(c->n_cap, c->m_cap) <
+                           ctx_bytes(s->pool[best]->n_cap, s->pool[best]->m_cap)))
+        best = (int)q;
+    }
+    lc_ctx* c = nullptr;
+    if (best >= 0) {
+      c = s->pool[best];
+      s->pool.erase(s->pool.begin() + best);
+    } else {
+      const uint64_t need = ctx_bytes(j->n, j->m);
+      // release idle contexts (largest first) until the new one fits
+      while (s->in_use + need > s->budget && !s->pool.empty()) {
+        auto it = std::max_element(s->pool.begin(), s->pool.end(), [](lc_ctx* a, lc_ctx* b) {
+          return ctx_bytes(a->n_cap, a->m_cap) < ctx_bytes(b->n_cap, b->m_cap);
+        });
+        s->in_use -= ctx_bytes((*it)->n_cap, (*it)->m_cap);
+        lc_destroy(*it);
+        s->pool.erase(it);
+      }
+      if (s->in_use + need > s->budget) break;  // wait for running jobs to free memory
+      lc_status st = lc_create(j->n, nullptr, nullptr, j->m, j->seed, nullptr, &c);
+      if (st != LC_OK) {
+        s->queue.pop_front();
+        finish_job(s, j, st);
+        any = true;
+        continue;
+      }
+      s->in_use += need;
+    }
+    s->queue.pop_front();
+    j->slot = s->free_slots.back();
+    s->free_slots.pop_back();
+    if (std::find(s->in_use_ctx.begin(), s->in_use_ctx.end(), c) != s->in_use_ctx.end())
+      std::fprintf(stderr, "liblc: server: context given to two running jobs\n");
+    s->in_use_ctx.push_back(c);
+    j->ctx = c;
+    ctx_rebind(c, j->n, j->m, j->seed, s->streams[j->slot]);
+    lc_status st = LC_OK;
+    if (j->m > 0) {
+      if (cudaMemcpyAsync(c->own_src, j->h_src, j->m * 4, cudaMemcpyHostToDevice, c->stream) !=
+              cudaSuccess ||
+          cudaMemcpyAsync(c->own_dst, j->h_dst, j->m * 4, cudaMemcpyHostToDevice, c->stream) !=
+              cudaSuccess)
+        st = LC_ERR_CUDA;
+    }
+    if (st == LC_OK) st = run_begin(c, c->own_labels);
+    if (st != LC_OK) {
+      finish_job(s, j, st);
+    } else {
+      j->state = Job::kRunning;
+      s->active.push_back(j);
+      s->peak_active = std::max<uint64_t>(s->peak_active, s->active.size());
+    }
+    any = true;
+  }
+  return any;
+}
+
+// Advance every running job whose last enqueued work has completed.  A CUDA
+// error while polling fails the job (LC_ERR_CUDA) instead of leaving it
+// running.
+static bool progress(lc_server* s) {
+  bool any = false;
+  for (size_t q = 0; q < s->active.size();) {
+    Job* j = s->active[q];
+    lc_ctx* c = j->ctx;
+    bool finished = false;
+    if (j->state == Job::kRunning) {
+      cudaError_t e = c->rs.state == RunState::kDone ? cudaSuccess : cudaEventQuery(c->ev);
+      if (e == cudaSuccess) {
+        lc_status st = c->rs.state == RunState::kDone ? c->rs.st : run_complete(c);
+        if (st != LC_OK) {
+          finish_job(s, j, st);
+          finished = true;
+        } else if (c->rs.state == RunState::kDone) {
+          j->rounds = c->last_rounds;
+          if (j->n > 0 &&
+              (cudaMemcpyAsync(j->h_labels, c->own_labels, (uint64_t)j->n * 4,
+                               cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+               cudaEventRecord(c->ev, c->stream) != cudaSuccess)) {
+            finish_job(s, j, LC_ERR_CUDA);
+            finished = true;
+          } else {
+            j->state = Job::kCopying;
+          }
+        }
+        any = true;
+      } else if (e != cudaErrorNotReady) {
+        finish_job(s, j, LC_ERR_CUDA);
+        finished = true;
+        any = true;
+      }
+    } else if (j->state == Job::kCopying) {
+      cudaError_t e = j->n == 0 ? cudaSuccess : cudaEventQuery(c->ev);
+      if (e != cudaErrorNotReady) {
+        finish_job(s, j, e == cudaSuccess ? LC_OK : LC_ERR_CUDA);
+        finished = true;
+        any = true;
+      }
+    }
+    if (finished) {
+      s->active.erase(s->active.begin() + q);
+    } else {
+      ++q;
+    }
+  }
+  return any;
+}
+
+static void serve(lc_server* s) {
+  cudaSetDevice(s->device);
+  std::unique_lock<std::mutex> lock(s->mu);
+  for (;;) {
+    if (s->stop && s->queue.empty() && s->active.empty()) break;
+    bool any = admit(s);
+    any = progress(s) || any;
+    if (any) s->cv_done.notify_all();
+    if (s->active.empty() && (s->queue.empty() || s->free_slots.empty())) {
+      s->cv_work.wait(lock);
+    } else if (!any) {
+      lock.unlock();
+      std::this_thread::sleep_for(std::chrono::microseconds(20));
+      lock.lock();
+    }
+  }
+}
+
+extern "C" lc_status lc_server_create(uint64_t budget_bytes, uint32_t slots, lc_server** out) {
+  if (!out || slots == 0 || slots > 1024) return LC_ERR_INVALID;
+  *out = nullptr;
+  lc_server* s = new (std::nothrow) lc_server();
+  if (!s) return LC_ERR_OOM;
+  if (cudaGetDevice(&s->device) != cudaSuccess) {
+    delete s;
+    return LC_ERR_CUDA;
+  }
+  if (budget_bytes == 0) {
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+      delete s;
+      return LC_ERR_CUDA;
+    }
+    budget_bytes = (uint64_t)(free_b * 0.8);
+  }
+  s->budget = budget_bytes;
+  for (uint32_t q = 0; q < slots; ++q) {
+    cudaStream_t st = nullptr;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+      for (auto x : s->streams) cudaStreamDestroy(x);
+      delete s;
+      return LC_ERR_CUDA;
+    }
+    s->streams.push_back(st);
+    s->free_slots.push_back((int)(slots - 1 - q));
+  }
+  s->worker = std::thread(serve, s);
+  *out = s;
+  return LC_OK;
+}
+
+extern "C" lc_status lc_server_submit(lc_server* s, uint32_t n, const uint32_t* h_src,
+                                      const uint32_t* h_dst, uint64_t m, uint64_t seed,
+                                      uint32_t* h_labels, uint64_t* job) {
+  if (!s || !job) return LC_ERR_INVALID;
+  if (m > 0xFFFFFFFFull || (n == 0 && m > 0)) return LC_ERR_INVALID;
+  if ((m > 0 && (!h_src || !h_dst)) || (n > 0 && !h_labels)) return LC_ERR_INVALID;
+  if (ctx_bytes(n, m) > s->budget) return LC_ERR_OOM;  // could never be admitted
+  Job* j = new (std::nothrow) Job();
+  if (!j) return LC_ERR_OOM;
+  j->n = n;
+  j->m = m;
+  j->seed = seed;
+  j->h_src = h_src;
+  j->h_dst = h_dst;
+  j->h_labels = h_labels;
+  j->t_submit = std::chrono::steady_clock::now();
+  {
+    std::lock_guard<std::mutex> lock(s->mu);
+    if (s->stop) {
+      delete j;
+      return LC_ERR_INVALID;
+    }
+    j->id = s->next_id++;
+    s->jobs[j->id] = j;
+    s->queue.push_back(j);
+    *job = j->id;
+  }
+  s->cv_work.notify_one();
+  return LC_OK;
+}
+
+extern "C" lc_status lc_server_wait(lc_server* s, uint64_t job, double timeout_s,
+                                    uint32_t* rounds, double* latency_s) {
+  if (!s) return LC_ERR_INVALID;
+  std::unique_lock<std::mutex> lock(s->mu);
+  auto it = s->jobs.find(job);
+  if (it == s->jobs.end()) return LC_ERR_INVALID;
+  Job* j = it->second;
+  auto done = [j] { return j->state == Job::kDone; };
+  if (timeout_s > 0) {
+    if (!s->cv_done.wait_for(lock, std::chrono::duration<double>(timeout_s), done))
+      return LC_ERR_TIMEOUT;  // the job stays known: wait again later
+  } else {
+    s->cv_done.wait(lock, done);
+  }
+  if (rounds) *rounds = j->rounds;
+  if (latency_s) *latency_s = std::chrono::duration<double>(j->t_done - j->t_submit).count();
+  lc_status st = j->status;
+  s->jobs.erase(it);
+  delete j;
+  return st;
+}
+
+extern "C" lc_status lc_server_stats(lc_server* s, uint64_t* completed, uint64_t* peak_active,
+                                     uint64_t* bytes_in_use) {
+  if (!s) return LC_ERR_INVALID;
+  std::lock_guard<std::mutex> lock(s->mu);
+  if (completed) *completed = s->completed;
+  if (peak_active) *peak_active = s->peak_active;
+  if (bytes_in_use) *bytes_in_use = s->in_use;
+  return LC_OK;
+}
+
+extern "C" lc_status lc_server_destroy(lc_server* s) {
+  if (!s) return LC_OK;
+  {
+    std::lock_guard<std::mutex> lock(s->mu);
+    s->stop = true;
+  }
+  s->cv_work.notify_all();
+  if (s->worker.joinable()) s->worker.join();
+  for (auto& kv : s->jobs) delete kv.second;
+  for (auto c : s->pool) lc_destroy(c);
+  for (auto x : s->streams) cudaStreamDestroy(x);
+  delete s;
+  return LC_OK;
 }

@@ -1,5 +1,6 @@
 // Device-side building blocks shared by the LocalContraction kernels.
 #pragma once
+#include <cstddef>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -32,6 +33,7 @@ enum : uint32_t {
   kErrBadVertex = 1u,  // an input endpoint was >= n
   kErrTimeout = 2u,    // a bounded spin-wait gave up
   kErrOverflow = 4u,   // a dedup bucket held more distinct keys than its table
+  kErrCorrupt = 8u,    // a data-dependent index was out of range (access skipped)
 };
 
 // Bijective mixer of an edge key (xorshift-multiply rounds).  The hashed
@@ -84,8 +86,29 @@ struct Counters {
   unsigned long long n_next;   // surviving nodes (n_{i+1})
   unsigned long long emitted;  // keys written by relabel (m'_i minus repeats it dropped)
   unsigned int err;            // kErr* bits
-  unsigned int pad;
+  unsigned int bad_kernel;     // 1 + kernel id of the first failed index check
+  unsigned long long bad_index;
+  unsigned long long bad_limit;
+  unsigned long long tag;      // stamped by the last kernel of a phase (see run_complete)
 };
+static_assert(offsetof(Counters, bad_kernel) == offsetof(Counters, err) + 4, "layout");
+static_assert(offsetof(Counters, bad_index) == offsetof(Counters, err) + 8, "layout");
+static_assert(offsetof(Counters, bad_limit) == offsetof(Counters, err) + 16, "layout");
+
+// Index check of a data-dependent access: false (and the first failure
+// recorded next to the error word, see Counters) when idx >= limit.  Kernels
+// skip the access when it fails, so corrupted data gives an error status, not
+// a memory fault.
+__device__ __forceinline__ bool index_ok(unsigned* err, uint32_t kernel, uint64_t idx,
+                                         uint64_t limit) {
+  if (idx < limit) return true;
+  atomicOr(err, kErrCorrupt);
+  if (atomicCAS(err + 1, 0u, kernel + 1) == 0u) {
+    reinterpret_cast<unsigned long long*>(err + 2)[0] = idx;
+    reinterpret_cast<unsigned long long*>(err + 2)[1] = limit;
+  }
+  return false;
+}
 
 __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
 

@@ -168,13 +168,14 @@ void hist_reset(SortScratch& s, const Launch& L);
 // `bounds` holds (1 << hb) + 1 words.
 int hash_dedup(uint64_t* keys, uint64_t* alt, const unsigned long long* d_count,
                uint64_t max_count, const PassPlan& plan, int hb, bool hist_ready,
-               int half_bits, uint8_t* flags, uint32_t* bounds, unsigned long long* m_next,
-               SortScratch& s, unsigned* err, const Launch& L);
+               int half_bits, uint8_t* flags, uint32_t n, uint32_t* bounds,
+               unsigned long long* m_next, SortScratch& s, unsigned* err, const Launch& L);
 
 // e[j] = (newid[a] << 32 | newid[b]) for each mixed key
 // e[j] = key_mix(a << half_bits | b), j < *d_count.
 void rename_edges(uint64_t* e, const unsigned long long* d_count, uint64_t max_count,
-                  int half_bits, const uint32_t* newid, const Launch& L);
+                  int half_bits, const uint32_t* newid, uint32_t n, unsigned* err,
+                  const Launch& L);
 
 // In place: e[j] = key_unmix(e[j]) for j < *d_count.
 void unmix_keys(uint64_t* e, const unsigned long long* d_count, uint64_t max_count,
@@ -191,7 +192,7 @@ void scan_flags(const uint8_t* flags, uint32_t* out, uint32_t n, const uint32_t*
 // of equal keys and writes it renamed through newid as (newid[a] << 32 |
 // newid[b]) to out in sorted order; *m_next gets the number kept.
 void unique_rename(const uint64_t* keys, const unsigned long long* d_count, uint64_t max_count,
-                   int half_bits, const uint32_t* newid, uint64_t* out,
+                   int half_bits, const uint32_t* newid, uint32_t n, uint64_t* out,
                    unsigned long long* m_next, SortScratch& s, unsigned* err, const Launch& L);
 
 // ---------------------------------------------------------- phase steps
@@ -236,7 +237,10 @@ void batch_localize(uint32_t* labels, uint32_t n, const uint32_t* voff, uint32_t
 // root[v] = root of v's arborescence (follows the parent stored in the low
 // half of minkey, compressing as it goes); mo[root] = min over the tree of
 // mo[v] (phase 0: mo[v] = v).
-void jump(unsigned long long* minkey, uint32_t* root, uint32_t* mo, uint32_t n, const Launch& L);
+// A chase longer than n steps (only possible with corrupted data) stops and
+// sets kErrTimeout.
+void jump(unsigned long long* minkey, uint32_t* root, uint32_t* mo, uint32_t n, unsigned* err,
+          const Launch& L);
 
 // Relabel every edge through root, drop self-loops, emit (min << bits | max)
 // keys (mixed with key_mix when `mix`) compacted to keys_out.  With `plan`
@@ -251,12 +255,18 @@ void relabel(const uint32_t* src, const uint32_t* dst, const uint64_t* packed, u
              uint32_t n, const uint32_t* root, int bits, uint64_t* keys_out,
              unsigned long long* mprime, unsigned long long* emitted, bool mix,
              const PassPlan* plan, uint32_t* ghist, uint64_t* tmp, uint64_t window_bytes,
-             const Launch& L);
+             unsigned* err, const Launch& L);
 
 // labels_out[v] = kept(root[v]) ? labels_up[scan[root[v]]] : mo[root[v]], with
 // kept(r) = scan[r+1] > scan[r].  labels_out may alias root.
 void propagate(const uint32_t* root, const uint32_t* scan, const uint32_t* mo,
-               const uint32_t* labels_up, uint32_t* labels_out, uint32_t n, const Launch& L);
+               const uint32_t* labels_up, uint32_t* labels_out, uint32_t n, uint32_t n_up,
+               unsigned* err, const Launch& L);
+
+// ctr->tag = tag, ordered after everything enqueued before it on the stream
+// (lets the host check that the counters it reads belong to the phase it
+// expects).
+void stamp_counters(Counters* ctr, uint64_t tag, const Launch& L);
 
 // labels[v] = v (a graph without edges).
 void identity_labels(uint32_t* labels, uint32_t n, const Launch& L);

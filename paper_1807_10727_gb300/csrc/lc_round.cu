@@ -131,8 +131,10 @@ __global__ void __launch_bounds__(kThreads) k_edge_min_soa(
 // min_edge_window).
 template <class K>
 __device__ __forceinline__ void min_edge_packed(uint64_t x, const K& keys,
-                                                unsigned long long* minkey) {
+                                                unsigned long long* minkey, uint32_t n,
+                                                unsigned* err) {
   const uint32_t a = (uint32_t)(x >> 32), b = (uint32_t)x;
+  if (!index_ok(err, kKEdgeMinPacked, max(a, b), n)) return;
   uint64_t ka, kb;
   keys.pair(a, b, ka, kb);
   if (ka < kb) atomicMin(&minkey[b], (unsigned long long)ka);
@@ -142,17 +144,18 @@ __device__ __forceinline__ void min_edge_packed(uint64_t x, const K& keys,
 // Packed edges (a << 32 | b), two per 128-bit load.
 template <class K>
 __global__ void __launch_bounds__(kThreads) k_edge_min_packed(
-    const uint64_t* __restrict__ e, uint64_t m, K keys, unsigned long long* minkey) {
+    const uint64_t* __restrict__ e, uint64_t m, K keys, unsigned long long* minkey, uint32_t n,
+    unsigned* err) {
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   const uint64_t npair = m / 2;
   const ulonglong2* e2 = reinterpret_cast<const ulonglong2*>(e);
   const uint64_t gt = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   for (uint64_t q = gt; q < npair; q += stride) {
     ulonglong2 p = __ldcs(e2 + q);
-    min_edge_packed(p.x, keys, minkey);
-    min_edge_packed(p.y, keys, minkey);
+    min_edge_packed(p.x, keys, minkey, n, err);
+    min_edge_packed(p.y, keys, minkey, n, err);
   }
-  if ((m & 1) && gt == 0) min_edge_packed(e[m - 1], keys, minkey);
+  if ((m & 1) && gt == 0) min_edge_packed(e[m - 1], keys, minkey, n, err);
 }
 
 // ------------------------------------------------------- batches
@@ -224,16 +227,24 @@ __global__ void k_batch_localize(uint32_t* __restrict__ labels, uint32_t n,
 
 __global__ void __launch_bounds__(kThreads) k_jump(unsigned long long* minkey,
                                                    uint32_t* __restrict__ root,
-                                                   uint32_t* mo, uint32_t n) {
+                                                   uint32_t* mo, uint32_t n, unsigned* err) {
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
     uint32_t p = (uint32_t)minkey[v];
+    if (!index_ok(err, kKJump, p, n)) {
+      root[v] = (uint32_t)v;
+      continue;
+    }
     if (p != (uint32_t)v) {
       // every stored pointer leads to an ancestor, so chasing ends at the
-      // root (the only vertex whose stored pointer is itself)
+      // root (the only vertex whose stored pointer is itself) within n steps;
+      // the checks only guard against corrupted data
+      uint32_t steps = 0;
       for (;;) {
         uint32_t q = (uint32_t)minkey[p];
         if (q == p) break;
+        if (!index_ok(err, kKJump, q, n) || !index_ok(err, kKJump, ++steps, (uint64_t)n + 1))
+          break;
         p = q;
       }
       minkey[v] = p;  // compress: later chases through v go straight to the root
@@ -300,7 +311,8 @@ __global__ void __launch_bounds__(kThreads) k_relabel(
     const uint32_t* __restrict__ src, const uint32_t* __restrict__ dst,
     const uint64_t* __restrict__ packed, uint64_t m, uint32_t n, const uint32_t* __restrict__ root,
     int bits, uint64_t* __restrict__ keys_out, unsigned long long* mprime,
-    unsigned long long* emitted, int mix, PassPlan plan, uint32_t* __restrict__ ghist) {
+    unsigned long long* emitted, int mix, PassPlan plan, uint32_t* __restrict__ ghist,
+    unsigned* mprime_err) {
   __shared__ uint64_t cache[kRelCache];
   __shared__ uint32_t hist[3][kRadixMax];
   __shared__ uint32_t ws[kThreads / 32];
@@ -334,9 +346,15 @@ __global__ void __launch_bounds__(kThreads) k_relabel(
       }
       bool keep;
       key[i] = 0;
+      if (kMode == 1 && valid &&
+          !index_ok(mprime_err, kKRelabelPacked, max(u, v), n))
+        valid = false;
       if (kMode == 2) {
-        uint32_t a = (u & kResolved) ? (u & ~kResolved) : __ldg(root + u);
-        uint32_t b = (v & kResolved) ? (v & ~kResolved) : __ldg(root + v);
+        if (valid && (!index_ok(mprime_err, kKRelabelSoa, (u & kResolved) ? 0u : u, n) ||
+                      !index_ok(mprime_err, kKRelabelSoa, (v & kResolved) ? 0u : v, n)))
+          valid = false;
+        uint32_t a = !valid ? 0u : (u & kResolved) ? (u & ~kResolved) : __ldg(root + u);
+        uint32_t b = !valid ? 0u : (v & kResolved) ? (v & ~kResolved) : __ldg(root + v);
         keep = valid && a != b;
         if (keep) key[i] = ((uint64_t)min(a, b) << bits) | max(a, b);
       } else {
@@ -402,14 +420,25 @@ __global__ void __launch_bounds__(kThreads) k_propagate(const uint32_t* root,
                                                         const uint32_t* __restrict__ scan,
                                                         const uint32_t* __restrict__ mo,
                                                         const uint32_t* __restrict__ labels_up,
-                                                        uint32_t* labels_out, uint32_t n) {
+                                                        uint32_t* labels_out, uint32_t n,
+                                                        uint32_t n_up, unsigned* err) {
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
     uint32_t r = root[v];
+    if (!index_ok(err, kKPropagate, r, n)) {
+      labels_out[v] = (uint32_t)v;
+      continue;
+    }
     uint32_t s0 = scan[r], s1 = scan[r + 1];
+    if (s1 > s0 && !index_ok(err, kKPropagate, s0, n_up)) {
+      labels_out[v] = (uint32_t)v;
+      continue;
+    }
     labels_out[v] = s1 > s0 ? labels_up[s0] : mo[r];
   }
 }
+
+__global__ void k_stamp(Counters* ctr, unsigned long long tag) { ctr->tag = tag; }
 
 __global__ void k_identity(uint32_t* labels, uint32_t n) {
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
@@ -436,8 +465,8 @@ static void edge_min_impl(const uint32_t* src, const uint32_t* dst, const uint64
                           unsigned* err, uint64_t window_bytes, const Launch& L) {
   if (packed != nullptr) {
     KScope ks(L, kKEdgeMinPacked);
-    k_edge_min_packed<<<grid_for(m / 2 + 1, kThreads, L), kThreads, 0, L.stream>>>(packed, m,
-                                                                                   keys, minkey);
+    k_edge_min_packed<<<grid_for(m / 2 + 1, kThreads, L), kThreads, 0, L.stream>>>(
+        packed, m, keys, minkey, n, err);
   } else {
     int vec = ((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst)) & 15) == 0;
     // vertex windows whose minkey slices fit the L2 budget; one pass each
@@ -498,17 +527,18 @@ void batch_localize(uint32_t* labels, uint32_t n, const uint32_t* voff, uint32_t
   k_batch_localize<<<grid_for(n, kThreads, L), kThreads, 0, L.stream>>>(labels, n, voff, k);
 }
 
-void jump(unsigned long long* minkey, uint32_t* root, uint32_t* mo, uint32_t n, const Launch& L) {
+void jump(unsigned long long* minkey, uint32_t* root, uint32_t* mo, uint32_t n, unsigned* err,
+          const Launch& L) {
   if (n == 0) return;
   KScope ks(L, kKJump);
-  k_jump<<<grid_for(n, kThreads, L), kThreads, 0, L.stream>>>(minkey, root, mo, n);
+  k_jump<<<grid_for(n, kThreads, L), kThreads, 0, L.stream>>>(minkey, root, mo, n, err);
 }
 
 void relabel(const uint32_t* src, const uint32_t* dst, const uint64_t* packed, uint64_t m,
              uint32_t n, const uint32_t* root, int bits, uint64_t* keys_out,
              unsigned long long* mprime, unsigned long long* emitted, bool mix,
              const PassPlan* plan, uint32_t* ghist, uint64_t* tmp, uint64_t window_bytes,
-             const Launch& L) {
+             unsigned* err, const Launch& L) {
   PassPlan pl{};
   if (plan != nullptr) pl = *plan;  // passes == 0: no histogram
   if (m == 0) return;
@@ -516,7 +546,8 @@ void relabel(const uint32_t* src, const uint32_t* dst, const uint64_t* packed, u
   if (packed != nullptr) {
     KScope ks(L, kKRelabelPacked);
     k_relabel<1><<<grid, kThreads, 0, L.stream>>>(nullptr, nullptr, packed, m, n, root, bits,
-                                                  keys_out, mprime, emitted, mix, pl, ghist);
+                                                  keys_out, mprime, emitted, mix, pl, ghist,
+                                                  err);
   } else if (tmp != nullptr && n < kResolved && (uint64_t)n * 4 > window_bytes) {
     // two passes, each gathering from one half of root (see k_relabel_first_half)
     const uint32_t split = n / 2;
@@ -527,20 +558,27 @@ void relabel(const uint32_t* src, const uint32_t* dst, const uint64_t* packed, u
     }
     KScope ks(L, kKRelabelSoa);
     k_relabel<2><<<grid, kThreads, 0, L.stream>>>(nullptr, nullptr, tmp, m, n, root, bits,
-                                                  keys_out, mprime, emitted, mix, pl, ghist);
+                                                  keys_out, mprime, emitted, mix, pl, ghist,
+                                                  err);
   } else {
     KScope ks(L, kKRelabelSoa);
     k_relabel<0><<<grid, kThreads, 0, L.stream>>>(src, dst, nullptr, m, n, root, bits, keys_out,
-                                                  mprime, emitted, mix, pl, ghist);
+                                                  mprime, emitted, mix, pl, ghist, err);
   }
 }
 
 void propagate(const uint32_t* root, const uint32_t* scan, const uint32_t* mo,
-               const uint32_t* labels_up, uint32_t* labels_out, uint32_t n, const Launch& L) {
+               const uint32_t* labels_up, uint32_t* labels_out, uint32_t n, uint32_t n_up,
+               unsigned* err, const Launch& L) {
   if (n == 0) return;
   KScope ks(L, kKPropagate);
   k_propagate<<<grid_for(n, kThreads, L), kThreads, 0, L.stream>>>(root, scan, mo, labels_up,
-                                                                   labels_out, n);
+                                                                   labels_out, n, n_up, err);
+}
+
+void stamp_counters(Counters* ctr, uint64_t tag, const Launch& L) {
+  KScope ks(L, kKBatch);
+  k_stamp<<<1, 1, 0, L.stream>>>(ctr, tag);
 }
 
 void identity_labels(uint32_t* labels, uint32_t n, const Launch& L) {

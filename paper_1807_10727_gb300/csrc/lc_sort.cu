@@ -294,7 +294,10 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_sort_pass(
   // stage the tile in digit order
 #pragma unroll
   for (int i = 0; i < kSortItems; ++i) {
-    if (wbase + i * 32 + lane < nvalid) sk[whist[w][dg(k[i])] + off[i]] = k[i];
+    if (wbase + i * 32 + lane < nvalid) {
+      const uint32_t at = whist[w][dg(k[i])] + off[i];
+      if (index_ok(err, kKSortPass, at, nvalid)) sk[at] = k[i];
+    }
   }
   __syncthreads();
 
@@ -357,8 +360,8 @@ __device__ __forceinline__ void set_insert(uint64_t* table, uint64_t key, int* o
 // t, t + 256, ... when collecting, so the scan is free of bank conflicts.
 __global__ void __launch_bounds__(kSortThreads) k_bucket_dedup(
     const uint64_t* __restrict__ keys, const uint32_t* __restrict__ bounds, uint32_t nb,
-    uint64_t* __restrict__ out, unsigned long long* m_next, uint8_t* flags, int half_bits,
-    unsigned* ticket, unsigned* err) {
+    uint64_t* __restrict__ out, uint64_t cap, unsigned long long* m_next, uint8_t* flags,
+    uint32_t n, int half_bits, unsigned* ticket, unsigned* err) {
   extern __shared__ __align__(16) uint64_t table[];  // [kTableSlots]
   __shared__ uint32_t ws[kWarps];
   __shared__ uint32_t s_b;
@@ -406,10 +409,14 @@ __global__ void __launch_bounds__(kSortThreads) k_bucket_dedup(
     for (int s = 0; s < kPer; ++s) {
       uint64_t v = table[s * kSortThreads + tid];
       if (v != kEmpty) {
-        out[pos++] = v;
+        if (index_ok(err, kKBucketDedup, pos, cap)) out[pos] = v;
+        ++pos;
         uint64_t k = key_unmix(v);
-        flags[k >> half_bits] = 1;
-        flags[k & half_mask] = 1;
+        const uint64_t a = k >> half_bits, b = k & half_mask;
+        if (index_ok(err, kKBucketDedup, a > b ? a : b, n)) {
+          flags[a] = 1;
+          flags[b] = 1;
+        }
         table[s * kSortThreads + tid] = kEmpty;
       }
     }
@@ -419,13 +426,17 @@ __global__ void __launch_bounds__(kSortThreads) k_bucket_dedup(
 
 // e[j] = (newid[a] << 32 | newid[b]) for e[j] = key_mix(a << half_bits | b).
 __global__ void k_rename(uint64_t* __restrict__ e, const unsigned long long* d_count,
-                         int half_bits, const uint32_t* __restrict__ newid) {
+                         uint64_t cap, int half_bits, const uint32_t* __restrict__ newid,
+                         uint32_t n, unsigned* err) {
   const uint64_t count = *d_count;
+  if (!index_ok(err, kKRename, count, cap + 1)) return;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   const uint64_t half_mask = (1ull << half_bits) - 1;
   for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < count; j += stride) {
     uint64_t k = key_unmix(e[j]);
-    e[j] = ((uint64_t)newid[k >> half_bits] << 32) | newid[k & half_mask];
+    const uint64_t a = k >> half_bits, b = k & half_mask;
+    if (!index_ok(err, kKRename, a > b ? a : b, n)) continue;
+    e[j] = ((uint64_t)newid[a] << 32) | newid[b];
   }
 }
 
@@ -500,8 +511,9 @@ __global__ void __launch_bounds__(kSortThreads) k_scan_flags(
 
 __global__ void __launch_bounds__(kSortThreads) k_unique_rename(
     const uint64_t* __restrict__ keys, const unsigned long long* d_count, int half_bits,
-    const uint32_t* __restrict__ newid, uint64_t* __restrict__ out, unsigned long long* m_next,
-    uint64_t* status, uint32_t epoch, unsigned* ticket, unsigned* err) {
+    const uint32_t* __restrict__ newid, uint32_t n, uint64_t* __restrict__ out,
+    unsigned long long* m_next, uint64_t* status, uint32_t epoch, unsigned* ticket,
+    unsigned* err) {
   __shared__ uint32_t ws[kWarps];
   __shared__ uint32_t s_tile, s_excl;
   const unsigned tid = threadIdx.x;
@@ -543,9 +555,13 @@ __global__ void __launch_bounds__(kSortThreads) k_unique_rename(
 #pragma unroll
   for (int i = 0; i < kScanItems; ++i) {
     if (fl & (1u << i)) {
-      uint32_t a = newid[k[i] >> half_bits];
-      uint32_t b = newid[k[i] & half_mask];
-      out[pos++] = ((uint64_t)a << 32) | b;
+      const uint64_t ka = k[i] >> half_bits, kb = k[i] & half_mask;
+      if (index_ok(err, kKUniqueRename, ka > kb ? ka : kb, n)) {
+        uint32_t a = newid[ka];
+        uint32_t b = newid[kb];
+        out[pos] = ((uint64_t)a << 32) | b;
+      }
+      ++pos;
     }
   }
   if (base + kScanTile >= count && tid == 0) *m_next = (unsigned long long)s_excl + tile_total;
@@ -656,8 +672,8 @@ int hash_plan(uint64_t max_count, PassPlan* plan) {
 
 int hash_dedup(uint64_t* keys, uint64_t* alt, const unsigned long long* d_count,
                uint64_t max_count, const PassPlan& plan, int hb, bool hist_ready,
-               int half_bits, uint8_t* flags, uint32_t* bounds, unsigned long long* m_next,
-               SortScratch& s, unsigned* err, const Launch& L) {
+               int half_bits, uint8_t* flags, uint32_t n, uint32_t* bounds,
+               unsigned long long* m_next, SortScratch& s, unsigned* err, const Launch& L) {
   if (max_count == 0) return 0;
   int which =
       run_passes(keys, alt, d_count, max_count, plan, hist_ready, s, err, nullptr, half_bits, L);
@@ -674,9 +690,8 @@ int hash_dedup(uint64_t* keys, uint64_t* alt, const unsigned long long* d_count,
     KScope ks(L, kKBucketDedup);
     set_smem_limits();
     int g = (int)std::min<uint64_t>(nb, (uint64_t)L.sms * 6);
-    k_bucket_dedup<<<g, kSortThreads, dedup_smem(), L.stream>>>(part, bounds, nb, out, m_next,
-                                                                flags, half_bits, s.tickets + 10,
-                                                                err);
+    k_bucket_dedup<<<g, kSortThreads, dedup_smem(), L.stream>>>(
+        part, bounds, nb, out, max_count, m_next, flags, n, half_bits, s.tickets + 10, err);
   }
   return which;  // keys partitioned in `part` (0: keys, 1: alt); distinct keys in the other
 }
@@ -690,11 +705,12 @@ void unmix_keys(uint64_t* e, const unsigned long long* d_count, uint64_t max_cou
 }
 
 void rename_edges(uint64_t* e, const unsigned long long* d_count, uint64_t max_count,
-                  int half_bits, const uint32_t* newid, const Launch& L) {
+                  int half_bits, const uint32_t* newid, uint32_t n, unsigned* err,
+                  const Launch& L) {
   if (max_count == 0) return;
   KScope ks(L, kKRename);
   int g = (int)std::min<uint64_t>((max_count + 255) / 256, (uint64_t)L.sms * 8);
-  k_rename<<<g, 256, 0, L.stream>>>(e, d_count, half_bits, newid);
+  k_rename<<<g, 256, 0, L.stream>>>(e, d_count, max_count, half_bits, newid, n, err);
 }
 
 void scan_flags(const uint8_t* flags, uint32_t* out, uint32_t n, const uint32_t* mo_in,
@@ -710,7 +726,7 @@ void scan_flags(const uint8_t* flags, uint32_t* out, uint32_t n, const uint32_t*
 }
 
 void unique_rename(const uint64_t* keys, const unsigned long long* d_count, uint64_t max_count,
-                   int half_bits, const uint32_t* newid, uint64_t* out,
+                   int half_bits, const uint32_t* newid, uint32_t n, uint64_t* out,
                    unsigned long long* m_next, SortScratch& s, unsigned* err, const Launch& L) {
   if (max_count == 0) return;
   uint32_t epoch = next_epoch(s, L);
@@ -718,7 +734,7 @@ void unique_rename(const uint64_t* keys, const unsigned long long* d_count, uint
   uint64_t tiles = (max_count + kScanTile - 1) / kScanTile;
   KScope ks(L, kKUniqueRename);
   k_unique_rename<<<(unsigned)tiles, kSortThreads, 0, L.stream>>>(
-      keys, d_count, half_bits, newid, out, m_next, s.status, epoch, s.tickets + 9, err);
+      keys, d_count, half_bits, newid, n, out, m_next, s.status, epoch, s.tickets + 9, err);
 }
 
 }  // namespace lc

@@ -18,14 +18,17 @@ import numpy as np
 
 from . import _build
 
-LC_OK, LC_ERR_INVALID, LC_ERR_OOM, LC_ERR_CUDA, LC_ERR_NO_CONVERGENCE, LC_ERR_TIMEOUT = range(6)
+(LC_OK, LC_ERR_INVALID, LC_ERR_OOM, LC_ERR_CUDA, LC_ERR_NO_CONVERGENCE, LC_ERR_TIMEOUT,
+ LC_ERR_INTERNAL) = range(7)
 LC_VARIANT_FOREST, LC_VARIANT_TWO_HOP, LC_VARIANT_TREE = 0, 1, 2
 
 # every symbol include/lc.h declares (checked by the CPU test suite)
 LC_DEDUP_HASH, LC_DEDUP_SORT = 0, 1
 EXPORTED = ("lc_create", "lc_configure", "lc_set_dedup", "lc_set_param", "lc_run", "lc_run_host",
             "lc_last_stats", "lc_profile", "lc_kernel_stats", "lc_destroy", "lc_status_str",
-            "lc_rank_probe", "lc_run_static", "lc_batch_create", "lc_batch_run")
+            "lc_rank_probe", "lc_run_static", "lc_batch_create", "lc_batch_run",
+            "lc_server_create", "lc_server_submit", "lc_server_wait", "lc_server_stats",
+            "lc_server_destroy")
 LC_STATIC_MAX_N, LC_STATIC_MAX_M = 131072, 524288
 
 _lib = None
@@ -65,6 +68,11 @@ def load(path: str | None = None):
     lib.lc_run_static.argtypes = [u32, p, p, u64, u64, p, p, pu32, pu64, pu64, u32]
     lib.lc_batch_create.argtypes = [u32, p, p, p, p, p, p, ctypes.POINTER(p)]
     lib.lc_batch_run.argtypes = [p, p, p, p, p, u32]
+    lib.lc_server_create.argtypes = [u64, u32, ctypes.POINTER(p)]
+    lib.lc_server_submit.argtypes = [p, u32, p, p, u64, u64, p, pu64]
+    lib.lc_server_wait.argtypes = [p, u64, ctypes.c_double, pu32, ctypes.POINTER(ctypes.c_double)]
+    lib.lc_server_stats.argtypes = [p, pu64, pu64, pu64]
+    lib.lc_server_destroy.argtypes = [p]
     for name in EXPORTED:
         if name != "lc_status_str":
             getattr(lib, name).restype = i32
@@ -327,6 +335,62 @@ class BatchLocalContraction:
         if getattr(self, "ctx", None):
             lc_destroy(self.ctx)
             self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching request loop (see lc_server_* in include/lc.h).
+
+    submit() takes host uint32 arrays (kept alive until wait() returns; pinned
+    memory lets the copies overlap) and returns a job id; wait(id) returns
+    (labels, rounds, latency_s)."""
+
+    def __init__(self, budget_bytes: int = 0, slots: int = 32):
+        out = ctypes.c_void_p()
+        _check(load().lc_server_create(budget_bytes, slots, ctypes.byref(out)), "lc_server_create")
+        self.srv = out.value
+        self._held = {}
+
+    def submit(self, n: int, h_src: np.ndarray, h_dst: np.ndarray, seed: int = 0,
+               h_labels: np.ndarray | None = None) -> int:
+        m = int(h_src.size)
+        for a in (h_src, h_dst):
+            if a.dtype != np.uint32 or not a.flags.c_contiguous or a.size != m:
+                raise ValueError("host edges must be contiguous uint32 arrays of equal length")
+        if h_labels is None:
+            h_labels = np.empty(max(n, 1), dtype=np.uint32)
+        job = ctypes.c_uint64()
+        _check(load().lc_server_submit(self.srv, n, h_src.ctypes.data if m else 0,
+                                       h_dst.ctypes.data if m else 0, m, seed,
+                                       h_labels.ctypes.data, ctypes.byref(job)), "lc_server_submit")
+        self._held[job.value] = (h_src, h_dst, h_labels, n)
+        return job.value
+
+    def wait(self, job: int, timeout_s: float = 0.0):
+        R = ctypes.c_uint32()
+        lat = ctypes.c_double()
+        st = load().lc_server_wait(self.srv, job, timeout_s, ctypes.byref(R), ctypes.byref(lat))
+        if st == LC_ERR_TIMEOUT:
+            raise LCError(st, "lc_server_wait")  # still pending: may be waited on again
+        h_src, h_dst, h_labels, n = self._held.pop(job)
+        _check(st, "lc_server_wait")
+        return h_labels[:n], int(R.value), float(lat.value)
+
+    def stats(self) -> dict:
+        c, p, b = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+        _check(load().lc_server_stats(self.srv, ctypes.byref(c), ctypes.byref(p), ctypes.byref(b)),
+               "lc_server_stats")
+        return {"completed": c.value, "peak_active": p.value, "bytes_in_use": b.value}
+
+    def close(self) -> None:
+        if getattr(self, "srv", None):
+            load().lc_server_destroy(self.srv)
+            self.srv = None
 
     def __del__(self):
         try:
