@@ -189,32 +189,49 @@ def cpu_baseline(g, sample_edges=CPU_SAMPLE_EDGES):
                       % (k, g.m, g.n, dt)}
 
 
-def bench_batch(dev, stream, steps=5, k=4096):
+def bench_batch(dev, stream, steps=5, k=4096, world=1, rank=0, barrier=None, reduce_max=None):
     """Config 4: 4096 independent graphs (n log-uniform in [2^6, 2^16]; half ER
     with average degree 4, half R-MAT with average degree 16), one batched
     context vs one lc_run per graph on the same GPU (contexts created up front
-    in both cases; creation is not timed)."""
+    in both cases; creation is not timed).  With several ranks each rank runs
+    a size-balanced share of the graphs (no collective on the data path) and
+    the batched rate is all graphs over the slowest rank's time; the
+    one-run-per-graph comparison runs on a single rank only."""
     import torch
 
-    from paper_1807_10727_gb300 import lc, synth
-    b = synth.batch(k=k)
+    from paper_1807_10727_gb300 import lc, shard, synth
+    full = synth.batch(k=k)
+    mine = shard.balance(shard.graph_work(full.n, np.diff(full.eoff)), world)[rank]
+    n_, eoff_, src_, dst_, seeds_ = shard.sub_batch(full.n, full.eoff, full.src, full.dst,
+                                                    full.seeds, mine)
+    b = synth.Batch(n_, eoff_, src_, dst_, seeds_)
+    k_mine = b.k
     src = torch.from_numpy(b.src.view(np.int32)).to(dev)
     dst = torch.from_numpy(b.dst.view(np.int32)).to(dev)
     total = int(b.n.astype(np.int64).sum())
-    labels = torch.empty(total, dtype=torch.int32, device=dev)
+    labels = torch.empty(max(total, 1), dtype=torch.int32, device=dev)
     bl = lc.BatchLocalContraction(b.n, b.eoff, src, dst, b.seeds, stream=stream)
     for _ in range(2):
         bl.run(labels)
     torch.cuda.synchronize(dev)
+    if barrier:
+        barrier()
     t0 = time.perf_counter()
     for _ in range(steps):
         _, rounds, _, _ = bl.run(labels)
     torch.cuda.synchronize(dev)
     batched_s = (time.perf_counter() - t0) / steps
+    if reduce_max:
+        batched_s = reduce_max(batched_s)
     bl.close()
+    if world > 1:
+        return {"workload": "4096 graphs, n log-uniform [2^6, 2^16], ER deg 4 / R-MAT deg 16",
+                "graphs": k, "ranks": world, "graphs_this_rank": k_mine,
+                "batched_graphs_per_s": k / batched_s, "batched_ms": batched_s * 1e3}
     # one context and one lc_run per graph
     voff = np.concatenate([[0], np.cumsum(b.n.astype(np.int64))])
     ctxs = []
+    k = k_mine
     for g in range(k):
         lo, hi = int(b.eoff[g]), int(b.eoff[g + 1])
         ctxs.append(lc.LocalContraction(int(b.n[g]), src[lo:hi], dst[lo:hi], seed=int(b.seeds[g]),
@@ -482,9 +499,17 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(g)
     batched = None
-    if rank == 0 and not args.no_batch:
+    if not args.no_batch:
         torch.cuda.empty_cache()
-        batched = bench_batch(dev, stream)
+
+        def reduce_max(x):
+            t = torch.tensor([x], dtype=torch.float64, device=dev)
+            if world > 1:
+                dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            return float(t.item())
+
+        batched = bench_batch(dev, stream, world=world, rank=rank, barrier=barrier,
+                              reduce_max=reduce_max)
         log("batched leg done")
     serving = None
     if rank == 0 and not args.no_serving:
