@@ -80,7 +80,19 @@ lc_status lc_create(uint32_t n, const uint32_t* d_src, const uint32_t* d_dst, ui
  * finish: once 0 < m_i <= finish_edges, that phase merges each connected
  * component of G_i into one node (the paper's single-machine union-find finish,
  * Section 7).  finish_edges = 0 (default) disables it.  Both change the phase
- * count and per-phase sizes, never the labels. */
+ * count and per-phase sizes, never the labels.
+ *   LC_VARIANT_TWO_HOP  nodes are the classes of equal label l(v) = the
+ *            min-key vertex of N(N(v)), each named by its label vertex (which
+ *            need not belong to the class); allocates 8*n more device bytes
+ *            on first selection (LC_ERR_OOM if that fails).
+ *   LC_VARIANT_TREE     f(v) = min-key vertex of N(v) \ {v} (v itself when it
+ *            has no other neighbour); nodes are the weakly connected
+ *            components of f, named by the lower-key vertex of their terminal
+ *            2-cycle (Lemmas lem:cycle and lem:wccs).
+ * Returns LC_ERR_INVALID for an unknown variant, for finish_edges != 0 on a
+ * batch context (lc_batch_create: the threshold is per graph), or while a run
+ * of the context is in flight.  Contexts created by the serving loop and
+ * lc_run_static always use the forest variant without finish. */
 lc_status lc_configure(lc_ctx* ctx, lc_variant variant, uint64_t finish_edges);
 
 typedef enum {

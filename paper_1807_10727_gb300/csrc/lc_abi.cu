@@ -25,7 +25,7 @@ const char* kernel_name(int id) {
       "relabel_packed", "relabel_split", "sort_hist", "hist_scan",     "sort_pass",
       "scan_flags",
       "unique_rename", "propagate",  "bucket_bounds",   "bucket_dedup",  "rename",
-      "unmix",         "batch",      "identity",        "rank_probe"};
+      "unmix",         "batch",      "variant",         "identity",      "rank_probe"};
   static_assert(sizeof(names) / sizeof(names[0]) == kNumKernels, "one name per kernel");
   return (id >= 0 && id < kNumKernels) ? names[id] : "unknown";
 }
@@ -196,6 +196,7 @@ struct lc_ctx {
   uint32_t* own_labels = nullptr;
 
   unsigned long long* minkey = nullptr;
+  unsigned long long* minkey2 = nullptr;  // second-hop minima (two-hop variant only)
   uint8_t* flags = nullptr;
   uint64_t* ebuf[2] = {nullptr, nullptr};
   Counters* ctr = nullptr;
@@ -240,6 +241,7 @@ static void free_ctx(lc_ctx* c) {
   cudaFree(c->own_dst);
   cudaFree(c->own_labels);
   cudaFree(c->minkey);
+  cudaFree(c->minkey2);
   cudaFree(c->flags);
   cudaFree(c->ebuf[0]);
   cudaFree(c->ebuf[1]);
@@ -334,10 +336,15 @@ extern "C" lc_status lc_create(uint32_t n, const uint32_t* d_src, const uint32_t
 
 extern "C" lc_status lc_configure(lc_ctx* c, lc_variant variant, uint64_t finish_edges) {
   if (!c) return LC_ERR_INVALID;
-  if (variant != LC_VARIANT_FOREST) return LC_ERR_INVALID;  // other variants: not built yet
+  if (variant != LC_VARIANT_FOREST && variant != LC_VARIANT_TWO_HOP && variant != LC_VARIANT_TREE)
+    return LC_ERR_INVALID;
+  // the finish threshold compares one graph's edge count; a batch has many
+  if (finish_edges != 0 && c->batch != nullptr) return LC_ERR_INVALID;
+  if (c->rs.state != RunState::kDone) return LC_ERR_INVALID;
+  if (variant == LC_VARIANT_TWO_HOP && c->minkey2 == nullptr)
+    LC_TRY(cudaMalloc(&c->minkey2, std::max<uint64_t>(c->n_cap, 1) * 8));
   c->variant = variant;
   c->finish_edges = finish_edges;
-  if (finish_edges != 0) return LC_ERR_INVALID;
   return LC_OK;
 }
 
@@ -397,12 +404,32 @@ static lc_status enqueue_phase(lc_ctx* c) {
     bv = BatchView{b->d_rk, b->voff.back(), b->k};
   }
   const BatchView* bp = c->batch ? &bv : nullptr;
-  // (a) + (b): ranks and closed-neighbourhood minimum
+  const uint32_t* src0 = i == 0 ? c->src : nullptr;
+  const uint32_t* dst0 = i == 0 ? c->dst : nullptr;
+  // (a): ranks (and, in phase 0, each vertex's min original id = itself)
   init_keys(c->minkey, i == 0 ? r.lv.mo : nullptr, ni, rk, bp, L);
-  edge_min(i == 0 ? c->src : nullptr, i == 0 ? c->dst : nullptr, r.packed, mi, ni, rk, c->minkey,
-           err, c->window_bytes, bp, L);
-  // (c): roots of the parent arborescences
-  jump(c->minkey, r.lv.root, r.lv.mo, ni, err, L);
+  if (c->finish_edges != 0 && mi <= c->finish_edges) {
+    // small-graph finish: one node per connected component of G_i
+    union_find_names(src0, dst0, r.packed, mi, ni, reinterpret_cast<uint32_t*>(c->minkey),
+                     r.lv.root, r.lv.mo, err, L);
+  } else if (c->variant == LC_VARIANT_TREE) {
+    // (b) + (c): open-neighbourhood parent, names from the terminal 2-cycles
+    tree_names(src0, dst0, r.packed, mi, ni, rk, bp, c->minkey, r.lv.root, r.lv.mo, err, L);
+  } else {
+    // (b): closed-neighbourhood minimum
+    edge_min(src0, dst0, r.packed, mi, ni, rk, c->minkey, err, c->window_bytes, bp, L);
+    if (c->variant == LC_VARIANT_TWO_HOP) {
+      // second hop; names are label vertices, node minima in their own array
+      uint32_t* nmo = c->arena.alloc(ni, &aerr);
+      if (aerr != cudaSuccess) return fail(c, status_of(aerr));
+      two_hop_names(src0, dst0, r.packed, mi, ni, c->minkey, c->minkey2, r.lv.root, r.lv.mo, nmo,
+                    err, L);
+      r.lv.mo = nmo;
+    } else {
+      // (c): roots of the parent arborescences
+      jump(c->minkey, r.lv.root, r.lv.mo, ni, err, L);
+    }
+  }
   // (d): relabel, drop loops, deduplicate, compact
   if (cudaMemsetAsync(c->ctr, 0, 4 * sizeof(unsigned long long), c->stream) != cudaSuccess ||
       cudaMemsetAsync(c->flags, 0, ni, c->stream) != cudaSuccess)
@@ -412,7 +439,7 @@ static lc_status enqueue_phase(lc_ctx* c) {
   PassPlan hplan{};
   const int hb = hash_plan(mi, &hplan);
   if (!c->dedup_sort) hist_reset(c->sort, L);
-  relabel(i == 0 ? c->src : nullptr, i == 0 ? c->dst : nullptr, r.packed, mi, ni, r.lv.root,
+  relabel(src0, dst0, r.packed, mi, ni, r.lv.root,
           r.bits, r.keys, &c->ctr->mprime, &c->ctr->emitted, !c->dedup_sort,
           c->dedup_sort ? nullptr : &hplan, c->sort.hist, i == 0 ? r.alt : nullptr,
           c->relabel_window_bytes, err, L);

@@ -29,6 +29,7 @@ enum KernelId : int {
   kKRename,
   kKUnmix,
   kKBatch,
+  kKVariant,
   kKIdentity,
   kKRankProbe,
   kNumKernels
@@ -267,6 +268,26 @@ void propagate(const uint32_t* root, const uint32_t* scan, const uint32_t* mo,
 // (lets the host check that the counters it reads belong to the phase it
 // expects).
 void stamp_counters(Counters* ctr, uint64_t tag, const Launch& L);
+
+// Node names of the other phase variants (edges as in edge_min; root[v]
+// receives the name of v's node):
+//  - two_hop_names: published LocalContraction label, min key over N(N(v))
+//    (mk1 = closed-neighbourhood minima from edge_min; mk2 scratch); names
+//    need not be members of their group, so node minima go to nmo (n words).
+//  - tree_names: TreeContraction, open-neighbourhood parent, name = lower-key
+//    vertex of the terminal 2-cycle; node minima aggregated in mo in place.
+//  - union_find_names: every vertex named by its component's smallest id
+//    (the small-graph finish); parent is n words of scratch.
+void two_hop_names(const uint32_t* src, const uint32_t* dst, const uint64_t* packed, uint64_t m,
+                   uint32_t n, const unsigned long long* mk1, unsigned long long* mk2,
+                   uint32_t* root, const uint32_t* mo, uint32_t* nmo, unsigned* err,
+                   const Launch& L);
+void tree_names(const uint32_t* src, const uint32_t* dst, const uint64_t* packed, uint64_t m,
+                uint32_t n, uint64_t rk, const BatchView* batch, unsigned long long* minkey,
+                uint32_t* root, uint32_t* mo, unsigned* err, const Launch& L);
+void union_find_names(const uint32_t* src, const uint32_t* dst, const uint64_t* packed,
+                      uint64_t m, uint32_t n, uint32_t* parent, uint32_t* root, uint32_t* mo,
+                      unsigned* err, const Launch& L);
 
 // labels[v] = v (a graph without edges).
 void identity_labels(uint32_t* labels, uint32_t n, const Launch& L);

@@ -254,6 +254,191 @@ __global__ void __launch_bounds__(kThreads) k_jump(unsigned long long* minkey,
   }
 }
 
+// ------------------------------------------------------- phase variants
+
+// Edge visitor over uint32 pairs (phase 0: ids validated, bad ids set
+// kErrBadVertex and are skipped) or packed uint64 edges (ids checked).
+template <class Op>
+__global__ void __launch_bounds__(kThreads) k_for_edges(const uint32_t* __restrict__ src,
+                                                        const uint32_t* __restrict__ dst,
+                                                        const uint64_t* __restrict__ packed,
+                                                        uint64_t m, uint32_t n, Op op,
+                                                        unsigned* err) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += stride) {
+    uint32_t u, v;
+    if (packed != nullptr) {
+      const uint64_t x = __ldcs(packed + j);
+      u = (uint32_t)(x >> 32);
+      v = (uint32_t)x;
+      if (!index_ok(err, Op::kKernel, max(u, v), n)) continue;
+    } else {
+      u = __ldcs(src + j);
+      v = __ldcs(dst + j);
+      if (u >= n || v >= n) {
+        atomicOr(err, kErrBadVertex);
+        continue;
+      }
+    }
+    op(u, v);
+  }
+}
+
+// Second hop of the two-hop label (Section 3, LocalContraction):
+// mk2[v] = min over u in N(v) of mk1[u], starting from mk2 = mk1.  Only the
+// endpoint with the larger mk1 can improve (mk2 <= mk1), so one atomic.
+struct TwoHopOp {
+  static constexpr int kKernel = kKVariant;
+  const unsigned long long* mk1;
+  unsigned long long* mk2;
+  __device__ __forceinline__ void operator()(uint32_t u, uint32_t v) const {
+    const unsigned long long a = mk1[u], b = mk1[v];
+    if (a < b) atomicMin(&mk2[v], a);
+    else if (b < a) atomicMin(&mk2[u], b);
+  }
+};
+
+// Open-neighbourhood minimum (TreeContraction, Section 3): every non-loop
+// edge offers each endpoint the other's key.
+template <class K>
+struct OpenMinOp {
+  static constexpr int kKernel = kKVariant;
+  K keys;
+  unsigned long long* minkey;
+  __device__ __forceinline__ void operator()(uint32_t u, uint32_t v) const {
+    if (u == v) return;
+    uint64_t ku, kv;
+    keys.pair(u, v, ku, kv);
+    atomicMin(&minkey[u], (unsigned long long)kv);
+    atomicMin(&minkey[v], (unsigned long long)ku);
+  }
+};
+
+// Lock-free union of the endpoints' sets: the larger of the two roots is
+// hooked under the smaller with a compare-and-swap (retried when another
+// thread hooked it first).  parent[x] <= x always holds, so every find walks
+// strictly decreasing ids, and a set's root is its smallest id.  Reads go
+// through L2 (__ldcg) so that a retry sees the hooks of other SMs; a stale
+// value is still an ancestor, and only the compare-and-swap decides.
+__device__ __forceinline__ uint32_t uf_find(uint32_t* parent, uint32_t x, unsigned* err) {
+  for (;;) {
+    const uint32_t p = __ldcg(parent + x);
+    if (p == x) return x;
+    if (!index_ok(err, kKVariant, p, x)) return x;  // parent ids only decrease
+    const uint32_t gp = __ldcg(parent + p);
+    if (gp < p) parent[x] = gp;  // path halving: gp is an ancestor of x
+    x = p;
+  }
+}
+
+struct UnionOp {
+  static constexpr int kKernel = kKVariant;
+  uint32_t* parent;
+  unsigned* err;
+  __device__ __forceinline__ void operator()(uint32_t u, uint32_t v) const {
+    // each failed hook means that the larger root got a parent, so the pair
+    // of roots found next is smaller: at most 2n retries
+    for (uint64_t tries = 0;; ++tries) {
+      const uint32_t a = uf_find(parent, u, err), b = uf_find(parent, v, err);
+      if (a == b) return;
+      const uint32_t hi = max(a, b), lo = min(a, b);
+      if (atomicCAS(&parent[hi], hi, lo) == hi) return;
+      if (!index_ok(err, kKVariant, tries, 2ull * hi + 2)) return;
+    }
+  }
+};
+
+__global__ void k_copy_u64(unsigned long long* __restrict__ dst,
+                           const unsigned long long* __restrict__ src, uint32_t n) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride)
+    dst[v] = src[v];
+}
+
+// Two-hop names: root[v] = the label vertex low32(mk2[v]); nmo[name] = min of
+// the members' mo (a label vertex need not belong to its own group, so the
+// node minima live in their own array).
+__global__ void k_two_hop_names(const unsigned long long* __restrict__ mk2, uint32_t* root,
+                                const uint32_t* __restrict__ mo, uint32_t* nmo, uint32_t n,
+                                unsigned* err) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+    uint32_t name = (uint32_t)mk2[v];
+    if (!index_ok(err, kKVariant, name, n)) name = (uint32_t)v;
+    root[v] = name;
+    atomicMin(&nmo[name], mo[v]);
+  }
+}
+
+// TreeContraction names: follow f (f(x) = low32(minkey[x]), or x itself when
+// x has no other neighbour) to the terminal 2-cycle {p, f(p)} (Lemma
+// lem:cycle) and name the weakly connected component by the lower-key vertex
+// of that pair (Lemma lem:wccs).  The name is a member of its own group, so
+// node minima are aggregated in place.
+template <class K>
+__global__ void __launch_bounds__(kThreads) k_tree_names(const unsigned long long* __restrict__ minkey,
+                                                         uint32_t* root, uint32_t* mo, uint32_t n,
+                                                         K keys, unsigned* err) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  auto f = [&](uint32_t x) -> uint32_t {
+    const unsigned long long k = minkey[x];
+    return k == ~0ull ? x : (uint32_t)k;
+  };
+  for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+    uint32_t p = f((uint32_t)v);
+    bool ok = index_ok(err, kKVariant, p, n);
+    for (uint32_t steps = 0; ok; ++steps) {
+      const uint32_t q = f(p);
+      if (!index_ok(err, kKVariant, q, n) || !index_ok(err, kKVariant, steps, (uint64_t)n + 2)) {
+        ok = false;
+        break;
+      }
+      if (f(q) == p) break;  // p lies on the 2-cycle {p, q} (or q == p: no neighbour)
+      p = q;
+    }
+    uint32_t name = (uint32_t)v;
+    if (ok) {
+      const uint32_t q = f(p);
+      name = (q == p || keys.key(p) < keys.key(q)) ? p : q;
+    }
+    root[v] = name;
+    if (name != (uint32_t)v) atomicMin(&mo[name], mo[v]);
+  }
+}
+
+__global__ void k_uf_init(uint32_t* parent, uint32_t n) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride)
+    parent[v] = (uint32_t)v;
+}
+
+// Root of v once all unions are done (parents only decrease along a path).
+__device__ __forceinline__ uint32_t uf_root(const uint32_t* parent, uint32_t v, unsigned* err) {
+  uint32_t r = v;
+  for (;;) {
+    const uint32_t p = parent[r];
+    if (p == r) return r;
+    if (!index_ok(err, kKVariant, p, r)) return v;
+    r = p;
+  }
+}
+
+// Node minima of the union-find components, aggregated at the roots.
+__global__ void k_uf_names(const uint32_t* parent, uint32_t* mo, uint32_t n, unsigned* err) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+    const uint32_t r = uf_root(parent, (uint32_t)v, err);
+    if (r != (uint32_t)v) atomicMin(&mo[r], mo[v]);
+  }
+}
+
+// root[v] = the smallest id of v's component.
+__global__ void k_uf_flatten(const uint32_t* parent, uint32_t* root, uint32_t n, unsigned* err) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride)
+    root[v] = uf_root(parent, (uint32_t)v, err);
+}
+
 // ----------------------------------------------------------- relabel
 
 constexpr int kRelItems = 16;
@@ -579,6 +764,67 @@ void propagate(const uint32_t* root, const uint32_t* scan, const uint32_t* mo,
 void stamp_counters(Counters* ctr, uint64_t tag, const Launch& L) {
   KScope ks(L, kKBatch);
   k_stamp<<<1, 1, 0, L.stream>>>(ctr, tag);
+}
+
+template <class Op>
+static void for_edges(const uint32_t* src, const uint32_t* dst, const uint64_t* packed, uint64_t m,
+                      uint32_t n, Op op, unsigned* err, const Launch& L) {
+  if (m == 0) return;
+  KScope ks(L, kKVariant);
+  k_for_edges<<<grid_for(m, kThreads, L), kThreads, 0, L.stream>>>(src, dst, packed, m, n, op,
+                                                                   err);
+}
+
+void two_hop_names(const uint32_t* src, const uint32_t* dst, const uint64_t* packed, uint64_t m,
+                   uint32_t n, const unsigned long long* mk1, unsigned long long* mk2,
+                   uint32_t* root, const uint32_t* mo, uint32_t* nmo, unsigned* err,
+                   const Launch& L) {
+  if (n == 0) return;
+  {
+    KScope ks(L, kKVariant);
+    k_copy_u64<<<grid_for(n, kThreads, L), kThreads, 0, L.stream>>>(mk2, mk1, n);
+  }
+  for_edges(src, dst, packed, m, n, TwoHopOp{mk1, mk2}, err, L);
+  cudaMemsetAsync(nmo, 0xFF, sizeof(uint32_t) * n, L.stream);
+  KScope ks(L, kKVariant);
+  k_two_hop_names<<<grid_for(n, kThreads, L), kThreads, 0, L.stream>>>(mk2, root, mo, nmo, n,
+                                                                       err);
+}
+
+template <class K>
+static void tree_names_impl(const uint32_t* src, const uint32_t* dst, const uint64_t* packed,
+                            uint64_t m, uint32_t n, K keys, unsigned long long* minkey,
+                            uint32_t* root, uint32_t* mo, unsigned* err, const Launch& L) {
+  cudaMemsetAsync(minkey, 0xFF, sizeof(unsigned long long) * n, L.stream);
+  for_edges(src, dst, packed, m, n, OpenMinOp<K>{keys, minkey}, err, L);
+  KScope ks(L, kKVariant);
+  k_tree_names<<<grid_for(n, kThreads, L), kThreads, 0, L.stream>>>(minkey, root, mo, n, keys,
+                                                                    err);
+}
+
+void tree_names(const uint32_t* src, const uint32_t* dst, const uint64_t* packed, uint64_t m,
+                uint32_t n, uint64_t rk, const BatchView* batch, unsigned long long* minkey,
+                uint32_t* root, uint32_t* mo, unsigned* err, const Launch& L) {
+  if (n == 0) return;
+  if (batch)
+    tree_names_impl(src, dst, packed, m, n, BatchKeys{batch->rk, batch->voff, batch->k}, minkey,
+                    root, mo, err, L);
+  else
+    tree_names_impl(src, dst, packed, m, n, GraphKeys{rk}, minkey, root, mo, err, L);
+}
+
+void union_find_names(const uint32_t* src, const uint32_t* dst, const uint64_t* packed,
+                      uint64_t m, uint32_t n, uint32_t* parent, uint32_t* root, uint32_t* mo,
+                      unsigned* err, const Launch& L) {
+  if (n == 0) return;
+  {
+    KScope ks(L, kKVariant);
+    k_uf_init<<<grid_for(n, kThreads, L), kThreads, 0, L.stream>>>(parent, n);
+  }
+  for_edges(src, dst, packed, m, n, UnionOp{parent, err}, err, L);
+  KScope ks(L, kKVariant);
+  k_uf_names<<<grid_for(n, kThreads, L), kThreads, 0, L.stream>>>(parent, mo, n, err);
+  k_uf_flatten<<<grid_for(n, kThreads, L), kThreads, 0, L.stream>>>(parent, root, n, err);
 }
 
 void identity_labels(uint32_t* labels, uint32_t n, const Launch& L) {

@@ -310,7 +310,7 @@ class BatchLocalContraction:
     32-bit tensors src/dst (local ids); seeds: uint64[k] rank seeds.
     """
 
-    def __init__(self, n, eoff, src, dst, seeds, stream=None):
+    def __init__(self, n, eoff, src, dst, seeds, stream=None, variant: int = LC_VARIANT_FOREST):
         self.n = np.ascontiguousarray(n, dtype=np.uint32)
         self.k = int(self.n.shape[0])
         self.eoff = np.ascontiguousarray(eoff, dtype=np.uint64)
@@ -321,6 +321,8 @@ class BatchLocalContraction:
         self.ctx = lc_batch_create(self.k, self.n, self.eoff, _dev_ptr(src, m, "src") if m else 0,
                                    _dev_ptr(dst, m, "dst") if m else 0, seeds,
                                    _stream_handle(stream))
+        if variant != LC_VARIANT_FOREST:
+            lc_configure(self.ctx, variant, 0)
 
     def run(self, labels=None, cap: int = 256):
         import torch
