@@ -115,6 +115,57 @@ def path_bytes(n_i, m_i, mp_i):
     return total
 
 
+def variant_path_bytes(variant, finish, n_i, m_i, mp_i):
+    """path_bytes plus what a variant adds: the two-hop label reads every edge
+    once more and writes and copies a second n-word key array per phase; the
+    union-find finish phase reads its edges once for the unions."""
+    total = path_bytes(n_i, m_i, mp_i)
+    for i, (n, m) in enumerate(zip(n_i, m_i)):
+        if finish and m <= finish:
+            total += 8 * m + 8 * n
+        elif variant == 1:
+            total += 8 * m + 8 * n + 16 * n + 8 * n
+    return total
+
+
+def bench_variants(ctx, labels, stream, steps, warmup, peak, lc):
+    """The other phase variants and the union-find finish on the same graph
+    and context as the headline: edges/s, phases and the path roofline."""
+    import torch
+    out = {}
+    cases = [("two_hop", lc.LC_VARIANT_TWO_HOP, 0), ("tree", lc.LC_VARIANT_TREE, 0),
+             ("forest_finish_4M", lc.LC_VARIANT_FOREST, 1 << 22),
+             ("forest_finish_64M", lc.LC_VARIANT_FOREST, 1 << 26)]
+    for name, variant, finish in cases:
+        lc.lc_configure(ctx.ctx, variant, finish)
+        for _ in range(warmup):
+            _, res = ctx.run(labels)
+        mp, _ = lc.lc_last_stats(ctx.ctx)
+        ctx.profile(True)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            ctx.run(labels)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        ks = ctx.kernel_stats()
+        ctx.profile(False)
+        pb = variant_path_bytes(variant, finish, res.n_i, res.m_i, mp)
+        top = sorted(((v[1] / steps, k) for k, v in ks.items() if v[0]), reverse=True)[:4]
+        out[name] = {"value": res.m_i[0] / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
+                     "rounds": res.rounds, "sizes": [[int(a), int(b)] for a, b in
+                                                     zip(res.n_i, res.m_i)],
+                     "path_frac": pb / (ms / 1e3) / 1e9 / peak,
+                     "gpu_launches_per_step": sum(v[0] for v in ks.values()) / steps,
+                     "top_kernels_ms": {k: round(t, 3) for t, k in top}}
+        log(f"variant {name}: {ms:.2f} ms/step, {res.rounds} phases")
+    lc.lc_configure(ctx.ctx, lc.LC_VARIANT_FOREST, 0)
+    return out
+
+
 class ClockSampler:
     """nvidia-smi clock/throttle samples every 200 ms during the timed region."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -386,6 +437,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched (config 4) leg")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving (config 5) leg")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the two-hop / tree / union-find-finish leg")
     ap.add_argument("--no-profile", action="store_true",
                     help="skip the per-kernel event timing (roofline) of the timed steps")
     args = ap.parse_args()
@@ -469,6 +522,10 @@ def main():
     kernels = {k: {"launches_per_step": v[0] / args.steps, "ms_per_step": v[1] / args.steps}
                for k, v in kstats.items() if v[0]}
 
+    variants = None
+    if rank == 0 and not args.no_variants:
+        variants = bench_variants(ctx, labels, stream, args.steps, max(3, args.warmup), peak, lc)
+
     # end to end through the public host-buffer entry point
     e2e = None
     if not args.no_e2e:
@@ -528,7 +585,7 @@ def main():
                        "l2": "inputs (8 B/edge) larger than L2; no flush"},
             "roofline": roof, "path_roofline": path_roof,
             "e2e": e2e, "cpu_baseline": cpu, "gpu_launches": launches, "batched": batched,
-            "serving": serving,
+            "serving": serving, "variants": variants,
             "clocks": clk, "kernels": kernels,
             "sizes": [[int(a), int(b), int(c), int(d)]
                       for a, b, c, d in zip(res.n_i, res.m_i, mp, em)],

@@ -25,7 +25,8 @@ const char* kernel_name(int id) {
       "relabel_packed", "relabel_split", "sort_hist", "hist_scan",     "sort_pass",
       "scan_flags",
       "unique_rename", "propagate",  "bucket_bounds",   "bucket_dedup",  "rename",
-      "unmix",         "batch",      "variant",         "identity",      "rank_probe"};
+      "unmix",         "batch",      "two_hop",         "open_min",      "tree_names",
+      "union_find",    "identity",   "rank_probe"};
   static_assert(sizeof(names) / sizeof(names[0]) == kNumKernels, "one name per kernel");
   return (id >= 0 && id < kNumKernels) ? names[id] : "unknown";
 }
@@ -414,7 +415,11 @@ static lc_status enqueue_phase(lc_ctx* c) {
                      r.lv.root, r.lv.mo, err, L);
   } else if (c->variant == LC_VARIANT_TREE) {
     // (b) + (c): open-neighbourhood parent, names from the terminal 2-cycles
-    tree_names(src0, dst0, r.packed, mi, ni, rk, bp, c->minkey, r.lv.root, r.lv.mo, err, L);
+    if (cudaMemsetAsync(c->minkey, 0xFF, sizeof(unsigned long long) * ni, c->stream) !=
+        cudaSuccess)
+      return fail(c, LC_ERR_CUDA);
+    edge_min(src0, dst0, r.packed, mi, ni, rk, c->minkey, err, c->window_bytes, bp, L, true);
+    tree_names(c->minkey, r.lv.root, r.lv.mo, ni, rk, bp, err, L);
   } else {
     // (b): closed-neighbourhood minimum
     edge_min(src0, dst0, r.packed, mi, ni, rk, c->minkey, err, c->window_bytes, bp, L);

@@ -29,7 +29,10 @@ enum KernelId : int {
   kKRename,
   kKUnmix,
   kKBatch,
-  kKVariant,
+  kKTwoHop,
+  kKOpenMin,
+  kKTreeNames,
+  kKUnionFind,
   kKIdentity,
   kKRankProbe,
   kNumKernels
@@ -216,10 +219,12 @@ void init_keys(unsigned long long* minkey, uint32_t* mo, uint32_t n, uint64_t rk
 // kErrBadVertex and are skipped), or packed uint64 (a << 32 | b) sorted by a
 // (packed != nullptr).  For the uint32 form, vertices are processed in windows
 // of at most window_bytes / 8 ids, one pass over the edges per window, so that
-// each pass's atomics stay inside an L2-sized slice of minkey.
+// each pass's atomics stay inside an L2-sized slice of minkey.  open: the
+// open-neighbourhood minimum (no vertex offers its own key; the caller fills
+// minkey with ~0 first), two atomics per edge.
 void edge_min(const uint32_t* src, const uint32_t* dst, const uint64_t* packed, uint64_t m,
               uint32_t n, uint64_t rk, unsigned long long* minkey, unsigned* err,
-              uint64_t window_bytes, const BatchView* batch, const Launch& L);
+              uint64_t window_bytes, const BatchView* batch, const Launch& L, bool open = false);
 
 // Batches: phase seeds rk[g] for phase i; local -> global edge ids (ids
 // validated per graph); next level offsets voff_next[g] = scan[voff[g]] and
@@ -274,17 +279,17 @@ void stamp_counters(Counters* ctr, uint64_t tag, const Launch& L);
 //  - two_hop_names: published LocalContraction label, min key over N(N(v))
 //    (mk1 = closed-neighbourhood minima from edge_min; mk2 scratch); names
 //    need not be members of their group, so node minima go to nmo (n words).
-//  - tree_names: TreeContraction, open-neighbourhood parent, name = lower-key
-//    vertex of the terminal 2-cycle; node minima aggregated in mo in place.
+//  - tree_names: TreeContraction, parent = low half of the open-neighbourhood
+//    minimum in minkey (edge_min with open; ~0 = no other neighbour), name =
+//    lower-key vertex of the terminal 2-cycle; node minima in mo in place.
 //  - union_find_names: every vertex named by its component's smallest id
 //    (the small-graph finish); parent is n words of scratch.
 void two_hop_names(const uint32_t* src, const uint32_t* dst, const uint64_t* packed, uint64_t m,
                    uint32_t n, const unsigned long long* mk1, unsigned long long* mk2,
                    uint32_t* root, const uint32_t* mo, uint32_t* nmo, unsigned* err,
                    const Launch& L);
-void tree_names(const uint32_t* src, const uint32_t* dst, const uint64_t* packed, uint64_t m,
-                uint32_t n, uint64_t rk, const BatchView* batch, unsigned long long* minkey,
-                uint32_t* root, uint32_t* mo, unsigned* err, const Launch& L);
+void tree_names(const unsigned long long* minkey, uint32_t* root, uint32_t* mo, uint32_t n,
+                uint64_t rk, const BatchView* batch, unsigned* err, const Launch& L);
 void union_find_names(const uint32_t* src, const uint32_t* dst, const uint64_t* packed,
                       uint64_t m, uint32_t n, uint32_t* parent, uint32_t* root, uint32_t* mo,
                       unsigned* err, const Launch& L);

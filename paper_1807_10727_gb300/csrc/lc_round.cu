@@ -84,8 +84,10 @@ __global__ void k_rank_probe(uint64_t rk, uint32_t v0, uint32_t count, uint32_t*
 // only the larger endpoint's minimum can drop, to the other endpoint's key;
 // the edge needs one atomic, applied when that endpoint lies in
 // [lo, lo + span) (so one pass over the edges touches an L2-sized slice of
-// minkey).
-template <class K>
+// minkey).  kOpen: the open-neighbourhood minimum of TreeContraction (minkey
+// starts at ~0, not at the vertex's own key), where both endpoints take the
+// other's key, each when it lies in the window.
+template <bool kOpen, class K>
 __device__ __forceinline__ void min_edge_window(uint32_t u, uint32_t v, uint32_t n, const K& keys,
                                                 unsigned long long* minkey, unsigned* err,
                                                 uint32_t lo, uint32_t span, bool check) {
@@ -96,13 +98,18 @@ __device__ __forceinline__ void min_edge_window(uint32_t u, uint32_t v, uint32_t
   if (u == v) return;
   uint64_t ku, kv;
   keys.pair(u, v, ku, kv);
+  if (kOpen) {
+    if (u - lo < span) atomicMin(&minkey[u], (unsigned long long)kv);
+    if (v - lo < span) atomicMin(&minkey[v], (unsigned long long)ku);
+    return;
+  }
   const uint32_t hi = ku < kv ? v : u;
   if (hi - lo < span) atomicMin(&minkey[hi], (unsigned long long)(ku < kv ? ku : kv));
 }
 
 // Input edges as two uint32 arrays; `vec` = both arrays 16-byte aligned.
 // Updates only vertices in [lo, lo + span); ids are validated when `check`.
-template <class K>
+template <bool kOpen, class K>
 __global__ void __launch_bounds__(kThreads) k_edge_min_soa(
     const uint32_t* __restrict__ src, const uint32_t* __restrict__ dst, uint64_t m, uint32_t n,
     K keys, unsigned long long* minkey, unsigned* err, int vec, uint32_t lo, uint32_t span,
@@ -116,33 +123,40 @@ __global__ void __launch_bounds__(kThreads) k_edge_min_soa(
     const uint4* d4 = reinterpret_cast<const uint4*>(dst);
     for (uint64_t q = gt; q < nq; q += stride) {
       uint4 s = __ldcs(s4 + q), d = __ldcs(d4 + q);
-      min_edge_window(s.x, d.x, n, keys, minkey, err, lo, span, check);
-      min_edge_window(s.y, d.y, n, keys, minkey, err, lo, span, check);
-      min_edge_window(s.z, d.z, n, keys, minkey, err, lo, span, check);
-      min_edge_window(s.w, d.w, n, keys, minkey, err, lo, span, check);
+      min_edge_window<kOpen>(s.x, d.x, n, keys, minkey, err, lo, span, check);
+      min_edge_window<kOpen>(s.y, d.y, n, keys, minkey, err, lo, span, check);
+      min_edge_window<kOpen>(s.z, d.z, n, keys, minkey, err, lo, span, check);
+      min_edge_window<kOpen>(s.w, d.w, n, keys, minkey, err, lo, span, check);
     }
     done = nq * 4;
   }
   for (uint64_t j = done + gt; j < m; j += stride)
-    min_edge_window(__ldcs(src + j), __ldcs(dst + j), n, keys, minkey, err, lo, span, check);
+    min_edge_window<kOpen>(__ldcs(src + j), __ldcs(dst + j), n, keys, minkey, err, lo, span,
+                           check);
 }
 
 // One atomic per edge, at the endpoint with the larger key (see
-// min_edge_window).
-template <class K>
+// min_edge_window); two for the open-neighbourhood minimum.
+template <bool kOpen, class K>
 __device__ __forceinline__ void min_edge_packed(uint64_t x, const K& keys,
                                                 unsigned long long* minkey, uint32_t n,
                                                 unsigned* err) {
   const uint32_t a = (uint32_t)(x >> 32), b = (uint32_t)x;
-  if (!index_ok(err, kKEdgeMinPacked, max(a, b), n)) return;
+  if (!index_ok(err, kOpen ? kKOpenMin : kKEdgeMinPacked, max(a, b), n)) return;
   uint64_t ka, kb;
   keys.pair(a, b, ka, kb);
-  if (ka < kb) atomicMin(&minkey[b], (unsigned long long)ka);
-  else atomicMin(&minkey[a], (unsigned long long)kb);
+  if (kOpen) {
+    atomicMin(&minkey[a], (unsigned long long)kb);
+    atomicMin(&minkey[b], (unsigned long long)ka);
+  } else if (ka < kb) {
+    atomicMin(&minkey[b], (unsigned long long)ka);
+  } else {
+    atomicMin(&minkey[a], (unsigned long long)kb);
+  }
 }
 
 // Packed edges (a << 32 | b), two per 128-bit load.
-template <class K>
+template <bool kOpen, class K>
 __global__ void __launch_bounds__(kThreads) k_edge_min_packed(
     const uint64_t* __restrict__ e, uint64_t m, K keys, unsigned long long* minkey, uint32_t n,
     unsigned* err) {
@@ -152,10 +166,10 @@ __global__ void __launch_bounds__(kThreads) k_edge_min_packed(
   const uint64_t gt = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   for (uint64_t q = gt; q < npair; q += stride) {
     ulonglong2 p = __ldcs(e2 + q);
-    min_edge_packed(p.x, keys, minkey, n, err);
-    min_edge_packed(p.y, keys, minkey, n, err);
+    min_edge_packed<kOpen>(p.x, keys, minkey, n, err);
+    min_edge_packed<kOpen>(p.y, keys, minkey, n, err);
   }
-  if ((m & 1) && gt == 0) min_edge_packed(e[m - 1], keys, minkey, n, err);
+  if ((m & 1) && gt == 0) min_edge_packed<kOpen>(e[m - 1], keys, minkey, n, err);
 }
 
 // ------------------------------------------------------- batches
@@ -287,32 +301,69 @@ __global__ void __launch_bounds__(kThreads) k_for_edges(const uint32_t* __restri
 // Second hop of the two-hop label (Section 3, LocalContraction):
 // mk2[v] = min over u in N(v) of mk1[u], starting from mk2 = mk1.  Only the
 // endpoint with the larger mk1 can improve (mk2 <= mk1), so one atomic.
-struct TwoHopOp {
-  static constexpr int kKernel = kKVariant;
-  const unsigned long long* mk1;
-  unsigned long long* mk2;
-  __device__ __forceinline__ void operator()(uint32_t u, uint32_t v) const {
-    const unsigned long long a = mk1[u], b = mk1[v];
-    if (a < b) atomicMin(&mk2[v], a);
-    else if (b < a) atomicMin(&mk2[u], b);
-  }
-};
+__device__ __forceinline__ void two_hop_apply(uint32_t u, uint32_t v, unsigned long long a,
+                                              unsigned long long b, unsigned long long* mk2) {
+  if (a < b) atomicMin(&mk2[v], a);
+  else if (b < a) atomicMin(&mk2[u], b);
+}
 
-// Open-neighbourhood minimum (TreeContraction, Section 3): every non-loop
-// edge offers each endpoint the other's key.
-template <class K>
-struct OpenMinOp {
-  static constexpr int kKernel = kKVariant;
-  K keys;
-  unsigned long long* minkey;
-  __device__ __forceinline__ void operator()(uint32_t u, uint32_t v) const {
-    if (u == v) return;
-    uint64_t ku, kv;
-    keys.pair(u, v, ku, kv);
-    atomicMin(&minkey[u], (unsigned long long)kv);
-    atomicMin(&minkey[v], (unsigned long long)ku);
+// Edges as uint32 arrays (phase 0; `vec` = 16-byte aligned; ids >= n were
+// reported by edge_min and are skipped) or packed (a << 32 | b).  Four edges
+// per iteration, their eight mk1 gathers issued before any atomic.
+__global__ void __launch_bounds__(kThreads) k_two_hop(const uint32_t* __restrict__ src,
+                                                      const uint32_t* __restrict__ dst,
+                                                      const uint64_t* __restrict__ packed,
+                                                      uint64_t m, uint32_t n, int vec,
+                                                      const unsigned long long* __restrict__ mk1,
+                                                      unsigned long long* mk2, unsigned* err) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  const uint64_t gt = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const uint64_t nq = (packed != nullptr || vec) ? m / 4 : 0;
+  for (uint64_t q = gt; q < nq; q += stride) {
+    uint32_t u[4], v[4];
+    if (packed != nullptr) {
+      const ulonglong2* e2 = reinterpret_cast<const ulonglong2*>(packed);
+      const ulonglong2 p0 = __ldcs(e2 + 2 * q), p1 = __ldcs(e2 + 2 * q + 1);
+      const uint64_t x[4] = {p0.x, p0.y, p1.x, p1.y};
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        u[i] = (uint32_t)(x[i] >> 32);
+        v[i] = (uint32_t)x[i];
+      }
+    } else {
+      const uint4 s = __ldcs(reinterpret_cast<const uint4*>(src) + q);
+      const uint4 d = __ldcs(reinterpret_cast<const uint4*>(dst) + q);
+      u[0] = s.x; u[1] = s.y; u[2] = s.z; u[3] = s.w;
+      v[0] = d.x; v[1] = d.y; v[2] = d.z; v[3] = d.w;
+    }
+    bool ok[4];
+    unsigned long long a[4], b[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      ok[i] = packed != nullptr ? index_ok(err, kKTwoHop, max(u[i], v[i]), n)
+                                : (u[i] < n && v[i] < n);
+      a[i] = ok[i] ? __ldg(mk1 + u[i]) : 0ull;
+      b[i] = ok[i] ? __ldg(mk1 + v[i]) : 0ull;
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      if (ok[i]) two_hop_apply(u[i], v[i], a[i], b[i], mk2);
   }
-};
+  for (uint64_t j = nq * 4 + gt; j < m; j += stride) {
+    uint32_t u, v;
+    if (packed != nullptr) {
+      const uint64_t x = __ldcs(packed + j);
+      u = (uint32_t)(x >> 32);
+      v = (uint32_t)x;
+      if (!index_ok(err, kKTwoHop, max(u, v), n)) continue;
+    } else {
+      u = __ldcs(src + j);
+      v = __ldcs(dst + j);
+      if (u >= n || v >= n) continue;
+    }
+    two_hop_apply(u, v, __ldg(mk1 + u), __ldg(mk1 + v), mk2);
+  }
+}
 
 // Lock-free union of the endpoints' sets: the larger of the two roots is
 // hooked under the smaller with a compare-and-swap (retried when another
@@ -324,7 +375,7 @@ __device__ __forceinline__ uint32_t uf_find(uint32_t* parent, uint32_t x, unsign
   for (;;) {
     const uint32_t p = __ldcg(parent + x);
     if (p == x) return x;
-    if (!index_ok(err, kKVariant, p, x)) return x;  // parent ids only decrease
+    if (!index_ok(err, kKUnionFind, p, x)) return x;  // parent ids only decrease
     const uint32_t gp = __ldcg(parent + p);
     if (gp < p) parent[x] = gp;  // path halving: gp is an ancestor of x
     x = p;
@@ -332,18 +383,19 @@ __device__ __forceinline__ uint32_t uf_find(uint32_t* parent, uint32_t x, unsign
 }
 
 struct UnionOp {
-  static constexpr int kKernel = kKVariant;
+  static constexpr int kKernel = kKUnionFind;
   uint32_t* parent;
   unsigned* err;
+  uint32_t n;
   __device__ __forceinline__ void operator()(uint32_t u, uint32_t v) const {
-    // each failed hook means that the larger root got a parent, so the pair
-    // of roots found next is smaller: at most 2n retries
+    // each failed hook means that the larger root got a parent, so the sum of
+    // the two roots found next is smaller: fewer than 2n retries
     for (uint64_t tries = 0;; ++tries) {
       const uint32_t a = uf_find(parent, u, err), b = uf_find(parent, v, err);
       if (a == b) return;
       const uint32_t hi = max(a, b), lo = min(a, b);
       if (atomicCAS(&parent[hi], hi, lo) == hi) return;
-      if (!index_ok(err, kKVariant, tries, 2ull * hi + 2)) return;
+      if (!index_ok(err, kKUnionFind, tries, 2ull * n + 2)) return;
     }
   }
 };
@@ -364,7 +416,7 @@ __global__ void k_two_hop_names(const unsigned long long* __restrict__ mk2, uint
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
     uint32_t name = (uint32_t)mk2[v];
-    if (!index_ok(err, kKVariant, name, n)) name = (uint32_t)v;
+    if (!index_ok(err, kKTwoHop, name, n)) name = (uint32_t)v;
     root[v] = name;
     atomicMin(&nmo[name], mo[v]);
   }
@@ -386,10 +438,10 @@ __global__ void __launch_bounds__(kThreads) k_tree_names(const unsigned long lon
   };
   for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
     uint32_t p = f((uint32_t)v);
-    bool ok = index_ok(err, kKVariant, p, n);
+    bool ok = index_ok(err, kKTreeNames, p, n);
     for (uint32_t steps = 0; ok; ++steps) {
       const uint32_t q = f(p);
-      if (!index_ok(err, kKVariant, q, n) || !index_ok(err, kKVariant, steps, (uint64_t)n + 2)) {
+      if (!index_ok(err, kKTreeNames, q, n) || !index_ok(err, kKTreeNames, steps, (uint64_t)n + 2)) {
         ok = false;
         break;
       }
@@ -418,7 +470,7 @@ __device__ __forceinline__ uint32_t uf_root(const uint32_t* parent, uint32_t v, 
   for (;;) {
     const uint32_t p = parent[r];
     if (p == r) return r;
-    if (!index_ok(err, kKVariant, p, r)) return v;
+    if (!index_ok(err, kKUnionFind, p, r)) return v;
     r = p;
   }
 }
@@ -644,13 +696,13 @@ void init_keys(unsigned long long* minkey, uint32_t* mo, uint32_t n, uint64_t rk
     k_init_keys<<<grid_for(n, kThreads, L), kThreads, 0, L.stream>>>(minkey, mo, n, GraphKeys{rk});
 }
 
-template <class K>
+template <bool kOpen, class K>
 static void edge_min_impl(const uint32_t* src, const uint32_t* dst, const uint64_t* packed,
                           uint64_t m, uint32_t n, K keys, unsigned long long* minkey,
                           unsigned* err, uint64_t window_bytes, const Launch& L) {
   if (packed != nullptr) {
-    KScope ks(L, kKEdgeMinPacked);
-    k_edge_min_packed<<<grid_for(m / 2 + 1, kThreads, L), kThreads, 0, L.stream>>>(
+    KScope ks(L, kOpen ? kKOpenMin : kKEdgeMinPacked);
+    k_edge_min_packed<kOpen><<<grid_for(m / 2 + 1, kThreads, L), kThreads, 0, L.stream>>>(
         packed, m, keys, minkey, n, err);
   } else {
     int vec = ((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst)) & 15) == 0;
@@ -661,8 +713,8 @@ static void edge_min_impl(const uint32_t* src, const uint32_t* dst, const uint64
     for (uint32_t p = 0; p < passes; ++p) {
       uint64_t lo = (uint64_t)p * span;
       uint64_t sp = std::min<uint64_t>(span, n - lo);
-      KScope ks(L, kKEdgeMinSoa);
-      k_edge_min_soa<<<grid_for((m + 3) / 4, kThreads, L), kThreads, 0, L.stream>>>(
+      KScope ks(L, kOpen ? kKOpenMin : kKEdgeMinSoa);
+      k_edge_min_soa<kOpen><<<grid_for((m + 3) / 4, kThreads, L), kThreads, 0, L.stream>>>(
           src, dst, m, n, keys, minkey, err, vec, (uint32_t)lo, (uint32_t)sp, p == 0);
     }
   }
@@ -670,13 +722,17 @@ static void edge_min_impl(const uint32_t* src, const uint32_t* dst, const uint64
 
 void edge_min(const uint32_t* src, const uint32_t* dst, const uint64_t* packed, uint64_t m,
               uint32_t n, uint64_t rk, unsigned long long* minkey, unsigned* err,
-              uint64_t window_bytes, const BatchView* batch, const Launch& L) {
+              uint64_t window_bytes, const BatchView* batch, const Launch& L, bool open) {
   if (m == 0) return;
-  if (batch)
-    edge_min_impl(src, dst, packed, m, n, BatchKeys{batch->rk, batch->voff, batch->k}, minkey,
-                  err, window_bytes, L);
-  else
-    edge_min_impl(src, dst, packed, m, n, GraphKeys{rk}, minkey, err, window_bytes, L);
+  if (batch) {
+    const BatchKeys k{batch->rk, batch->voff, batch->k};
+    if (open) edge_min_impl<true>(src, dst, packed, m, n, k, minkey, err, window_bytes, L);
+    else edge_min_impl<false>(src, dst, packed, m, n, k, minkey, err, window_bytes, L);
+  } else {
+    const GraphKeys k{rk};
+    if (open) edge_min_impl<true>(src, dst, packed, m, n, k, minkey, err, window_bytes, L);
+    else edge_min_impl<false>(src, dst, packed, m, n, k, minkey, err, window_bytes, L);
+  }
 }
 
 void batch_phase_seeds(const uint64_t* seeds, uint32_t k, uint32_t i, uint64_t* rk,
@@ -770,7 +826,7 @@ template <class Op>
 static void for_edges(const uint32_t* src, const uint32_t* dst, const uint64_t* packed, uint64_t m,
                       uint32_t n, Op op, unsigned* err, const Launch& L) {
   if (m == 0) return;
-  KScope ks(L, kKVariant);
+  KScope ks(L, Op::kKernel);
   k_for_edges<<<grid_for(m, kThreads, L), kThreads, 0, L.stream>>>(src, dst, packed, m, n, op,
                                                                    err);
 }
@@ -781,36 +837,32 @@ void two_hop_names(const uint32_t* src, const uint32_t* dst, const uint64_t* pac
                    const Launch& L) {
   if (n == 0) return;
   {
-    KScope ks(L, kKVariant);
+    KScope ks(L, kKTwoHop);
     k_copy_u64<<<grid_for(n, kThreads, L), kThreads, 0, L.stream>>>(mk2, mk1, n);
   }
-  for_edges(src, dst, packed, m, n, TwoHopOp{mk1, mk2}, err, L);
+  if (m) {
+    const int vec =
+        ((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst)) & 15) == 0;
+    KScope ks(L, kKTwoHop);
+    k_two_hop<<<grid_for((m + 3) / 4, kThreads, L), kThreads, 0, L.stream>>>(
+        src, dst, packed, m, n, vec, mk1, mk2, err);
+  }
   cudaMemsetAsync(nmo, 0xFF, sizeof(uint32_t) * n, L.stream);
-  KScope ks(L, kKVariant);
+  KScope ks(L, kKTwoHop);
   k_two_hop_names<<<grid_for(n, kThreads, L), kThreads, 0, L.stream>>>(mk2, root, mo, nmo, n,
                                                                        err);
 }
 
-template <class K>
-static void tree_names_impl(const uint32_t* src, const uint32_t* dst, const uint64_t* packed,
-                            uint64_t m, uint32_t n, K keys, unsigned long long* minkey,
-                            uint32_t* root, uint32_t* mo, unsigned* err, const Launch& L) {
-  cudaMemsetAsync(minkey, 0xFF, sizeof(unsigned long long) * n, L.stream);
-  for_edges(src, dst, packed, m, n, OpenMinOp<K>{keys, minkey}, err, L);
-  KScope ks(L, kKVariant);
-  k_tree_names<<<grid_for(n, kThreads, L), kThreads, 0, L.stream>>>(minkey, root, mo, n, keys,
-                                                                    err);
-}
-
-void tree_names(const uint32_t* src, const uint32_t* dst, const uint64_t* packed, uint64_t m,
-                uint32_t n, uint64_t rk, const BatchView* batch, unsigned long long* minkey,
-                uint32_t* root, uint32_t* mo, unsigned* err, const Launch& L) {
+void tree_names(const unsigned long long* minkey, uint32_t* root, uint32_t* mo, uint32_t n,
+                uint64_t rk, const BatchView* batch, unsigned* err, const Launch& L) {
   if (n == 0) return;
+  KScope ks(L, kKTreeNames);
   if (batch)
-    tree_names_impl(src, dst, packed, m, n, BatchKeys{batch->rk, batch->voff, batch->k}, minkey,
-                    root, mo, err, L);
+    k_tree_names<<<grid_for(n, kThreads, L), kThreads, 0, L.stream>>>(
+        minkey, root, mo, n, BatchKeys{batch->rk, batch->voff, batch->k}, err);
   else
-    tree_names_impl(src, dst, packed, m, n, GraphKeys{rk}, minkey, root, mo, err, L);
+    k_tree_names<<<grid_for(n, kThreads, L), kThreads, 0, L.stream>>>(minkey, root, mo, n,
+                                                                      GraphKeys{rk}, err);
 }
 
 void union_find_names(const uint32_t* src, const uint32_t* dst, const uint64_t* packed,
@@ -818,11 +870,11 @@ void union_find_names(const uint32_t* src, const uint32_t* dst, const uint64_t* 
                       unsigned* err, const Launch& L) {
   if (n == 0) return;
   {
-    KScope ks(L, kKVariant);
+    KScope ks(L, kKUnionFind);
     k_uf_init<<<grid_for(n, kThreads, L), kThreads, 0, L.stream>>>(parent, n);
   }
-  for_edges(src, dst, packed, m, n, UnionOp{parent, err}, err, L);
-  KScope ks(L, kKVariant);
+  for_edges(src, dst, packed, m, n, UnionOp{parent, err, n}, err, L);
+  KScope ks(L, kKUnionFind);
   k_uf_names<<<grid_for(n, kThreads, L), kThreads, 0, L.stream>>>(parent, mo, n, err);
   k_uf_flatten<<<grid_for(n, kThreads, L), kThreads, 0, L.stream>>>(parent, root, n, err);
 }
