@@ -65,7 +65,7 @@ def _bind(lib):
     lib.oracle_uf_labels.restype = i32
     lib.oracle_node_names.argtypes = [i32, u32, p, p, u64, u64, u32, p, p]
     lib.oracle_node_names.restype = i32
-    lib.oracle_lc_run.argtypes = [u32, p, p, u64, u64, i32, u64, u32, p, p, p, p, p, p, u32]
+    lib.oracle_lc_run.argtypes = [u32, p, p, u64, u64, i32, u64, p, u32, u32, p, p, p, p, p, p, u32]
     lib.oracle_lc_run.restype = i32
     return lib
 
@@ -146,8 +146,10 @@ class Result:
 
 
 def lc_run(n: int, src, dst, seed: int, variant: int = FOREST, finish_edges: int = 0,
-           max_rounds: int = 1 << 20, cap: int = 4096) -> Result:
+           max_rounds: int = 1 << 20, cap: int = 4096, merge_alpha=()) -> Result:
+    """merge_alpha[i] > 0: MergeToLarge step with parameter alpha_i in phase i."""
     src, dst = _u32(src), _u32(dst)
+    alpha = np.ascontiguousarray(np.asarray(merge_alpha, dtype=np.uint32).reshape(-1))
     labels = np.empty(n, dtype=np.uint32)
     n_i = np.zeros(cap, dtype=np.uint64)
     m_i = np.zeros(cap, dtype=np.uint64)
@@ -155,7 +157,8 @@ def lc_run(n: int, src, dst, seed: int, variant: int = FOREST, finish_edges: int
     J_i = np.zeros(cap, dtype=np.uint32)
     R = ctypes.c_uint32(0)
     rc = _L().oracle_lc_run(n, src.ctypes.data, dst.ctypes.data, src.size, seed, variant,
-                            finish_edges, max_rounds, labels.ctypes.data, ctypes.byref(R),
+                            finish_edges, alpha.ctypes.data if alpha.size else None, alpha.size,
+                            max_rounds, labels.ctypes.data, ctypes.byref(R),
                             n_i.ctypes.data, m_i.ctypes.data, mp_i.ctypes.data, J_i.ctypes.data,
                             cap)
     if rc == 1:

@@ -37,6 +37,16 @@
 //    merges each connected component of G_i into one node by union-find, as the
 //    paper's small-graph optimisation does on one machine (Section 7); that
 //    phase is counted as a phase.
+//  * optional MergeToLarge step (off by default; Section 5, the step used by
+//    the O(log log n) analysis on random graphs): with parameter alpha_i for
+//    phase i, a node of the contracted graph H is large when at least alpha_i
+//    vertices of G_i were merged into it; its priority is the alpha_i-th
+//    largest phase-i key among those vertices.  Every node that is not large
+//    and has a large node at distance 1 or 2 in H joins the large node of
+//    highest priority; large nodes never move (the paper merges small nodes
+//    into large ones).  Keys are distinct, so priorities are.  The step is
+//    part of phase i (it does not count as a phase) and is skipped in a
+//    union-find finish phase.
 #include <algorithm>
 #include <cstdint>
 #include <cstring>
@@ -140,6 +150,46 @@ std::vector<uint32_t> node_names(int variant, uint32_t n,
   return name;
 }
 
+// MergeToLarge (Section 5) applied to the node names of one phase: H is G_i
+// contracted by `name`; name[v] is replaced by the name of the large node
+// that v's node joins.
+void merge_to_large(uint32_t n, const std::vector<std::pair<uint32_t, uint32_t>>& E,
+                    std::vector<uint32_t>& name, uint64_t rk, uint32_t alpha) {
+  // members of every node of H (a node is identified by its name)
+  std::vector<std::vector<uint64_t>> member_keys(n);
+  for (uint32_t v = 0; v < n; ++v) member_keys[name[v]].push_back(key_of(rk, v));
+  // priority + 1 of each large node (0: not large): the alpha-th largest key
+  std::vector<uint64_t> prio(n, 0);
+  for (uint32_t x = 0; x < n; ++x) {
+    std::vector<uint64_t>& k = member_keys[x];
+    if (alpha == 0 || k.size() < alpha) continue;
+    std::sort(k.begin(), k.end(), [](uint64_t a, uint64_t b) { return a > b; });
+    prio[x] = k[alpha - 1] + 1;
+  }
+  // adjacency of H without loops
+  std::vector<std::vector<uint32_t>> adj(n);
+  for (const auto& e : E) {
+    uint32_t a = name[e.first], b = name[e.second];
+    if (a == b) continue;
+    adj[a].push_back(b);
+    adj[b].push_back(a);
+  }
+  // best priority within distance 1 (h1) and within distance 2 (h2)
+  std::vector<uint64_t> h1(prio), h2;
+  for (uint32_t x = 0; x < n; ++x)
+    for (uint32_t y : adj[x]) h1[x] = std::max(h1[x], prio[y]);
+  h2 = h1;
+  for (uint32_t x = 0; x < n; ++x)
+    for (uint32_t y : adj[x]) h2[x] = std::max(h2[x], h1[y]);
+  // a priority is a member's key, whose low half is that member's id
+  std::vector<uint32_t> target(n);
+  for (uint32_t x = 0; x < n; ++x) {
+    target[x] = x;
+    if (prio[x] == 0 && h2[x] != 0) target[x] = name[(uint32_t)(h2[x] - 1)];
+  }
+  for (uint32_t v = 0; v < n; ++v) name[v] = target[name[v]];
+}
+
 // Union-find with path halving; find returns the set's root.
 struct UF {
   std::vector<uint32_t> par;
@@ -208,13 +258,15 @@ int oracle_node_names(int variant, uint32_t n, const uint32_t* src, const uint32
   return 0;
 }
 
-// The whole round loop.  Outputs: labels[n]; *rounds = R; n_i, m_i, mp_i
+// The whole round loop; alpha[i] (i < alpha_count, 0 = off) is the
+// MergeToLarge parameter of phase i.  Outputs: labels[n]; *rounds = R; n_i, m_i, mp_i
 // (edges after relabel and loop removal, before deduplication) and J_i for
 // i < min(R, cap).  Returns 0 on success, 1 on invalid input, 2 when R > cap
 // (outputs up to cap are valid, labels are not written), 3 when max_rounds is
 // exceeded.
 int oracle_lc_run(uint32_t n, const uint32_t* src, const uint32_t* dst, uint64_t m, uint64_t seed,
-                  int variant, uint64_t finish_edges, uint32_t max_rounds, uint32_t* labels,
+                  int variant, uint64_t finish_edges, const uint32_t* alpha,
+                  uint32_t alpha_count, uint32_t max_rounds, uint32_t* labels,
                   uint32_t* rounds, uint64_t* n_i, uint64_t* m_i, uint64_t* mp_i, uint32_t* J_i,
                   uint32_t cap) {
   if (variant < FOREST || variant > TREE) return 1;
@@ -239,6 +291,7 @@ int oracle_lc_run(uint32_t n, const uint32_t* src, const uint32_t* dst, uint64_t
       for (uint32_t v = 0; v < ni; ++v) name[v] = uf.find(v);
     } else {
       name = node_names(variant, ni, E, round_key(seed, i), &J);
+      if (i < alpha_count && alpha[i] > 0) merge_to_large(ni, E, name, round_key(seed, i), alpha[i]);
     }
     // relabel every edge through the names, drop self-loops (the contraction)
     std::vector<std::pair<uint32_t, uint32_t>> E1;

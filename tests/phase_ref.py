@@ -11,6 +11,9 @@ phase a different way:
 * tree: f(v) over the open neighbourhood; the weakly connected components of
   the f-graph (scipy) are named by the lower-key vertex of their 2-cycle
   (Section 3, TreeContraction; Lemmas lem:cycle, lem:wccs);
+* MergeToLarge (Section 5): node sizes and priorities from Python lists of
+  member keys, the radius-2 ball of every node of the contracted graph read
+  off the sparsity pattern of (A_H + I)^2;
 * contraction with Python sets (relabel, drop loops, deduplicate), new ids by
   sorting the surviving names.
 
@@ -87,7 +90,34 @@ def names_tree(n, s, d, key):
     return np.array([name_of.get(comp[v], v) for v in range(n)], dtype=np.int64)
 
 
-def run(n, s, d, seed, variant=FOREST, finish_edges=0):
+def merge_to_large(n, s, d, name, key, alpha):
+    """Replace each vertex's node name by the name of the large node its node
+    joins (nodes with >= alpha members are large; priority = the alpha-th
+    largest member key; a small node joins the highest-priority large node at
+    distance <= 2 in the contracted graph)."""
+    members = {}
+    for v in range(n):
+        members.setdefault(int(name[v]), []).append(int(key[v]))
+    prio = {x: sorted(k, reverse=True)[alpha - 1] for x, k in members.items() if len(k) >= alpha}
+    a = np.asarray([int(name[u]) for u in s], dtype=np.int64)
+    b = np.asarray([int(name[u]) for u in d], dtype=np.int64)
+    keep = a != b
+    AH = sp.coo_matrix((np.ones(int(keep.sum()), dtype=np.int8), (a[keep], b[keep])),
+                       shape=(n, n)).tocsr()
+    AH = (((AH + AH.T) > 0).astype(np.int8) + sp.identity(n, dtype=np.int8, format="csr"))
+    B2 = ((AH @ AH) > 0).tocsr()
+    target = {}
+    for x in members:
+        if x in prio:
+            continue
+        ball = B2.indices[B2.indptr[x]:B2.indptr[x + 1]]
+        cand = [(prio[int(y)], int(y)) for y in ball if int(y) in prio]
+        if cand:
+            target[x] = max(cand)[1]
+    return np.array([target.get(int(name[v]), int(name[v])) for v in range(n)], dtype=np.int64)
+
+
+def run(n, s, d, seed, variant=FOREST, finish_edges=0, merge_alpha=()):
     """Returns (labels, [(n_i, m_i)], [mp_i])."""
     s = np.asarray(s, dtype=np.int64)
     d = np.asarray(d, dtype=np.int64)
@@ -114,7 +144,10 @@ def run(n, s, d, seed, variant=FOREST, finish_edges=0):
                 rep.setdefault(comp[v], v)
             name = np.array([rep[comp[v]] for v in range(ni)], dtype=np.int64)
         else:
-            name = namers[variant](ni, es, ed, keys(seed, i, ni))
+            k = keys(seed, i, ni)
+            name = namers[variant](ni, es, ed, k)
+            if i < len(merge_alpha) and merge_alpha[i] > 0:
+                name = merge_to_large(ni, es, ed, name, k, int(merge_alpha[i]))
         rel = [(min(a, b), max(a, b)) for a, b in zip(name[es], name[ed]) if a != b]
         uniq = sorted(set(rel))
         keep = sorted({x for e in uniq for x in e})

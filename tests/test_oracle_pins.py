@@ -170,6 +170,60 @@ def test_finish_matches_independent_construction():
         assert int(r.m_i[-1]) <= fin
 
 
+@pytest.mark.parametrize("variant", [oracle.FOREST, oracle.TWO_HOP, oracle.TREE])
+def test_merge_to_large_matches_independent_construction(variant):
+    """MergeToLarge (Section 5) against the radius-2-ball construction."""
+    rng = np.random.default_rng(41 + variant)
+    for n, m in [(12, 20), (40, 60), (80, 240), (200, 300), (300, 1200)]:
+        for alpha in ([2], [3, 2], [4, 4, 4], [0, 3], [6, 1, 2]):
+            s, d = random_graph(rng, n, m)
+            r = oracle.lc_run(n, s, d, 7, variant, merge_alpha=alpha)
+            labels, sizes, mps = phase_ref.run(n, s, d, 7, variant, merge_alpha=alpha)
+            assert np.array_equal(r.labels, labels)
+            assert r.sizes() == sizes and list(r.mp_i) == mps, (n, m, alpha)
+
+
+def test_merge_to_large_degenerate_parameters():
+    """alpha = 1 makes every node large (nobody moves); alpha above the vertex
+    count makes none large: both give the run without the step."""
+    rng = np.random.default_rng(43)
+    for n, m in [(50, 80), (300, 900)]:
+        s, d = random_graph(rng, n, m)
+        for variant in (oracle.FOREST, oracle.TWO_HOP, oracle.TREE):
+            plain = oracle.lc_run(n, s, d, 2, variant)
+            for alpha in ([1] * 8, [n + 1] * 8):
+                r = oracle.lc_run(n, s, d, 2, variant, merge_alpha=alpha)
+                assert r.sizes() == plain.sizes() and np.array_equal(r.labels, plain.labels)
+
+
+def test_merge_to_large_coarsens_the_first_phase():
+    """The step only merges nodes, so G_1 never has more vertices or edges
+    than without it, and labels do not change."""
+    rng = np.random.default_rng(47)
+    for t in range(30):
+        n = int(rng.integers(20, 400))
+        s, d = random_graph(rng, n, int(rng.integers(n, 4 * n)))
+        plain = oracle.lc_run(n, s, d, t, oracle.FOREST)
+        r = oracle.lc_run(n, s, d, t, oracle.FOREST, merge_alpha=[int(rng.integers(2, 8))])
+        assert np.array_equal(r.labels, plain.labels)
+        if plain.rounds > 1:
+            assert r.rounds == 1 or (r.n_i[1] <= plain.n_i[1] and r.m_i[1] <= plain.m_i[1])
+
+
+def test_merge_to_large_random_graph_lemma():
+    """Lemma lem:random: for G ~ G(n, alpha/n) with alpha >= (4 + 4c) ln n, one
+    phase of LocalContraction (two-hop label) with MergeToLarge parameter
+    alpha / 4 leaves at most n / alpha vertices w.h.p. (c = 1 here)."""
+    import math
+    for n, seed in [(2048, 1), (4096, 2), (8192, 3)]:
+        alpha = 8 * math.log(n)
+        m = int(round(alpha / n * n * (n - 1) / 2))
+        rng = np.random.default_rng(seed)
+        s, d = rng.integers(0, n, m), rng.integers(0, n, m)
+        r = oracle.lc_run(n, s, d, seed, oracle.TWO_HOP, merge_alpha=[int(alpha / 4)])
+        assert r.rounds == 1 or r.n_i[1] <= n / alpha
+
+
 def test_workload_labels_match_union_find_and_scipy():
     from paper_1807_10727_gb300 import synth
     for name in ("er16", "rmat14", "gridmix_small"):
@@ -301,6 +355,12 @@ MUTANTS = {
     "wrong SplitMix constant": ("0x94D049BB133111EBULL", "0x94D049BB133111EAULL"),
     "two-hop reads one hop": ("std::vector<uint64_t> mk2 = closed_min(n, E, mk1);",
                               "std::vector<uint64_t> mk2 = mk1;"),
+    "merge priority = alpha-th smallest key": ("[](uint64_t a, uint64_t b) { return a > b; }",
+                                               "[](uint64_t a, uint64_t b) { return a < b; }"),
+    "merge looks one hop only": ("  h2 = h1;\n  for (uint32_t x = 0; x < n; ++x)\n    for (uint32_t y : adj[x]) h2[x] = std::max(h2[x], h1[y]);",
+                                 "  h2 = h1;"),
+    "merge moves large nodes too": ("if (prio[x] == 0 && h2[x] != 0)", "if (h2[x] != 0 && h2[x] != prio[x])"),
+    "merge size counts one short": ("k.size() < alpha", "k.size() <= alpha"),
 }
 
 
@@ -313,6 +373,13 @@ def pins_pass():
             s, d = random_graph(rng, n, m)
             r = oracle.lc_run(n, s, d, 3, variant)
             labels, sizes, mps = phase_ref.run(n, s, d, 3, variant)
+            if not (np.array_equal(r.labels, labels) and r.sizes() == sizes and list(r.mp_i) == mps):
+                return False
+    for variant in (oracle.FOREST, oracle.TREE):
+        for n, m, alpha in [(80, 240, [3, 2]), (200, 300, [4]), (300, 1200, [2, 3])]:
+            s, d = random_graph(rng, n, m)
+            r = oracle.lc_run(n, s, d, 7, variant, merge_alpha=alpha)
+            labels, sizes, mps = phase_ref.run(n, s, d, 7, variant, merge_alpha=alpha)
             if not (np.array_equal(r.labels, labels) and r.sizes() == sizes and list(r.mp_i) == mps):
                 return False
     return True
