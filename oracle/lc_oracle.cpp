@@ -283,6 +283,7 @@ int oracle_lc_run(uint32_t n, const uint32_t* src, const uint32_t* dst, uint64_t
   while (!E.empty()) {
     if (i >= max_rounds) return 3;
     uint32_t J = 0;
+    bool merge = false;
     std::vector<uint32_t> name;
     if (finish_edges > 0 && E.size() <= finish_edges) {
       UF uf(ni);
@@ -291,8 +292,14 @@ int oracle_lc_run(uint32_t n, const uint32_t* src, const uint32_t* dst, uint64_t
       for (uint32_t v = 0; v < ni; ++v) name[v] = uf.find(v);
     } else {
       name = node_names(variant, ni, E, round_key(seed, i), &J);
-      if (i < alpha_count && alpha[i] > 0) merge_to_large(ni, E, name, round_key(seed, i), alpha[i]);
+      merge = i < alpha_count && alpha[i] > 0;
     }
+    // m'_i: edges that the phase's contraction leaves, loops dropped, before
+    // deduplication (and before a MergeToLarge step, which works on the
+    // contracted graph)
+    uint64_t mprime = 0;
+    for (const auto& e : E) mprime += name[e.first] != name[e.second] ? 1 : 0;
+    if (merge) merge_to_large(ni, E, name, round_key(seed, i), alpha[i]);
     // relabel every edge through the names, drop self-loops (the contraction)
     std::vector<std::pair<uint32_t, uint32_t>> E1;
     E1.reserve(E.size());
@@ -301,7 +308,6 @@ int oracle_lc_run(uint32_t n, const uint32_t* src, const uint32_t* dst, uint64_t
       if (a == b) continue;
       E1.push_back({std::min(a, b), std::max(a, b)});
     }
-    uint64_t mprime = E1.size();
     // remove duplicates
     std::sort(E1.begin(), E1.end());
     E1.erase(std::unique(E1.begin(), E1.end()), E1.end());

@@ -146,14 +146,16 @@ def run(n, s, d, seed, variant=FOREST, finish_edges=0, merge_alpha=()):
         else:
             k = keys(seed, i, ni)
             name = namers[variant](ni, es, ed, k)
-            if i < len(merge_alpha) and merge_alpha[i] > 0:
-                name = merge_to_large(ni, es, ed, name, k, int(merge_alpha[i]))
+        mp = int(np.count_nonzero(name[es] != name[ed]))
+        if not (finish_edges and len(es) <= finish_edges) and i < len(merge_alpha) \
+                and merge_alpha[i] > 0:
+            name = merge_to_large(ni, es, ed, name, k, int(merge_alpha[i]))
         rel = [(min(a, b), max(a, b)) for a, b in zip(name[es], name[ed]) if a != b]
         uniq = sorted(set(rel))
         keep = sorted({x for e in uniq for x in e})
         newid = {r: k for k, r in enumerate(keep)}
         sizes.append((ni, len(es)))
-        mps.append(len(rel))
+        mps.append(mp)
         ni = len(keep)
         es = np.array([newid[a] for a, _ in uniq], dtype=np.int64)
         ed = np.array([newid[b] for _, b in uniq], dtype=np.int64)
