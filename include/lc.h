@@ -95,6 +95,22 @@ lc_status lc_create(uint32_t n, const uint32_t* d_src, const uint32_t* d_dst, ui
  * lc_run_static always use the forest variant without finish. */
 lc_status lc_configure(lc_ctx* ctx, lc_variant variant, uint64_t finish_edges);
 
+/* MergeToLarge step (Section 5, the step of the O(log log n) analysis on
+ * random graphs), off by default.  alpha: host uint32[count], copied; phase i
+ * < count with alpha[i] > 0 ends with the step, with parameter alpha_i: a node
+ * of the phase's contracted graph is large when at least alpha_i vertices of
+ * G_i were merged into it, and its priority is the alpha_i-th largest phase-i
+ * key (rank << 32 | id) among them; every node that is not large and has a
+ * large node at distance 1 or 2 joins the large node of highest priority
+ * (large nodes do not move).  The step is part of phase i: it changes
+ * (n_{i+1}, m_{i+1}) and later phases, not the phase count's meaning nor the
+ * labels.  It is skipped after a union-find finish phase.  count = 0 turns it
+ * off.  Device scratch comes from the context's arena (about 40 bytes per
+ * node of the contracted graph plus 12 per vertex of G_i).
+ * Returns LC_ERR_INVALID for alpha == NULL with count > 0, for a batch
+ * context, or while a run of the context is in flight. */
+lc_status lc_set_merge_to_large(lc_ctx* ctx, const uint32_t* alpha, uint32_t count);
+
 typedef enum {
   LC_DEDUP_HASH = 0, /* hashed bucket partition + per-bucket hash set (default) */
   LC_DEDUP_SORT = 1  /* full LSD radix sort of the edge keys, keep the first of each run */

@@ -27,7 +27,7 @@ LC_SO = os.path.join(LIB_DIR, "liblc.so")
 ARCH_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
               "--expt-relaxed-constexpr", "-Xptxas", "-warn-spills"]
-LC_SOURCES = ["lc_abi.cu", "lc_round.cu", "lc_sort.cu"]
+LC_SOURCES = ["lc_abi.cu", "lc_round.cu", "lc_sort.cu", "lc_merge.cu"]
 
 
 def _nvcc() -> str:

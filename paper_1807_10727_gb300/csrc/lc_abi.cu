@@ -26,7 +26,8 @@ const char* kernel_name(int id) {
       "scan_flags",
       "unique_rename", "propagate",  "bucket_bounds",   "bucket_dedup",  "rename",
       "unmix",         "batch",      "two_hop",         "open_min",      "tree_names",
-      "union_find",    "identity",   "rank_probe"};
+      "union_find",    "m2l_group",  "m2l_select",      "m2l_hop",       "m2l_target",
+      "identity",      "rank_probe"};
   static_assert(sizeof(names) / sizeof(names[0]) == kNumKernels, "one name per kernel");
   return (id >= 0 && id < kNumKernels) ? names[id] : "unknown";
 }
@@ -152,6 +153,7 @@ struct DeviceGuard {
 struct RunState {
   enum State { kDone = 0, kPhase, kSortPhase, kLabels } state = kDone;
   lc_status st = LC_OK;
+  bool merge_step = false;  // the level in flight is phase i's MergeToLarge step
   uint32_t* d_labels = nullptr;
   uint32_t i = 0, ni = 0;
   uint64_t mi = 0;
@@ -189,6 +191,7 @@ struct lc_ctx {
   Prof prof;
   lc_variant variant = LC_VARIANT_FOREST;
   uint64_t finish_edges = 0;
+  std::vector<uint32_t> merge_alpha;  // MergeToLarge parameter of phase i (0: off)
 
   const uint32_t* src = nullptr;
   const uint32_t* dst = nullptr;
@@ -349,6 +352,14 @@ extern "C" lc_status lc_configure(lc_ctx* c, lc_variant variant, uint64_t finish
   return LC_OK;
 }
 
+extern "C" lc_status lc_set_merge_to_large(lc_ctx* c, const uint32_t* alpha, uint32_t count) {
+  if (!c || (count > 0 && alpha == nullptr)) return LC_ERR_INVALID;
+  if (count > 0 && c->batch != nullptr) return LC_ERR_INVALID;
+  if (c->rs.state != RunState::kDone) return LC_ERR_INVALID;
+  c->merge_alpha.assign(alpha, alpha + count);
+  return LC_OK;
+}
+
 static uint32_t round_cap(uint32_t n) { return 64 + 4 * (uint32_t)bits_for(std::max(n, 2u)); }
 
 // ---------------------------------------------------------------------------
@@ -405,11 +416,40 @@ static lc_status enqueue_phase(lc_ctx* c) {
     bv = BatchView{b->d_rk, b->voff.back(), b->k};
   }
   const BatchView* bp = c->batch ? &bv : nullptr;
-  const uint32_t* src0 = i == 0 ? c->src : nullptr;
-  const uint32_t* dst0 = i == 0 ? c->dst : nullptr;
-  // (a): ranks (and, in phase 0, each vertex's min original id = itself)
-  init_keys(c->minkey, i == 0 ? r.lv.mo : nullptr, ni, rk, bp, L);
-  if (c->finish_edges != 0 && mi <= c->finish_edges) {
+  // the input edges are read only by phase 0 itself (a merge step after
+  // phase 0 works on the packed edges that phase 0 wrote)
+  const bool first = i == 0 && !r.merge_step;
+  const uint32_t* src0 = first ? c->src : nullptr;
+  const uint32_t* dst0 = first ? c->dst : nullptr;
+  if (r.merge_step) {
+    // MergeToLarge on the graph that phase i just produced
+    const Level& prev = c->levels.back();
+    MergeScratch ms{};
+    uint32_t** u32s[] = {&ms.cnt, &ms.off, &ms.fill, &ms.list};
+    for (uint32_t** q : u32s) {
+      *q = c->arena.alloc(ni, &aerr);
+      if (aerr != cudaSuccess) return fail(c, status_of(aerr));
+    }
+    ms.members = c->arena.alloc(prev.n, &aerr);
+    if (aerr != cudaSuccess) return fail(c, status_of(aerr));
+    ms.cand = reinterpret_cast<unsigned long long*>(c->arena.alloc(2ull * prev.n, &aerr));
+    if (aerr != cudaSuccess) return fail(c, status_of(aerr));
+    unsigned long long** u64s[] = {&ms.prio, &ms.h1, &ms.h2};
+    for (unsigned long long** q : u64s) {
+      *q = reinterpret_cast<unsigned long long*>(c->arena.alloc(2ull * ni, &aerr));
+      if (aerr != cudaSuccess) return fail(c, status_of(aerr));
+    }
+    ms.ctrs = c->arena.alloc(2, &aerr);
+    if (aerr != cudaSuccess) return fail(c, status_of(aerr));
+    merge_to_large_names(prev.root, prev.scan, prev.n, rk, c->merge_alpha[i], r.packed, mi, ni,
+                         r.lv.root, r.lv.mo, ms, err, L);
+  } else {
+    // (a): ranks (and, in phase 0, each vertex's min original id = itself)
+    init_keys(c->minkey, first ? r.lv.mo : nullptr, ni, rk, bp, L);
+  }
+  if (r.merge_step) {
+    // names computed above
+  } else if (c->finish_edges != 0 && mi <= c->finish_edges) {
     // small-graph finish: one node per connected component of G_i
     union_find_names(src0, dst0, r.packed, mi, ni, reinterpret_cast<uint32_t*>(c->minkey),
                      r.lv.root, r.lv.mo, err, L);
@@ -446,7 +486,7 @@ static lc_status enqueue_phase(lc_ctx* c) {
   if (!c->dedup_sort) hist_reset(c->sort, L);
   relabel(src0, dst0, r.packed, mi, ni, r.lv.root,
           r.bits, r.keys, &c->ctr->mprime, &c->ctr->emitted, !c->dedup_sort,
-          c->dedup_sort ? nullptr : &hplan, c->sort.hist, i == 0 ? r.alt : nullptr,
+          c->dedup_sort ? nullptr : &hplan, c->sort.hist, first ? r.alt : nullptr,
           c->relabel_window_bytes, err, L);
   if (!c->dedup_sort) {
     int which = hash_dedup(r.keys, r.alt, &c->ctr->emitted, mi, hplan, hb, true, r.bits, c->flags,
@@ -578,7 +618,7 @@ static lc_status run_complete(lc_ctx* c) {
     // the label kernels report index failures through the device error word
     if (c->h_ctr->tag != c->tag && c->m > 0) return report_internal(c, "stale counters");
     if (c->h_ctr->err & kErrCorrupt) return report_corrupt(c);
-    c->last_rounds = (uint32_t)c->levels.size();
+    c->last_rounds = (uint32_t)r.hn.size();  // phases (merge steps add levels, not phases)
     r.state = RunState::kDone;
     return LC_OK;
   }
@@ -610,16 +650,26 @@ static lc_status run_complete(lc_ctx* c) {
   }
   if ((h.n_next > 0) != (h.m_next > 0) || h.n_next > r.ni || h.m_next > h.emitted)
     return report_internal(c, "inconsistent phase counters");
-  r.hn.push_back(r.ni);
-  r.hm.push_back(r.mi);
-  c->last_mp.push_back(h.mprime);
-  c->last_emitted.push_back(h.emitted);
+  const bool was_merge = r.merge_step;
+  if (!was_merge) {
+    r.hn.push_back(r.ni);
+    r.hm.push_back(r.mi);
+    c->last_mp.push_back(h.mprime);
+    c->last_emitted.push_back(h.emitted);
+  }
+  const bool finished_by_uf = !was_merge && c->finish_edges != 0 && r.mi <= c->finish_edges;
   c->levels.push_back(r.lv);
   r.ni = (uint32_t)h.n_next;
   r.mi = h.m_next;
   r.packed = r.next;
   r.mo_cur = r.mo_next;
+  r.merge_step = false;
   if (r.mi == 0) return enqueue_labels(c);
+  if (!was_merge && !finished_by_uf && r.i < c->merge_alpha.size() && c->merge_alpha[r.i] > 0) {
+    // the phase's MergeToLarge step: one more contraction level, same phase
+    r.merge_step = true;
+    return enqueue_phase(c);
+  }
   if (++r.i >= round_cap(c->n)) return fail(c, LC_ERR_NO_CONVERGENCE);
   return enqueue_phase(c);
 }

@@ -33,6 +33,10 @@ enum KernelId : int {
   kKOpenMin,
   kKTreeNames,
   kKUnionFind,
+  kKMergeGroup,
+  kKMergeSelect,
+  kKMergeHop,
+  kKMergeTarget,
   kKIdentity,
   kKRankProbe,
   kNumKernels
@@ -293,6 +297,25 @@ void tree_names(const unsigned long long* minkey, uint32_t* root, uint32_t* mo, 
 void union_find_names(const uint32_t* src, const uint32_t* dst, const uint64_t* packed,
                       uint64_t m, uint32_t n, uint32_t* parent, uint32_t* root, uint32_t* mo,
                       unsigned* err, const Launch& L);
+
+// Scratch of the MergeToLarge step: n' words for cnt, off, fill, list and
+// n' 64-bit words for prio, h1, h2 (n' = nodes of the contracted graph); n_i
+// words for members and n_i 64-bit words for cand (n_i = vertices of the
+// phase's input); two counter words.
+struct MergeScratch {
+  uint32_t *cnt, *off, *fill, *list, *members;
+  unsigned long long *cand, *prio, *h1, *h2;
+  unsigned* ctrs;
+};
+
+// MergeToLarge (Section 5) on the graph G' (n2 nodes, packed edges e[m])
+// that the last phase made from G_i (n_i vertices; root_i, scan_i its root
+// map and keep-scan; rk its key seed): t[x] = node that x joins (x itself
+// when it stays); node minima mo aggregated in place at the targets.
+void merge_to_large_names(const uint32_t* root_i, const uint32_t* scan_i, uint32_t n_i,
+                          uint64_t rk, uint32_t alpha, const uint64_t* e, uint64_t m,
+                          uint32_t n2, uint32_t* t, uint32_t* mo, const MergeScratch& s,
+                          unsigned* err, const Launch& L);
 
 // labels[v] = v (a graph without edges).
 void identity_labels(uint32_t* labels, uint32_t n, const Launch& L);

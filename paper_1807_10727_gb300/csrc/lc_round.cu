@@ -874,8 +874,11 @@ void union_find_names(const uint32_t* src, const uint32_t* dst, const uint64_t* 
     k_uf_init<<<grid_for(n, kThreads, L), kThreads, 0, L.stream>>>(parent, n);
   }
   for_edges(src, dst, packed, m, n, UnionOp{parent, err, n}, err, L);
+  {
+    KScope ks(L, kKUnionFind);
+    k_uf_names<<<grid_for(n, kThreads, L), kThreads, 0, L.stream>>>(parent, mo, n, err);
+  }
   KScope ks(L, kKUnionFind);
-  k_uf_names<<<grid_for(n, kThreads, L), kThreads, 0, L.stream>>>(parent, mo, n, err);
   k_uf_flatten<<<grid_for(n, kThreads, L), kThreads, 0, L.stream>>>(parent, root, n, err);
 }
 

@@ -24,7 +24,7 @@ LC_VARIANT_FOREST, LC_VARIANT_TWO_HOP, LC_VARIANT_TREE = 0, 1, 2
 
 # every symbol include/lc.h declares (checked by the CPU test suite)
 LC_DEDUP_HASH, LC_DEDUP_SORT = 0, 1
-EXPORTED = ("lc_create", "lc_configure", "lc_set_dedup", "lc_set_param", "lc_run", "lc_run_host",
+EXPORTED = ("lc_create", "lc_configure", "lc_set_merge_to_large", "lc_set_dedup", "lc_set_param", "lc_run", "lc_run_host",
             "lc_last_stats", "lc_profile", "lc_kernel_stats", "lc_destroy", "lc_status_str",
             "lc_rank_probe", "lc_run_static", "lc_batch_create", "lc_batch_run",
             "lc_server_create", "lc_server_submit", "lc_server_wait", "lc_server_stats",
@@ -53,6 +53,8 @@ def load(path: str | None = None):
     pu32, pu64 = ctypes.POINTER(u32), ctypes.POINTER(u64)
     lib.lc_create.argtypes = [u32, p, p, u64, u64, p, ctypes.POINTER(p)]
     lib.lc_configure.argtypes = [p, i32, u64]
+    lib.lc_set_merge_to_large.argtypes = [p, p, u32]
+    lib.lc_set_merge_to_large.restype = i32
     lib.lc_set_dedup.argtypes = [p, i32]
     lib.lc_set_param.argtypes = [p, ctypes.c_char_p, u64]
     lib.lc_run.argtypes = [p, p, pu32, pu64, pu64, u32]
@@ -116,6 +118,12 @@ def lc_create(n: int, d_src: int, d_dst: int, m: int, seed: int, stream: int) ->
 
 def lc_configure(ctx: int, variant: int, finish_edges: int = 0) -> None:
     _check(load().lc_configure(ctx, variant, finish_edges), "lc_configure")
+
+
+def lc_set_merge_to_large(ctx: int, alpha) -> None:
+    a = np.ascontiguousarray(np.asarray(alpha, dtype=np.uint32).reshape(-1))
+    _check(load().lc_set_merge_to_large(ctx, a.ctypes.data if a.size else None, a.size),
+           "lc_set_merge_to_large")
 
 
 def lc_set_dedup(ctx: int, mode: int) -> None:
@@ -239,7 +247,7 @@ class LocalContraction:
 
     def __init__(self, n: int, src=None, dst=None, m: int | None = None, seed: int = 0,
                  stream=None, variant: int = LC_VARIANT_FOREST, finish_edges: int = 0,
-                 dedup: int = LC_DEDUP_HASH):
+                 dedup: int = LC_DEDUP_HASH, merge_alpha=()):
         if src is None:
             if m is None:
                 raise ValueError("m is required when the context owns its inputs")
@@ -257,6 +265,8 @@ class LocalContraction:
             lc_configure(self.ctx, variant, finish_edges)
         if dedup != LC_DEDUP_HASH:
             lc_set_dedup(self.ctx, dedup)
+        if len(merge_alpha):
+            lc_set_merge_to_large(self.ctx, merge_alpha)
 
     def run(self, labels=None, cap: int = 1024):
         import torch
