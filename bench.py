@@ -25,6 +25,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import subprocess
 import sys
@@ -133,11 +134,20 @@ def bench_variants(ctx, labels, stream, steps, warmup, peak, lc):
     and context as the headline: edges/s, phases and the path roofline."""
     import torch
     out = {}
-    cases = [("two_hop", lc.LC_VARIANT_TWO_HOP, 0), ("tree", lc.LC_VARIANT_TREE, 0),
-             ("forest_finish_4M", lc.LC_VARIANT_FOREST, 1 << 22),
-             ("forest_finish_64M", lc.LC_VARIANT_FOREST, 1 << 26)]
-    for name, variant, finish in cases:
+    # MergeToLarge parameters: alpha_0 = 4 ln n, squared every phase (the
+    # recurrence of the O(log log n) argument, Section 5), capped at n
+    a, alpha = 4 * math.log(ctx.n), []
+    for _ in range(12):
+        alpha.append(int(min(a, ctx.n)))
+        a *= a
+    cases = [("two_hop", lc.LC_VARIANT_TWO_HOP, 0, ()), ("tree", lc.LC_VARIANT_TREE, 0, ()),
+             ("forest_finish_4M", lc.LC_VARIANT_FOREST, 1 << 22, ()),
+             ("forest_finish_64M", lc.LC_VARIANT_FOREST, 1 << 26, ()),
+             ("forest_merge_to_large", lc.LC_VARIANT_FOREST, 0, alpha),
+             ("two_hop_merge_to_large", lc.LC_VARIANT_TWO_HOP, 0, alpha)]
+    for name, variant, finish, merge in cases:
         lc.lc_configure(ctx.ctx, variant, finish)
+        lc.lc_set_merge_to_large(ctx.ctx, merge)
         for _ in range(warmup):
             _, res = ctx.run(labels)
         mp, _ = lc.lc_last_stats(ctx.ctx)
@@ -161,8 +171,11 @@ def bench_variants(ctx, labels, stream, steps, warmup, peak, lc):
                      "path_frac": pb / (ms / 1e3) / 1e9 / peak,
                      "gpu_launches_per_step": sum(v[0] for v in ks.values()) / steps,
                      "top_kernels_ms": {k: round(t, 3) for t, k in top}}
+        if merge:
+            out[name]["merge_alpha"] = list(merge[:res.rounds])
         log(f"variant {name}: {ms:.2f} ms/step, {res.rounds} phases")
     lc.lc_configure(ctx.ctx, lc.LC_VARIANT_FOREST, 0)
+    lc.lc_set_merge_to_large(ctx.ctx, [])
     return out
 
 

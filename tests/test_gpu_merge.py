@@ -128,3 +128,20 @@ def test_merge_rejections(lc_lib, cuda):
         assert res.rounds == ref.rounds and list(zip(res.n_i, res.m_i)) == ref.sizes()
         assert np.array_equal(labels.cpu().numpy().view(np.uint32), ref.labels)
     ctx.close()
+
+
+@pytest.mark.slow
+def test_merge_er_few_phases(lc_lib, cuda):
+    """ER G(n, alpha/n), alpha = 4 ln n, n = 2^20 (~2.9e7 edges): with
+    MergeToLarge (alpha_0 = alpha, squared every phase) the run is bit-exact
+    with the oracle and needs no more phases than without it (Section 5's
+    O(log log n) bound; log2 log2 n ~ 4.3 here)."""
+    n = 1 << 20
+    a = 4 * math.log(n)
+    m = int(round(a / n * n * (n - 1) / 2))
+    rng = np.random.default_rng(71)
+    s = rng.integers(0, n, m).astype(np.uint32)
+    d = rng.integers(0, n, m).astype(np.uint32)
+    res, ref = assert_parity(n, s, d, 11, cuda, log_alpha(n), lc.LC_VARIANT_TWO_HOP)
+    plain = oracle.lc_run(n, s, d, 11, variant=oracle.TWO_HOP)
+    assert res.rounds <= plain.rounds and res.rounds <= 5
