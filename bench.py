@@ -62,7 +62,7 @@ def peaks():
 # sector amplification is not algorithmic and is not counted; a phase-0
 # minimum window pass or a relabel half-pass reads all edges, so each such
 # launch counts that read.
-def algorithmic_bytes(n_i, m_i, mp_i, em_i, window_passes, relabel_split):
+def algorithmic_bytes(n_i, m_i, mp_i, em_i, passes_i, window_passes, relabel_split):
     per = {}
 
     def add(k, b):
@@ -84,7 +84,12 @@ def algorithmic_bytes(n_i, m_i, mp_i, em_i, window_passes, relabel_split):
             add("edge_min_packed", 8 * m + 8 * n)
             add("relabel_packed", 8 * m + 8 * em + 4 * n)
         add("jump", 8 * n + 4 * n + 4 * n)
-        add("sort_pass", 16 * em * hash_passes(m))
+        add("sort_pass", 16 * em * passes_i[i])
+        if m >= LATE_PLAN_EDGES:
+            # phases that size their buckets after the relabel: one read of
+            # the keys for the distinct-count sketch, one for the histogram
+            add("hll", 8 * em)
+            add("sort_hist", 8 * em)
         add("bucket_dedup", 8 * em + 8 * m_next + 2 * n)
         add("rename", 16 * m_next + 4 * n)
         add("scan_flags", n + 4 * n + 8 * (m_next and n))
@@ -92,13 +97,7 @@ def algorithmic_bytes(n_i, m_i, mp_i, em_i, window_passes, relabel_split):
     return per
 
 
-def hash_passes(m):
-    """Partition passes of the hashed dedup for m edges (digits <= 8 bits over
-    the bucket bits, 2048 keys per bucket)."""
-    hb = 0
-    while hb < 24 and (2048 << hb) < m:
-        hb += 1
-    return (hb + 7) // 8
+LATE_PLAN_EDGES = 1 << 22  # phases of at least this many edges plan their dedup after relabel
 
 
 def path_bytes(n_i, m_i, mp_i):
@@ -485,6 +484,7 @@ def main():
     for _ in range(max(3, args.warmup)):
         _, res = ctx.run(labels)
     mp, em = lc.lc_last_stats(ctx.ctx)
+    passes = lc.lc_last_passes(ctx.ctx)
 
     clocks = ClockSampler(gpu_id_for(local))
     ctx.profile(not args.no_profile)
@@ -515,7 +515,7 @@ def main():
     peak, peak_kind = peaks()
     wpass = max(1, -(-8 * g.n // (192 << 20)))
     split = g.n < (1 << 31) and 4 * g.n > (160 << 20)
-    alg = algorithmic_bytes(res.n_i, res.m_i, mp, em, wpass, split)
+    alg = algorithmic_bytes(res.n_i, res.m_i, mp, em, passes, wpass, split)
     top = max(kstats.items(), key=lambda kv: kv[1][1])
     top_name, (top_launches, top_ms) = top
     roof = None

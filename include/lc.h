@@ -135,6 +135,21 @@ lc_status lc_set_dedup(lc_ctx* ctx, lc_dedup mode);
  *                   is larger than this, phase 0 relabels the input edges in
  *                   two passes, each gathering roots from one half of the
  *                   array (default 160 MiB; needs n < 2^31).
+ *   "relabel_cache_slots"  size (a power of two in [2^10, 2^26], or 0 = off)
+ *                   of a device-wide direct-mapped cache of relabelled keys
+ *                   used in phases with at least 2^22 edges: a key already in
+ *                   it is not written again, so repeated edges between the
+ *                   same pair of nodes reach the deduplication a few times
+ *                   instead of once per edge.  8 bytes per slot of device
+ *                   memory, reallocated on change (default 2^22 for contexts
+ *                   of at least 2^22 edges, else 0).  Not while a run is in
+ *                   flight.
+ *   "relabel_cache_admit"  a key missing from that cache enters it at one in
+ *                   2^value of its occurrences (0..16, default 2), so that
+ *                   keys seen once rarely evict repeated ones.
+ * Phases with at least 2^22 edges also size their deduplication buckets from
+ * a HyperLogLog estimate (Flajolet et al. 2007) of the distinct relabelled
+ * keys, read back after the relabel step; the others from m_i.
  * Unknown names or out-of-range values give LC_ERR_INVALID. */
 lc_status lc_set_param(lc_ctx* ctx, const char* name, uint64_t value);
 
@@ -192,6 +207,13 @@ lc_status lc_batch_run(lc_ctx* ctx, uint32_t* d_labels, uint32_t* rounds, uint64
  * reads fewer keys; emitted_i <= mp_i).  Returns the phase count in *rounds. */
 lc_status lc_last_stats(const lc_ctx* ctx, uint32_t* rounds, uint64_t* mp_i, uint64_t* emitted_i,
                         uint32_t cap);
+
+/* Partition passes that the hashed deduplication of each phase of the last
+ * run planned (host uint32[cap]; 0 for LC_DEDUP_SORT and for phases small
+ * enough for one bucket); no counterpart in the paper, used to count the
+ * bytes the passes must move.  Returns the phase count in *rounds, and
+ * LC_ERR_INVALID if cap is smaller than it (the first cap are filled). */
+lc_status lc_last_passes(const lc_ctx* ctx, uint32_t* rounds, uint32_t* passes_i, uint32_t cap);
 
 /* Per-kernel instrumentation (no counterpart in the paper; used to measure
  * the kernels against the HBM roofline).  Launch counts of every kernel are

@@ -2,6 +2,7 @@
 // phase loop of LocalContraction (arXiv 1807.10727, Section 3), one CUDA
 // stream, one device synchronisation per phase to read the phase's sizes.
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <chrono>
 #include <condition_variable>
@@ -27,7 +28,7 @@ const char* kernel_name(int id) {
       "unique_rename", "propagate",  "bucket_bounds",   "bucket_dedup",  "rename",
       "unmix",         "batch",      "two_hop",         "open_min",      "tree_names",
       "union_find",    "m2l_group",  "m2l_select",      "m2l_hop",       "m2l_target",
-      "identity",      "rank_probe"};
+      "identity",      "rank_probe", "hll"};
   static_assert(sizeof(names) / sizeof(names[0]) == kNumKernels, "one name per kernel");
   return (id >= 0 && id < kNumKernels) ? names[id] : "unknown";
 }
@@ -127,6 +128,15 @@ struct Arena {
 
 uint64_t host_mix(uint64_t z) { return splitmix_mix(z); }
 
+// Phases with at least this many edges use the relabel's device-wide
+// duplicate cache, and size their deduplication buckets from a HyperLogLog
+// estimate of the distinct keys read back after the relabel (below it the
+// block caches and the dedup are cheap, and a mid-phase wait would cost more
+// than it saves).
+constexpr uint64_t kGCacheMinEdges = 1ull << 22;
+constexpr uint32_t kGCacheSlots = 1u << 22;  // default size (32 MB)
+constexpr int kGCacheAdmit = 2;              // default admission: 1 in 4 occurrences
+
 // Stream seed of phase i: output i+1 of the SplitMix64 stream seeded with seed.
 uint64_t phase_seed(uint64_t seed, uint32_t i) { return host_mix(seed + (uint64_t)(i + 1) * kGamma); }
 
@@ -151,9 +161,10 @@ struct DeviceGuard {
 
 // Progress of one run of the phase loop (see run_begin / run_complete).
 struct RunState {
-  enum State { kDone = 0, kPhase, kSortPhase, kLabels } state = kDone;
+  enum State { kDone = 0, kRelabel, kPhase, kSortPhase, kLabels } state = kDone;
   lc_status st = LC_OK;
   bool merge_step = false;  // the level in flight is phase i's MergeToLarge step
+  uint32_t passes = 0;      // partition passes planned for the level in flight
   uint32_t* d_labels = nullptr;
   uint32_t i = 0, ni = 0;
   uint64_t mi = 0;
@@ -201,6 +212,11 @@ struct lc_ctx {
 
   unsigned long long* minkey = nullptr;
   unsigned long long* minkey2 = nullptr;  // second-hop minima (two-hop variant only)
+  unsigned long long* gcache = nullptr;   // relabel's device-wide duplicate cache
+  uint32_t gcache_slots = 0;
+  int gcache_admit = kGCacheAdmit;        // log2 of the cache's admission period
+  uint32_t* d_hll = nullptr;              // HyperLogLog registers of the relabel's keys
+  uint32_t* h_hll = nullptr;              // (pinned host copy)
   uint8_t* flags = nullptr;
   uint64_t* ebuf[2] = {nullptr, nullptr};
   Counters* ctr = nullptr;
@@ -218,6 +234,7 @@ struct lc_ctx {
   uint32_t last_rounds = 0;
   std::vector<uint64_t> last_mp;
   std::vector<uint64_t> last_emitted;
+  std::vector<uint32_t> last_passes;  // partition passes of each phase's hashed dedup
 
   cudaEvent_t ev = nullptr;  // completion of the work enqueued last (none: sync the stream)
   RunState rs;
@@ -246,6 +263,9 @@ static void free_ctx(lc_ctx* c) {
   cudaFree(c->own_labels);
   cudaFree(c->minkey);
   cudaFree(c->minkey2);
+  cudaFree(c->gcache);
+  cudaFree(c->d_hll);
+  if (c->h_hll) cudaFreeHost(c->h_hll);
   cudaFree(c->flags);
   cudaFree(c->ebuf[0]);
   cudaFree(c->ebuf[1]);
@@ -288,6 +308,12 @@ static lc_status alloc_ctx(lc_ctx* c) {
   LC_TRY(cudaMalloc(&c->sort.hist, sizeof(uint32_t) * kMaxPasses * kRadixMax));
   LC_TRY(cudaMalloc(&c->sort.tickets, sizeof(unsigned) * 16));
   LC_TRY(cudaMalloc(&c->bounds, sizeof(uint32_t) * ((1ull << hash_bits_for(m)) + 1)));
+  if (m >= kGCacheMinEdges) {
+    c->gcache_slots = kGCacheSlots;
+    LC_TRY(cudaMalloc(&c->gcache, 8ull * c->gcache_slots));
+    LC_TRY(cudaMalloc(&c->d_hll, 4ull * kHllRegs));
+    LC_TRY(cudaMallocHost(&c->h_hll, 4ull * kHllRegs));
+  }
   // first arena chunk: 3 arrays per level for levels whose sizes sum to 2n,
   // plus the next level's min-original-id array
   LC_TRY(c->arena.init(4 * (2 * n + 256)));
@@ -376,6 +402,7 @@ static lc_status record(lc_ctx* c) {
 }
 
 static lc_status enqueue_sort_dedup(lc_ctx* c);
+static lc_status enqueue_dedup(lc_ctx* c, const PassPlan& hplan, int hb, bool hist_ready);
 
 static lc_status fail(lc_ctx* c, lc_status st) {
   c->rs.st = st;
@@ -481,16 +508,66 @@ static lc_status enqueue_phase(lc_ctx* c) {
     return fail(c, LC_ERR_CUDA);
   r.keys = (r.packed == c->ebuf[0]) ? c->ebuf[1] : c->ebuf[0];
   r.alt = (r.keys == c->ebuf[0]) ? c->ebuf[1] : c->ebuf[0];
+  const bool big = mi >= kGCacheMinEdges;
+  // large phases plan their buckets after the relabel, from the estimated
+  // number of distinct keys; the others from m_i, with the histogram fused
+  const bool late = !c->dedup_sort && big && c->d_hll != nullptr;
   PassPlan hplan{};
-  const int hb = hash_plan(mi, &hplan);
-  if (!c->dedup_sort) hist_reset(c->sort, L);
+  const int hb = late ? 0 : hash_plan(mi, &hplan);
+  if (!c->dedup_sort && !late) hist_reset(c->sort, L);
+  if (late && cudaMemsetAsync(c->d_hll, 0, 4ull * kHllRegs, c->stream) != cudaSuccess)
+    return fail(c, LC_ERR_CUDA);
+  const bool use_gcache = c->gcache != nullptr && big;
+  if (use_gcache &&
+      cudaMemsetAsync(c->gcache, 0xFF, 8ull * c->gcache_slots, c->stream) != cudaSuccess)
+    return fail(c, LC_ERR_CUDA);
   relabel(src0, dst0, r.packed, mi, ni, r.lv.root,
           r.bits, r.keys, &c->ctr->mprime, &c->ctr->emitted, !c->dedup_sort,
-          c->dedup_sort ? nullptr : &hplan, c->sort.hist, first ? r.alt : nullptr,
-          c->relabel_window_bytes, err, L);
+          (c->dedup_sort || late) ? nullptr : &hplan, c->sort.hist, first ? r.alt : nullptr,
+          c->relabel_window_bytes, use_gcache ? c->gcache : nullptr,
+          use_gcache ? c->gcache_slots : 0, c->gcache_admit, err, L);
+  if (late) {
+    hll_sketch(r.keys, &c->ctr->emitted, mi, c->d_hll, L);
+    stamp_counters(c->ctr, ++c->tag, L);
+    if (cudaMemcpyAsync(c->h_ctr, c->ctr, sizeof(Counters), cudaMemcpyDeviceToHost, c->stream) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(c->h_hll, c->d_hll, 4ull * kHllRegs, cudaMemcpyDeviceToHost,
+                        c->stream) != cudaSuccess)
+      return fail(c, LC_ERR_CUDA);
+    r.state = RunState::kRelabel;
+    lc_status st = record(c);
+    return st == LC_OK ? st : fail(c, st);
+  }
+  return enqueue_dedup(c, hplan, hb, true);
+}
+
+// HyperLogLog estimate of the number of distinct keys from the registers
+// (Flajolet, Fusy, Gandouet, Meunier 2007; linear counting for small counts).
+static double hll_estimate(const uint32_t* reg) {
+  const double m = kHllRegs;
+  double sum = 0.0;
+  uint32_t zeros = 0;
+  for (int i = 0; i < kHllRegs; ++i) {
+    sum += std::ldexp(1.0, -(int)reg[i]);
+    zeros += reg[i] == 0 ? 1u : 0u;
+  }
+  double e = (0.7213 / (1.0 + 1.079 / m)) * m * m / sum;
+  if (e <= 2.5 * m && zeros > 0) e = m * std::log(m / zeros);
+  return e;
+}
+
+// Steps (d2) and (d3) of phase rs.i on the relabelled keys in rs.keys, then
+// the copy of the phase counters to the host.
+static lc_status enqueue_dedup(lc_ctx* c, const PassPlan& hplan, int hb, bool hist_ready) {
+  RunState& r = c->rs;
+  const Launch& L = c->L;
+  unsigned* err = &c->ctr->err;
+  const uint32_t ni = r.ni;
+  const uint64_t mi = r.mi;
+  r.passes = c->dedup_sort ? 0u : (uint32_t)hplan.passes;
   if (!c->dedup_sort) {
-    int which = hash_dedup(r.keys, r.alt, &c->ctr->emitted, mi, hplan, hb, true, r.bits, c->flags,
-                           ni, c->bounds, &c->ctr->m_next, c->sort, err, L);
+    int which = hash_dedup(r.keys, r.alt, &c->ctr->emitted, mi, hplan, hb, hist_ready, r.bits,
+                           c->flags, ni, c->bounds, &c->ctr->m_next, c->sort, err, L);
     r.part = which ? r.alt : r.keys;
     r.next = which ? r.keys : r.alt;
     scan_flags(c->flags, r.lv.scan, ni, r.lv.mo, r.mo_next, &c->ctr->n_next, c->sort, err, L);
@@ -556,6 +633,7 @@ static lc_status run_begin(lc_ctx* c, uint32_t* d_labels) {
   c->last_rounds = 0;
   c->last_mp.clear();
   c->last_emitted.clear();
+  c->last_passes.clear();
   c->levels.clear();
   c->arena.reset();
   if (c->n == 0) {
@@ -622,12 +700,27 @@ static lc_status run_complete(lc_ctx* c) {
     r.state = RunState::kDone;
     return LC_OK;
   }
-  if (r.state != RunState::kPhase && r.state != RunState::kSortPhase) return r.st;
+  if (r.state != RunState::kPhase && r.state != RunState::kSortPhase &&
+      r.state != RunState::kRelabel)
+    return r.st;
   const Counters& h = *c->h_ctr;
   if (h.tag != c->tag) return report_internal(c, "stale counters");
   if (h.err & kErrCorrupt) return report_corrupt(c);
   if (h.err & kErrBadVertex) return fail(c, LC_ERR_INVALID);
   if (h.err & kErrTimeout) return fail(c, LC_ERR_TIMEOUT);
+  if (r.state == RunState::kRelabel) {
+    // buckets of at most 1.5 kBucketTarget distinct keys on average (a 5%
+    // margin on the estimate, whose standard error is 2.3%), which keeps the
+    // bucket sets below three quarters full; never sized above the written keys
+    if (h.emitted > r.mi || h.mprime > r.mi)
+      return report_internal(c, "inconsistent relabel counters");
+    const double est = hll_estimate(c->h_hll) * 1.05 / 1.5 + 1.0;
+    const uint64_t target = std::min<uint64_t>(std::max<uint64_t>(h.emitted, 1),
+                                               (uint64_t)std::min(est, (double)r.mi));
+    PassPlan hplan{};
+    const int hb = hash_plan(target, &hplan);
+    return enqueue_dedup(c, hplan, hb, false);
+  }
   if (r.state == RunState::kPhase && (h.err & kErrOverflow)) {
     // a bucket held more distinct keys than its shared-memory set: redo this
     // phase's deduplication by a full sort of the intact keys
@@ -656,6 +749,7 @@ static lc_status run_complete(lc_ctx* c) {
     r.hm.push_back(r.mi);
     c->last_mp.push_back(h.mprime);
     c->last_emitted.push_back(h.emitted);
+    c->last_passes.push_back(r.passes);
   }
   const bool finished_by_uf = !was_merge && c->finish_edges != 0 && r.mi <= c->finish_edges;
   c->levels.push_back(r.lv);
@@ -830,6 +924,15 @@ extern "C" lc_status lc_last_stats(const lc_ctx* c, uint32_t* rounds, uint64_t* 
   return LC_OK;
 }
 
+extern "C" lc_status lc_last_passes(const lc_ctx* c, uint32_t* rounds, uint32_t* passes_i,
+                                    uint32_t cap) {
+  if (!c) return LC_ERR_INVALID;
+  if (rounds) *rounds = c->last_rounds;
+  for (uint32_t i = 0; i < std::min<uint32_t>(cap, (uint32_t)c->last_passes.size()); ++i)
+    if (passes_i) passes_i[i] = c->last_passes[i];
+  return c->last_passes.size() > cap ? LC_ERR_INVALID : LC_OK;
+}
+
 extern "C" lc_status lc_set_dedup(lc_ctx* c, lc_dedup mode) {
   if (!c) return LC_ERR_INVALID;
   if (mode != LC_DEDUP_HASH && mode != LC_DEDUP_SORT) return LC_ERR_INVALID;
@@ -846,6 +949,26 @@ extern "C" lc_status lc_set_param(lc_ctx* c, const char* name, uint64_t value) {
   }
   if (std::strcmp(name, "relabel_window_bytes") == 0) {
     c->relabel_window_bytes = value;
+    return LC_OK;
+  }
+  if (std::strcmp(name, "relabel_cache_admit") == 0) {
+    if (value > 16) return LC_ERR_INVALID;
+    c->gcache_admit = (int)value;
+    return LC_OK;
+  }
+  if (std::strcmp(name, "relabel_cache_slots") == 0) {
+    if (value != 0 && (value < 1024 || value > (1ull << 26) || (value & (value - 1)) != 0))
+      return LC_ERR_INVALID;
+    if (c->rs.state != RunState::kDone) return LC_ERR_INVALID;
+    DeviceGuard g(c->device);
+    LC_TRY(cudaStreamSynchronize(c->stream));
+    cudaFree(c->gcache);
+    c->gcache = nullptr;
+    c->gcache_slots = 0;
+    if (value != 0) {
+      LC_TRY(cudaMalloc(&c->gcache, 8ull * value));
+      c->gcache_slots = (uint32_t)value;
+    }
     return LC_OK;
   }
   return LC_ERR_INVALID;
@@ -1027,7 +1150,8 @@ uint64_t ctx_bytes(uint64_t n, uint64_t m) {
   const uint64_t status = std::max(sort_status_words(m), sort_status_words(n)) * 8;
   const uint64_t bounds = 4 * ((1ull << hash_bits_for(m)) + 1);
   const uint64_t arena = 4 * std::max<uint64_t>(4 * (2 * n + 256), 1024);
-  return 8 * std::max<uint64_t>(n, 1) + n + 32 + 16 * std::max<uint64_t>(m, 2) + status +
+  const uint64_t gcache = m >= kGCacheMinEdges ? 8ull * kGCacheSlots + 4ull * kHllRegs : 0;
+  return gcache + 8 * std::max<uint64_t>(n, 1) + n + 32 + 16 * std::max<uint64_t>(m, 2) + status +
          bounds + arena + 8 * std::max<uint64_t>(m, 1) + 4 * std::max<uint64_t>(n, 1) +
          sizeof(Counters) + 4096 + 16 * 4 + 4ull * kMaxPasses * kRadixMax + (1u << 16);
 }

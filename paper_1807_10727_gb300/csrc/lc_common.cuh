@@ -99,6 +99,20 @@ static_assert(offsetof(Counters, bad_limit) == offsetof(Counters, err) + 16, "la
 // recorded next to the error word, see Counters) when idx >= limit.  Kernels
 // skip the access when it fails, so corrupted data gives an error status, not
 // a memory fault.
+// atomicMin / atomicMax preceded by a read through L2: the stored values
+// only move one way, so a read value is never past the current one, and a
+// candidate that does not beat it cannot change the word.  Addresses that many
+// threads update (hubs) then take few atomics instead of one per update.
+__device__ __forceinline__ void min_if_lower(unsigned long long* p, unsigned long long v) {
+  if (v < __ldcg(p)) atomicMin(p, v);
+}
+__device__ __forceinline__ void min_if_lower(unsigned* p, unsigned v) {
+  if (v < __ldcg(p)) atomicMin(p, v);
+}
+__device__ __forceinline__ void max_if_higher(unsigned long long* p, unsigned long long v) {
+  if (v > __ldcg(p)) atomicMax(p, v);
+}
+
 __device__ __forceinline__ bool index_ok(unsigned* err, uint32_t kernel, uint64_t idx,
                                          uint64_t limit) {
   if (idx < limit) return true;

@@ -39,6 +39,7 @@ enum KernelId : int {
   kKMergeTarget,
   kKIdentity,
   kKRankProbe,
+  kKHll,
   kNumKernels
 };
 
@@ -100,6 +101,8 @@ static_assert(kRadixMax % 256 == 0, "scan kernels assume whole digits per thread
 constexpr int kMaxPasses = 8;
 constexpr int kBucketTarget = 2048;  // average keys per dedup bucket
 constexpr int kMaxHashBits = 24;
+constexpr int kHllBits = 11;                 // HyperLogLog: 2^11 registers
+constexpr int kHllRegs = 1 << kHllBits;
 
 // Digit of a key in one pass: bits [shift, shift + bits).
 struct DigitFn {
@@ -161,6 +164,13 @@ int hash_plan(uint64_t max_count, PassPlan* plan);
 
 // Zero the digit counts of s.hist (before a producer accumulates them).
 void hist_reset(SortScratch& s, const Launch& L);
+
+// HyperLogLog registers (Flajolet, Fusy, Gandouet, Meunier 2007) of the
+// *d_count mixed keys in keys: register = top kHllBits bits, value = max
+// position of the first one bit below them.  hll: kHllRegs words, zero
+// before the call.
+void hll_sketch(const uint64_t* keys, const unsigned long long* d_count, uint64_t max_count,
+                uint32_t* hll, const Launch& L);
 
 // Duplicate removal without a full sort, on mixed keys (key_mix of
 // a << half_bits | b): a stable LSD partition of keys[0, *d_count) by their
@@ -260,12 +270,16 @@ void jump(unsigned long long* minkey, uint32_t* root, uint32_t* mo, uint32_t n, 
 // two passes, each gathering from one L2-sized half of root, with `tmp`
 // (8 bytes per edge) holding the half-resolved edges in between.  *mprime gets the number of non-loop edges;
 // *emitted the number of keys written, which omits repeats of a key that the
-// same block has already written (the written keys hold every distinct key).
+// same block has already written or that the device-wide cache holds (gcache:
+// gslots 64-bit slots, a power of two, all ~0 when the phase's relabel
+// starts; nullptr / 0 = no such cache; a missing key enters it at one in
+// 2^admit of its occurrences).  The written keys hold every distinct key.
 void relabel(const uint32_t* src, const uint32_t* dst, const uint64_t* packed, uint64_t m,
              uint32_t n, const uint32_t* root, int bits, uint64_t* keys_out,
              unsigned long long* mprime, unsigned long long* emitted, bool mix,
              const PassPlan* plan, uint32_t* ghist, uint64_t* tmp, uint64_t window_bytes,
-             unsigned* err, const Launch& L);
+             unsigned long long* gcache, uint32_t gslots, int admit, unsigned* err,
+             const Launch& L);
 
 // labels_out[v] = kept(root[v]) ? labels_up[scan[root[v]]] : mo[root[v]], with
 // kept(r) = scan[r+1] > scan[r].  labels_out may alias root.

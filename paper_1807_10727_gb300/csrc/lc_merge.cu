@@ -156,8 +156,8 @@ __global__ void __launch_bounds__(kThreads) k_m2l_hop(const uint64_t* __restrict
     const uint32_t a = (uint32_t)(x >> 32), b = (uint32_t)x;
     if (!index_ok(err, kKMergeHop, max(a, b), n2)) continue;
     const unsigned long long pa = src[a], pb = src[b];
-    if (pa > pb) atomicMax(&dst[b], pa);
-    else if (pb > pa) atomicMax(&dst[a], pb);
+    if (pa > pb) max_if_higher(&dst[b], pa);
+    else if (pb > pa) max_if_higher(&dst[a], pb);
   }
 }
 
@@ -188,7 +188,7 @@ __global__ void k_m2l_target(const unsigned long long* __restrict__ prio,
       }
     }
     t[x] = y;
-    if (y != (uint32_t)x) atomicMin(&mo[y], mo[x]);
+    if (y != (uint32_t)x) min_if_lower(&mo[y], mo[x]);
   }
 }
 

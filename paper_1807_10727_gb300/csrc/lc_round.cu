@@ -99,12 +99,12 @@ __device__ __forceinline__ void min_edge_window(uint32_t u, uint32_t v, uint32_t
   uint64_t ku, kv;
   keys.pair(u, v, ku, kv);
   if (kOpen) {
-    if (u - lo < span) atomicMin(&minkey[u], (unsigned long long)kv);
-    if (v - lo < span) atomicMin(&minkey[v], (unsigned long long)ku);
+    if (u - lo < span) min_if_lower(&minkey[u], (unsigned long long)kv);
+    if (v - lo < span) min_if_lower(&minkey[v], (unsigned long long)ku);
     return;
   }
   const uint32_t hi = ku < kv ? v : u;
-  if (hi - lo < span) atomicMin(&minkey[hi], (unsigned long long)(ku < kv ? ku : kv));
+  if (hi - lo < span) min_if_lower(&minkey[hi], (unsigned long long)(ku < kv ? ku : kv));
 }
 
 // Input edges as two uint32 arrays; `vec` = both arrays 16-byte aligned.
@@ -146,12 +146,12 @@ __device__ __forceinline__ void min_edge_packed(uint64_t x, const K& keys,
   uint64_t ka, kb;
   keys.pair(a, b, ka, kb);
   if (kOpen) {
-    atomicMin(&minkey[a], (unsigned long long)kb);
-    atomicMin(&minkey[b], (unsigned long long)ka);
+    min_if_lower(&minkey[a], (unsigned long long)kb);
+    min_if_lower(&minkey[b], (unsigned long long)ka);
   } else if (ka < kb) {
-    atomicMin(&minkey[b], (unsigned long long)ka);
+    min_if_lower(&minkey[b], (unsigned long long)ka);
   } else {
-    atomicMin(&minkey[a], (unsigned long long)kb);
+    min_if_lower(&minkey[a], (unsigned long long)kb);
   }
 }
 
@@ -262,7 +262,7 @@ __global__ void __launch_bounds__(kThreads) k_jump(unsigned long long* minkey,
         p = q;
       }
       minkey[v] = p;  // compress: later chases through v go straight to the root
-      atomicMin(&mo[p], mo[v]);
+      min_if_lower(&mo[p], mo[v]);
     }
     root[v] = p;
   }
@@ -303,8 +303,8 @@ __global__ void __launch_bounds__(kThreads) k_for_edges(const uint32_t* __restri
 // endpoint with the larger mk1 can improve (mk2 <= mk1), so one atomic.
 __device__ __forceinline__ void two_hop_apply(uint32_t u, uint32_t v, unsigned long long a,
                                               unsigned long long b, unsigned long long* mk2) {
-  if (a < b) atomicMin(&mk2[v], a);
-  else if (b < a) atomicMin(&mk2[u], b);
+  if (a < b) min_if_lower(&mk2[v], a);
+  else if (b < a) min_if_lower(&mk2[u], b);
 }
 
 // Edges as uint32 arrays (phase 0; `vec` = 16-byte aligned; ids >= n were
@@ -418,7 +418,7 @@ __global__ void k_two_hop_names(const unsigned long long* __restrict__ mk2, uint
     uint32_t name = (uint32_t)mk2[v];
     if (!index_ok(err, kKTwoHop, name, n)) name = (uint32_t)v;
     root[v] = name;
-    atomicMin(&nmo[name], mo[v]);
+    min_if_lower(&nmo[name], mo[v]);
   }
 }
 
@@ -454,7 +454,7 @@ __global__ void __launch_bounds__(kThreads) k_tree_names(const unsigned long lon
       name = (q == p || keys.key(p) < keys.key(q)) ? p : q;
     }
     root[v] = name;
-    if (name != (uint32_t)v) atomicMin(&mo[name], mo[v]);
+    if (name != (uint32_t)v) min_if_lower(&mo[name], mo[v]);
   }
 }
 
@@ -480,7 +480,7 @@ __global__ void k_uf_names(const uint32_t* parent, uint32_t* mo, uint32_t n, uns
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
     const uint32_t r = uf_root(parent, (uint32_t)v, err);
-    if (r != (uint32_t)v) atomicMin(&mo[r], mo[v]);
+    if (r != (uint32_t)v) min_if_lower(&mo[r], mo[v]);
   }
 }
 
@@ -510,13 +510,16 @@ __device__ __forceinline__ void relabel_one(uint32_t u, uint32_t v, bool valid, 
 constexpr int kRelCache = 4096;  // per-block direct-mapped cache of emitted keys
 
 // Each block handles tiles of kThreads * kRelItems edges.  Every non-loop
-// edge is counted in *mprime; its key is written only if the block's cache
-// does not already hold it.  The cache slot of a key is overwritten by the
-// thread that writes the key, so a key is dropped only after this block has
-// written a copy of it: the written keys contain every distinct key.  Heavily
-// repeated keys (pairs of large trees) are thus written about once per block,
-// which keeps the dedup buckets small.  The written keys are compacted with a
-// block scan and appended after one atomicAdd per tile.
+// edge is counted in *mprime; its key is written only if neither the block's
+// cache nor the optional device-wide cache (gcache, gmask + 1 slots, both
+// direct-mapped) holds it.  A key enters the device-wide cache only from the
+// thread that then writes it, and the block cache only from a thread that
+// writes it or that found it in the device-wide cache, so a key is dropped
+// only when a copy of it is written: the written keys contain every distinct
+// key.  Heavily repeated keys (pairs of large trees) are thus written a few
+// times instead of once per edge, which shrinks the deduplication.  The
+// written keys are compacted with a block scan and appended after one
+// atomicAdd per tile.
 // Half-resolved endpoint: the root id with this bit set (ids < 2^31 only).
 constexpr uint32_t kResolved = 0x80000000u;
 
@@ -549,7 +552,7 @@ __global__ void __launch_bounds__(kThreads) k_relabel(
     const uint64_t* __restrict__ packed, uint64_t m, uint32_t n, const uint32_t* __restrict__ root,
     int bits, uint64_t* __restrict__ keys_out, unsigned long long* mprime,
     unsigned long long* emitted, int mix, PassPlan plan, uint32_t* __restrict__ ghist,
-    unsigned* mprime_err) {
+    unsigned* mprime_err, unsigned long long* gcache, uint32_t gmask, int admit) {
   __shared__ uint64_t cache[kRelCache];
   __shared__ uint32_t hist[3][kRadixMax];
   __shared__ uint32_t ws[kThreads / 32];
@@ -607,10 +610,27 @@ __global__ void __launch_bounds__(kThreads) k_relabel(
         if (mix) key[i] = y;
         if (cache[slot] != key[i]) {
           cache[slot] = key[i];
-          emitmask |= 1u << i;
+          bool emit = true;
+          if (gcache != nullptr) {
+            // device-wide cache (slot from other bits than the block's); a
+            // missing key is admitted for one in 2^admit of its occurrences
+            // (chosen by the edge's position), so that keys seen once rarely
+            // evict repeated ones
+            unsigned long long* g = gcache + ((uint32_t)(y >> 20) & gmask);
+            if (__ldcg(g) == key[i]) {
+              emit = false;
+            } else {
+              const uint64_t j = base + (uint64_t)i * 32 + lane;
+              if (admit == 0 || ((j * kGamma) >> (64 - admit)) == 0)
+                __stcg(g, (unsigned long long)key[i]);
+            }
+          }
+          if (emit) {
+            emitmask |= 1u << i;
 #pragma unroll
-          for (int p = 0; p < 3; ++p)
-            if (p < plan.passes) atomicAdd(&hist[p][plan.digit(p, key[i])], 1u);
+            for (int p = 0; p < 3; ++p)
+              if (p < plan.passes) atomicAdd(&hist[p][plan.digit(p, key[i])], 1u);
+          }
         }
       }
     }
@@ -779,7 +799,10 @@ void relabel(const uint32_t* src, const uint32_t* dst, const uint64_t* packed, u
              uint32_t n, const uint32_t* root, int bits, uint64_t* keys_out,
              unsigned long long* mprime, unsigned long long* emitted, bool mix,
              const PassPlan* plan, uint32_t* ghist, uint64_t* tmp, uint64_t window_bytes,
-             unsigned* err, const Launch& L) {
+             unsigned long long* gcache, uint32_t gslots, int admit, unsigned* err,
+             const Launch& L) {
+  const uint32_t gmask = gslots ? gslots - 1 : 0;
+  if (gslots == 0) gcache = nullptr;
   PassPlan pl{};
   if (plan != nullptr) pl = *plan;  // passes == 0: no histogram
   if (m == 0) return;
@@ -788,7 +811,7 @@ void relabel(const uint32_t* src, const uint32_t* dst, const uint64_t* packed, u
     KScope ks(L, kKRelabelPacked);
     k_relabel<1><<<grid, kThreads, 0, L.stream>>>(nullptr, nullptr, packed, m, n, root, bits,
                                                   keys_out, mprime, emitted, mix, pl, ghist,
-                                                  err);
+                                                  err, gcache, gmask, admit);
   } else if (tmp != nullptr && n < kResolved && (uint64_t)n * 4 > window_bytes) {
     // two passes, each gathering from one half of root (see k_relabel_first_half)
     const uint32_t split = n / 2;
@@ -800,11 +823,12 @@ void relabel(const uint32_t* src, const uint32_t* dst, const uint64_t* packed, u
     KScope ks(L, kKRelabelSoa);
     k_relabel<2><<<grid, kThreads, 0, L.stream>>>(nullptr, nullptr, tmp, m, n, root, bits,
                                                   keys_out, mprime, emitted, mix, pl, ghist,
-                                                  err);
+                                                  err, gcache, gmask, admit);
   } else {
     KScope ks(L, kKRelabelSoa);
     k_relabel<0><<<grid, kThreads, 0, L.stream>>>(src, dst, nullptr, m, n, root, bits, keys_out,
-                                                  mprime, emitted, mix, pl, ghist, err);
+                                                  mprime, emitted, mix, pl, ghist, err, gcache,
+                                                  gmask, admit);
   }
 }
 

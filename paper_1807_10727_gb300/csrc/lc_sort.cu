@@ -130,6 +130,28 @@ __global__ void __launch_bounds__(kSortThreads) k_hist_scan(uint32_t* ghist) {
   }
 }
 
+// ------------------------------------------------------------ HyperLogLog
+
+__global__ void __launch_bounds__(kSortThreads) k_hll(const uint64_t* __restrict__ keys,
+                                                      const unsigned long long* d_count,
+                                                      uint32_t* __restrict__ ghll) {
+  __shared__ uint32_t reg[kHllRegs];
+  for (int i = threadIdx.x; i < kHllRegs; i += blockDim.x) reg[i] = 0;
+  __syncthreads();
+  const uint64_t count = *d_count;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride) {
+    const uint64_t y = __ldcs(keys + i);
+    const uint64_t rest = y << kHllBits;
+    const uint32_t rank =
+        rest ? (uint32_t)__clzll((long long)rest) + 1u : (uint32_t)(65 - kHllBits);
+    atomicMax(&reg[(uint32_t)(y >> (64 - kHllBits))], rank);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < kHllRegs; i += blockDim.x)
+    if (reg[i]) atomicMax(&ghll[i], reg[i]);
+}
+
 // ------------------------------------------------------------ one pass
 
 // Digit-parallel look-back for the digits this thread owns: publish each
@@ -648,6 +670,15 @@ int radix_sort_u64(uint64_t* keys, uint64_t* alt, const unsigned long long* d_co
     plan.bits[p] = kRadixBits;
   }
   return run_passes(keys, alt, d_count, max_count, plan, false, s, err, mark_flags, half_bits, L);
+}
+
+void hll_sketch(const uint64_t* keys, const unsigned long long* d_count, uint64_t max_count,
+                uint32_t* hll, const Launch& L) {
+  if (max_count == 0) return;
+  const int grid = (int)std::min<uint64_t>((max_count + kSortTile - 1) / kSortTile,
+                                           (uint64_t)L.sms * 4);
+  KScope ks(L, kKHll);
+  k_hll<<<grid, kSortThreads, 0, L.stream>>>(keys, d_count, hll);
 }
 
 int hash_bits_for(uint64_t max_count) {

@@ -172,3 +172,30 @@ def test_output_cap_too_small(lc_lib, cuda):
         lc.lc_run(ctx.ctx, labels.data_ptr(), cap=1)
     assert ei.value.code == lc.LC_ERR_INVALID
     ctx.close()
+
+
+@pytest.mark.parametrize("dedup", [lc.LC_DEDUP_HASH, lc.LC_DEDUP_SORT])
+def test_relabel_cache_sizes(lc_lib, cuda, dedup):
+    """The device-wide relabel cache (phases of >= 2^22 edges) at sizes from
+    heavy collisions to none: results never change, and it only drops keys."""
+    g = synth.workload("rmat18")
+    ref = oracle.lc_run(g.n, g.src, g.dst, g.seed)
+    ts, td = dev(g.src, cuda), dev(g.dst, cuda)
+    emitted = {}
+    for slots in (0, 1024, 1 << 16, 1 << 20, 1 << 24):
+        ctx = lc.LocalContraction(g.n, ts, td, seed=g.seed, dedup=dedup)
+        ctx.set_param("relabel_cache_slots", slots)
+        labels, res = ctx.run()
+        mp, em = lc.lc_last_stats(ctx.ctx)
+        ctx.close()
+        assert res.rounds == ref.rounds
+        assert list(zip(res.n_i, res.m_i)) == ref.sizes()
+        assert mp == [int(x) for x in ref.mp_i]
+        assert np.array_equal(labels.cpu().numpy().view(np.uint32), ref.labels)
+        emitted[slots] = em[0]
+    assert emitted[1 << 20] <= emitted[0]
+    for bad in (3, 512, 1 << 27):
+        ctx = lc.LocalContraction(g.n, ts, td, seed=g.seed)
+        with pytest.raises(lc.LCError):
+            ctx.set_param("relabel_cache_slots", bad)
+        ctx.close()
