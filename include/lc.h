@@ -138,14 +138,16 @@ lc_status lc_set_dedup(lc_ctx* ctx, lc_dedup mode);
  *   "relabel_cache_slots"  size (a power of two in [2^10, 2^26], or 0 = off)
  *                   of a device-wide direct-mapped cache of relabelled keys
  *                   used in phases with at least 2^22 edges: a key already in
- *                   it is not written again, so repeated edges between the
- *                   same pair of nodes reach the deduplication a few times
- *                   instead of once per edge.  8 bytes per slot of device
- *                   memory, reallocated on change (default 2^22 for contexts
+ *                   it is dropped before the deduplication (in a filter pass
+ *                   after the relabel with LC_DEDUP_HASH, inside the relabel
+ *                   with LC_DEDUP_SORT), so repeated edges between the same
+ *                   pair of nodes reach the deduplication a few times instead
+ *                   of once per edge.  8 bytes per slot of device
+ *                   memory, reallocated on change (default 2^23 for contexts
  *                   of at least 2^22 edges, else 0).  Not while a run is in
  *                   flight.
  *   "relabel_cache_admit"  a key missing from that cache enters it at one in
- *                   2^value of its occurrences (0..16, default 2), so that
+ *                   2^value of its occurrences (0..16, default 3), so that
  *                   keys seen once rarely evict repeated ones.
  * Phases with at least 2^22 edges also size their deduplication buckets from
  * a HyperLogLog estimate (Flajolet et al. 2007) of the distinct relabelled
@@ -202,9 +204,9 @@ lc_status lc_batch_run(lc_ctx* ctx, uint32_t* d_labels, uint32_t* rounds, uint64
 
 /* Diagnostics of the last successful run, host uint64[cap] each (NULL to skip):
  * mp_i = edges of phase i left after relabelling and loop removal, before
- * deduplication (m'_i); emitted_i = how many of those the relabel step wrote
- * out (it skips repeats of a key it has just written, so the deduplication
- * reads fewer keys; emitted_i <= mp_i).  Returns the phase count in *rounds. */
+ * deduplication (m'_i); emitted_i = how many of those reach the
+ * deduplication (the relabel step and the device-wide cache drop repeats of a
+ * key already kept, so the deduplication reads fewer keys; emitted_i <= mp_i).  Returns the phase count in *rounds. */
 lc_status lc_last_stats(const lc_ctx* ctx, uint32_t* rounds, uint64_t* mp_i, uint64_t* emitted_i,
                         uint32_t cap);
 

@@ -28,7 +28,7 @@ const char* kernel_name(int id) {
       "unique_rename", "propagate",  "bucket_bounds",   "bucket_dedup",  "rename",
       "unmix",         "batch",      "two_hop",         "open_min",      "tree_names",
       "union_find",    "m2l_group",  "m2l_select",      "m2l_hop",       "m2l_target",
-      "identity",      "rank_probe", "hll"};
+      "identity",      "rank_probe", "filter_hll"};
   static_assert(sizeof(names) / sizeof(names[0]) == kNumKernels, "one name per kernel");
   return (id >= 0 && id < kNumKernels) ? names[id] : "unknown";
 }
@@ -134,8 +134,8 @@ uint64_t host_mix(uint64_t z) { return splitmix_mix(z); }
 // block caches and the dedup are cheap, and a mid-phase wait would cost more
 // than it saves).
 constexpr uint64_t kGCacheMinEdges = 1ull << 22;
-constexpr uint32_t kGCacheSlots = 1u << 22;  // default size (32 MB)
-constexpr int kGCacheAdmit = 2;              // default admission: 1 in 4 occurrences
+constexpr uint32_t kGCacheSlots = 1u << 23;  // default size (64 MB)
+constexpr int kGCacheAdmit = 3;              // default admission: 1 in 8 occurrences
 
 // Stream seed of phase i: output i+1 of the SplitMix64 stream seeded with seed.
 uint64_t phase_seed(uint64_t seed, uint32_t i) { return host_mix(seed + (uint64_t)(i + 1) * kGamma); }
@@ -517,17 +517,32 @@ static lc_status enqueue_phase(lc_ctx* c) {
   if (!c->dedup_sort && !late) hist_reset(c->sort, L);
   if (late && cudaMemsetAsync(c->d_hll, 0, 4ull * kHllRegs, c->stream) != cudaSuccess)
     return fail(c, LC_ERR_CUDA);
+  // the device-wide duplicate cache: in the relabel itself with the full
+  // sort, else in the filter pass of a late-planned phase
   const bool use_gcache = c->gcache != nullptr && big;
   if (use_gcache &&
       cudaMemsetAsync(c->gcache, 0xFF, 8ull * c->gcache_slots, c->stream) != cudaSuccess)
     return fail(c, LC_ERR_CUDA);
+  const bool gcache_in_relabel = use_gcache && !late;
   relabel(src0, dst0, r.packed, mi, ni, r.lv.root,
           r.bits, r.keys, &c->ctr->mprime, &c->ctr->emitted, !c->dedup_sort,
           (c->dedup_sort || late) ? nullptr : &hplan, c->sort.hist, first ? r.alt : nullptr,
-          c->relabel_window_bytes, use_gcache ? c->gcache : nullptr,
-          use_gcache ? c->gcache_slots : 0, c->gcache_admit, err, L);
+          c->relabel_window_bytes, gcache_in_relabel ? c->gcache : nullptr,
+          gcache_in_relabel ? c->gcache_slots : 0, c->gcache_admit, err, L);
   if (late) {
-    hll_sketch(r.keys, &c->ctr->emitted, mi, c->d_hll, L);
+    // drop repeats through the device-wide cache while sketching the distinct
+    // count; the kept keys replace the relabelled ones (and their count the
+    // emitted count)
+    if (cudaMemsetAsync(&c->ctr->filtered, 0, sizeof(unsigned long long), c->stream) !=
+        cudaSuccess)
+      return fail(c, LC_ERR_CUDA);
+    filter_hll(r.keys, &c->ctr->emitted, mi, r.alt, &c->ctr->filtered,
+               use_gcache ? c->gcache : nullptr, use_gcache ? c->gcache_slots : 0,
+               c->gcache_admit, c->d_hll, L);
+    std::swap(r.keys, r.alt);
+    if (cudaMemcpyAsync(&c->ctr->emitted, &c->ctr->filtered, sizeof(unsigned long long),
+                        cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess)
+      return fail(c, LC_ERR_CUDA);
     stamp_counters(c->ctr, ++c->tag, L);
     if (cudaMemcpyAsync(c->h_ctr, c->ctr, sizeof(Counters), cudaMemcpyDeviceToHost, c->stream) !=
             cudaSuccess ||

@@ -90,15 +90,12 @@ struct Counters {
   unsigned long long bad_index;
   unsigned long long bad_limit;
   unsigned long long tag;      // stamped by the last kernel of a phase (see run_complete)
+  unsigned long long filtered; // keys left by the device-wide duplicate filter
 };
 static_assert(offsetof(Counters, bad_kernel) == offsetof(Counters, err) + 4, "layout");
 static_assert(offsetof(Counters, bad_index) == offsetof(Counters, err) + 8, "layout");
 static_assert(offsetof(Counters, bad_limit) == offsetof(Counters, err) + 16, "layout");
 
-// Index check of a data-dependent access: false (and the first failure
-// recorded next to the error word, see Counters) when idx >= limit.  Kernels
-// skip the access when it fails, so corrupted data gives an error status, not
-// a memory fault.
 // atomicMin / atomicMax preceded by a read through L2: the stored values
 // only move one way, so a read value is never past the current one, and a
 // candidate that does not beat it cannot change the word.  Addresses that many
@@ -113,6 +110,10 @@ __device__ __forceinline__ void max_if_higher(unsigned long long* p, unsigned lo
   if (v > __ldcg(p)) atomicMax(p, v);
 }
 
+// Index check of a data-dependent access: false (and the first failure
+// recorded next to the error word, see Counters) when idx >= limit.  Kernels
+// skip the access when it fails, so corrupted data gives an error status, not
+// a memory fault.
 __device__ __forceinline__ bool index_ok(unsigned* err, uint32_t kernel, uint64_t idx,
                                          uint64_t limit) {
   if (idx < limit) return true;

@@ -39,7 +39,7 @@ enum KernelId : int {
   kKMergeTarget,
   kKIdentity,
   kKRankProbe,
-  kKHll,
+  kKFilter,
   kNumKernels
 };
 
@@ -165,12 +165,16 @@ int hash_plan(uint64_t max_count, PassPlan* plan);
 // Zero the digit counts of s.hist (before a producer accumulates them).
 void hist_reset(SortScratch& s, const Launch& L);
 
-// HyperLogLog registers (Flajolet, Fusy, Gandouet, Meunier 2007) of the
-// *d_count mixed keys in keys: register = top kHllBits bits, value = max
-// position of the first one bit below them.  hll: kHllRegs words, zero
-// before the call.
-void hll_sketch(const uint64_t* keys, const unsigned long long* d_count, uint64_t max_count,
-                uint32_t* hll, const Launch& L);
+// Duplicate filter and distinct-count sketch of the *d_in mixed keys in `in`:
+// keys found in the device-wide cache (gcache, gslots slots, a power of two,
+// ~0 in every slot when a phase starts using it; 0 slots = keep all) are
+// dropped, the others appended to out (count added to *d_out, zero before)
+// and entered in the cache at one in 2^admit of their positions; hll
+// (kHllRegs words, zero before) receives the HyperLogLog registers (Flajolet
+// et al. 2007) of the kept keys.  The kept keys hold every distinct key.
+void filter_hll(const uint64_t* in, const unsigned long long* d_in, uint64_t max_count,
+                uint64_t* out, unsigned long long* d_out, unsigned long long* gcache,
+                uint32_t gslots, int admit, uint32_t* hll, const Launch& L);
 
 // Duplicate removal without a full sort, on mixed keys (key_mix of
 // a << half_bits | b): a stable LSD partition of keys[0, *d_count) by their

@@ -130,25 +130,87 @@ __global__ void __launch_bounds__(kSortThreads) k_hist_scan(uint32_t* ghist) {
   }
 }
 
-// ------------------------------------------------------------ HyperLogLog
+// ------------------------------------------------- duplicate filter + HLL
 
-__global__ void __launch_bounds__(kSortThreads) k_hll(const uint64_t* __restrict__ keys,
-                                                      const unsigned long long* d_count,
-                                                      uint32_t* __restrict__ ghll) {
+constexpr int kFilterItems = 8;  // keys per thread per tile
+
+// Keys in[0, *d_in) pass through a device-wide direct-mapped cache of keys
+// already kept (gcache, gmask + 1 slots; nullptr = keep every key): a key
+// found there is dropped, since the thread that put it there keeps that copy;
+// a key not found is kept and enters the cache at one in 2^admit of its
+// positions.  Kept keys are compacted to out (one atomicAdd on *d_out per
+// tile) and update the HyperLogLog registers (Flajolet, Fusy, Gandouet,
+// Meunier 2007): register = top kHllBits bits of the mixed key, value = the
+// position of the first one bit below them.  The cache entries of a thread's
+// kFilterItems keys are read together, so their loads overlap.
+__global__ void __launch_bounds__(kSortThreads) k_filter_hll(
+    const uint64_t* __restrict__ in, const unsigned long long* d_in, uint64_t* __restrict__ out,
+    unsigned long long* d_out, unsigned long long* gcache, uint32_t gmask, int admit,
+    uint32_t* __restrict__ ghll) {
+  constexpr uint64_t kTile = (uint64_t)kSortThreads * kFilterItems;
   __shared__ uint32_t reg[kHllRegs];
-  for (int i = threadIdx.x; i < kHllRegs; i += blockDim.x) reg[i] = 0;
+  __shared__ uint32_t ws[kWarps];
+  __shared__ unsigned long long s_base;
+  const unsigned tid = threadIdx.x, lane = lane_id(), w = tid >> 5;
+  for (int i = tid; i < kHllRegs; i += kSortThreads) reg[i] = 0;
   __syncthreads();
-  const uint64_t count = *d_count;
-  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride) {
-    const uint64_t y = __ldcs(keys + i);
-    const uint64_t rest = y << kHllBits;
-    const uint32_t rank =
-        rest ? (uint32_t)__clzll((long long)rest) + 1u : (uint32_t)(65 - kHllBits);
-    atomicMax(&reg[(uint32_t)(y >> (64 - kHllBits))], rank);
+  const uint64_t count = *d_in;
+  const uint64_t tiles = (count + kTile - 1) / kTile;
+  for (uint64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+    const uint64_t base = t * kTile + (uint64_t)w * 32 * kFilterItems;
+    uint64_t k[kFilterItems];
+    unsigned long long gv[kFilterItems];
+#pragma unroll
+    for (int i = 0; i < kFilterItems; ++i) {
+      const uint64_t j = base + (uint64_t)i * 32 + lane;
+      k[i] = j < count ? __ldcs(in + j) : 0ull;
+    }
+#pragma unroll
+    for (int i = 0; i < kFilterItems; ++i) {
+      const uint64_t j = base + (uint64_t)i * 32 + lane;
+      gv[i] = (j < count && gcache != nullptr) ? __ldcg(gcache + ((uint32_t)(k[i] >> 20) & gmask))
+                                               : 0ull;
+    }
+    uint32_t keep = 0;
+#pragma unroll
+    for (int i = 0; i < kFilterItems; ++i) {
+      const uint64_t j = base + (uint64_t)i * 32 + lane;
+      if (j >= count || (gcache != nullptr && gv[i] == k[i])) continue;
+      keep |= 1u << i;
+      if (gcache != nullptr && (admit == 0 || ((j * kGamma) >> (64 - admit)) == 0))
+        __stcg(gcache + ((uint32_t)(k[i] >> 20) & gmask), (unsigned long long)k[i]);
+      const uint64_t rest = k[i] << kHllBits;
+      const uint32_t rank =
+          rest ? (uint32_t)__clzll((long long)rest) + 1u : (uint32_t)(65 - kHllBits);
+      atomicMax(&reg[(uint32_t)(k[i] >> (64 - kHllBits))], rank);
+    }
+    // warp offsets, then one block scan over the warp totals
+    const uint32_t mine = __popc(keep);
+    uint32_t incl = mine;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+      if (lane >= (unsigned)o) incl += y;
+    }
+    if (lane == 31) ws[w] = incl;
+    __syncthreads();
+    if (tid == 0) {
+      uint32_t run = 0;
+      for (int q = 0; q < kWarps; ++q) {
+        const uint32_t c = ws[q];
+        ws[q] = run;
+        run += c;
+      }
+      s_base = run ? atomicAdd(d_out, (unsigned long long)run) : 0ull;
+    }
+    __syncthreads();
+    uint64_t pos = s_base + ws[w] + (incl - mine);
+#pragma unroll
+    for (int i = 0; i < kFilterItems; ++i)
+      if (keep & (1u << i)) __stcs(out + pos++, k[i]);
+    __syncthreads();
   }
-  __syncthreads();
-  for (int i = threadIdx.x; i < kHllRegs; i += blockDim.x)
+  for (int i = tid; i < kHllRegs; i += kSortThreads)
     if (reg[i]) atomicMax(&ghll[i], reg[i]);
 }
 
@@ -672,13 +734,16 @@ int radix_sort_u64(uint64_t* keys, uint64_t* alt, const unsigned long long* d_co
   return run_passes(keys, alt, d_count, max_count, plan, false, s, err, mark_flags, half_bits, L);
 }
 
-void hll_sketch(const uint64_t* keys, const unsigned long long* d_count, uint64_t max_count,
-                uint32_t* hll, const Launch& L) {
+void filter_hll(const uint64_t* in, const unsigned long long* d_in, uint64_t max_count,
+                uint64_t* out, unsigned long long* d_out, unsigned long long* gcache,
+                uint32_t gslots, int admit, uint32_t* hll, const Launch& L) {
   if (max_count == 0) return;
   const int grid = (int)std::min<uint64_t>((max_count + kSortTile - 1) / kSortTile,
-                                           (uint64_t)L.sms * 4);
-  KScope ks(L, kKHll);
-  k_hll<<<grid, kSortThreads, 0, L.stream>>>(keys, d_count, hll);
+                                           (uint64_t)L.sms * 8);
+  KScope ks(L, kKFilter);
+  k_filter_hll<<<grid, kSortThreads, 0, L.stream>>>(in, d_in, out, d_out,
+                                                    gslots ? gcache : nullptr,
+                                                    gslots ? gslots - 1 : 0u, admit, hll);
 }
 
 int hash_bits_for(uint64_t max_count) {
