@@ -38,9 +38,11 @@ if REPO not in sys.path:
     sys.path.insert(0, REPO)
 
 METRIC = "input edges/sec to final labels (1 GB300), HBM roofline %"
-# DRAM bytes / algorithmic bytes per launch from the committed ncu capture
-# (profiles/traffic_rmat23.md); valid while the kernel is unchanged.
-TRAFFIC_RATIO = {"sort_pass": 1.007, "relabel_soa": 0.98, "bucket_dedup": 0.93}
+# DRAM bytes / algorithmic bytes per launch of the phase-0 launches, from the
+# committed full-size ncu capture (profiles/traffic_rmat26.md); valid while
+# the kernels are unchanged and only for the R-MAT 26 workload.
+TRAFFIC_RATIO = {"relabel_soa": 2.435, "relabel_split": 2.369, "edge_min_soa": 1.742,
+                 "filter_hll": 1.333, "sort_pass": 1.003, "bucket_dedup": 1.142}
 UNIT = "edges/s"
 CPU_SAMPLE_EDGES = 1 << 24
 
@@ -62,7 +64,7 @@ def peaks():
 # sector amplification is not algorithmic and is not counted; a phase-0
 # minimum window pass or a relabel half-pass reads all edges, so each such
 # launch counts that read.
-def algorithmic_bytes(n_i, m_i, mp_i, em_i, passes_i, window_passes, relabel_split):
+def algorithmic_bytes(n_i, m_i, mp_i, em_i, kept_i, passes_i, window_passes, relabel_split):
     per = {}
 
     def add(k, b):
@@ -84,13 +86,15 @@ def algorithmic_bytes(n_i, m_i, mp_i, em_i, passes_i, window_passes, relabel_spl
             add("edge_min_packed", 8 * m + 8 * n)
             add("relabel_packed", 8 * m + 8 * em + 4 * n)
         add("jump", 8 * n + 4 * n + 4 * n)
-        add("sort_pass", 16 * em * passes_i[i])
-        if m >= LATE_PLAN_EDGES:
-            # phases that size their buckets after the relabel: one read of
-            # the keys for the distinct-count sketch, one for the histogram
-            add("hll", 8 * em)
-            add("sort_hist", 8 * em)
-        add("bucket_dedup", 8 * em + 8 * m_next + 2 * n)
+        kept = kept_i[i]
+        add("sort_pass", 16 * kept * passes_i[i])
+        if kept != em or m >= LATE_PLAN_EDGES:
+            # phases that size their buckets after the relabel: the filter
+            # pass reads the written keys and writes the kept ones, the
+            # histogram pass reads the kept keys
+            add("filter_hll", 8 * em + 8 * kept)
+            add("sort_hist", 8 * kept)
+        add("bucket_dedup", 8 * kept + 8 * m_next + 2 * n)
         add("rename", 16 * m_next + 4 * n)
         add("scan_flags", n + 4 * n + 8 * (m_next and n))
         add("propagate", 4 * n + 4 * n + 4 * n)
@@ -449,6 +453,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched (config 4) leg")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving (config 5) leg")
+    ap.add_argument("--param", action="append", default=[], metavar="NAME=VALUE",
+                    help="lc_set_param tuning value for the headline context (repeatable)")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the two-hop / tree / union-find-finish leg")
     ap.add_argument("--no-profile", action="store_true",
@@ -480,11 +486,14 @@ def main():
     labels = torch.empty(g.n, dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream(dev)
     ctx = lc.LocalContraction(g.n, src, dst, seed=g.seed, stream=stream)
+    for kv in args.param:
+        name, value = kv.split("=", 1)
+        ctx.set_param(name, int(value))
 
     for _ in range(max(3, args.warmup)):
         _, res = ctx.run(labels)
     mp, em = lc.lc_last_stats(ctx.ctx)
-    passes = lc.lc_last_passes(ctx.ctx)
+    kept, passes = lc.lc_last_dedup(ctx.ctx)
 
     clocks = ClockSampler(gpu_id_for(local))
     ctx.profile(not args.no_profile)
@@ -515,14 +524,14 @@ def main():
     peak, peak_kind = peaks()
     wpass = max(1, -(-8 * g.n // (192 << 20)))
     split = g.n < (1 << 31) and 4 * g.n > (160 << 20)
-    alg = algorithmic_bytes(res.n_i, res.m_i, mp, em, passes, wpass, split)
+    alg = algorithmic_bytes(res.n_i, res.m_i, mp, em, kept, passes, wpass, split)
     top = max(kstats.items(), key=lambda kv: kv[1][1])
     top_name, (top_launches, top_ms) = top
     roof = None
     if top_ms > 0:
         achieved = alg.get(top_name, 0) * args.steps / (top_ms / 1e3) / 1e9
         per_launch = alg.get(top_name, 0) * args.steps / max(1, top_launches)
-        ratio = TRAFFIC_RATIO.get(top_name)
+        ratio = TRAFFIC_RATIO.get(top_name) if args.workload == "rmat26" and not args.param else None
         roof = {"bound": "hbm", "kernel": top_name, "achieved": achieved, "peak": peak,
                 "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind,
                 "traffic": ratio * per_launch if ratio else None,
@@ -600,8 +609,9 @@ def main():
             "e2e": e2e, "cpu_baseline": cpu, "gpu_launches": launches, "batched": batched,
             "serving": serving, "variants": variants,
             "clocks": clk, "kernels": kernels,
-            "sizes": [[int(a), int(b), int(c), int(d)]
-                      for a, b, c, d in zip(res.n_i, res.m_i, mp, em)],
+            "sizes": [[int(a), int(b), int(c), int(d), int(e)]
+                      for a, b, c, d, e in zip(res.n_i, res.m_i, mp, em, kept)],
+            "sizes_columns": ["n_i", "m_i", "m'_i", "relabel keys written", "keys deduplicated"],
         }
         print(json.dumps(line))
     if world > 1:

@@ -133,8 +133,9 @@ lc_status lc_set_dedup(lc_ctx* ctx, lc_dedup mode);
  *                   edges per window (default 192 MiB).
  *   "relabel_window_bytes"  when the phase-0 root array (4 bytes per vertex)
  *                   is larger than this, phase 0 relabels the input edges in
- *                   two passes, each gathering roots from one half of the
- *                   array (default 160 MiB; needs n < 2^31).
+ *                   one pass per part of the array of at most this size (at
+ *                   most 8 parts), each gathering roots from its part only
+ *                   (default 160 MiB; needs n < 2^31).
  *   "relabel_cache_slots"  size (a power of two in [2^10, 2^26], or 0 = off)
  *                   of a device-wide direct-mapped cache of relabelled keys
  *                   used in phases with at least 2^22 edges: a key already in
@@ -204,18 +205,24 @@ lc_status lc_batch_run(lc_ctx* ctx, uint32_t* d_labels, uint32_t* rounds, uint64
 
 /* Diagnostics of the last successful run, host uint64[cap] each (NULL to skip):
  * mp_i = edges of phase i left after relabelling and loop removal, before
- * deduplication (m'_i); emitted_i = how many of those reach the
- * deduplication (the relabel step and the device-wide cache drop repeats of a
- * key already kept, so the deduplication reads fewer keys; emitted_i <= mp_i).  Returns the phase count in *rounds. */
+ * deduplication (m'_i); emitted_i = how many of those the relabel step wrote
+ * out (it skips repeats of a key it has just written, so the deduplication
+ * reads fewer keys; emitted_i <= mp_i).  Returns the phase count in *rounds. */
 lc_status lc_last_stats(const lc_ctx* ctx, uint32_t* rounds, uint64_t* mp_i, uint64_t* emitted_i,
                         uint32_t cap);
 
-/* Partition passes that the hashed deduplication of each phase of the last
- * run planned (host uint32[cap]; 0 for LC_DEDUP_SORT and for phases small
- * enough for one bucket); no counterpart in the paper, used to count the
- * bytes the passes must move.  Returns the phase count in *rounds, and
- * LC_ERR_INVALID if cap is smaller than it (the first cap are filled). */
-lc_status lc_last_passes(const lc_ctx* ctx, uint32_t* rounds, uint32_t* passes_i, uint32_t cap);
+/* Deduplication of each phase of the last run (no counterpart in the paper;
+ * used to count the bytes the deduplication must move), host arrays of cap
+ * entries each (NULL to skip):
+ *   kept_i    keys that reached the deduplication: emitted_i, less the
+ *             repeats that the device-wide cache dropped in phases of at
+ *             least 2^22 edges (see "relabel_cache_slots").
+ *   passes_i  partition passes the hashed deduplication planned (0 for
+ *             LC_DEDUP_SORT and for phases small enough for one bucket).
+ * Returns the phase count in *rounds, and LC_ERR_INVALID if cap is smaller
+ * than it (the first cap are filled). */
+lc_status lc_last_dedup(const lc_ctx* ctx, uint32_t* rounds, uint64_t* kept_i, uint32_t* passes_i,
+                        uint32_t cap);
 
 /* Per-kernel instrumentation (no counterpart in the paper; used to measure
  * the kernels against the HBM roofline).  Launch counts of every kernel are

@@ -165,6 +165,7 @@ struct RunState {
   lc_status st = LC_OK;
   bool merge_step = false;  // the level in flight is phase i's MergeToLarge step
   uint32_t passes = 0;      // partition passes planned for the level in flight
+  bool filtered = false;    // the level's keys went through the filter pass
   uint32_t* d_labels = nullptr;
   uint32_t i = 0, ni = 0;
   uint64_t mi = 0;
@@ -235,6 +236,7 @@ struct lc_ctx {
   std::vector<uint64_t> last_mp;
   std::vector<uint64_t> last_emitted;
   std::vector<uint32_t> last_passes;  // partition passes of each phase's hashed dedup
+  std::vector<uint64_t> last_kept;    // keys each phase deduplicated
 
   cudaEvent_t ev = nullptr;  // completion of the work enqueued last (none: sync the stream)
   RunState rs;
@@ -402,6 +404,12 @@ static lc_status record(lc_ctx* c) {
 }
 
 static lc_status enqueue_sort_dedup(lc_ctx* c);
+
+// Device count of the keys the level in flight deduplicates.
+static unsigned long long* kept_count(lc_ctx* c) {
+  return c->rs.filtered ? &c->ctr->filtered : &c->ctr->emitted;
+}
+
 static lc_status enqueue_dedup(lc_ctx* c, const PassPlan& hplan, int hb, bool hist_ready);
 
 static lc_status fail(lc_ctx* c, lc_status st) {
@@ -508,6 +516,7 @@ static lc_status enqueue_phase(lc_ctx* c) {
     return fail(c, LC_ERR_CUDA);
   r.keys = (r.packed == c->ebuf[0]) ? c->ebuf[1] : c->ebuf[0];
   r.alt = (r.keys == c->ebuf[0]) ? c->ebuf[1] : c->ebuf[0];
+  r.filtered = false;
   const bool big = mi >= kGCacheMinEdges;
   // large phases plan their buckets after the relabel, from the estimated
   // number of distinct keys; the others from m_i, with the histogram fused
@@ -531,8 +540,7 @@ static lc_status enqueue_phase(lc_ctx* c) {
           gcache_in_relabel ? c->gcache_slots : 0, c->gcache_admit, err, L);
   if (late) {
     // drop repeats through the device-wide cache while sketching the distinct
-    // count; the kept keys replace the relabelled ones (and their count the
-    // emitted count)
+    // count; the kept keys (counted in `filtered`) replace the relabelled ones
     if (cudaMemsetAsync(&c->ctr->filtered, 0, sizeof(unsigned long long), c->stream) !=
         cudaSuccess)
       return fail(c, LC_ERR_CUDA);
@@ -540,9 +548,7 @@ static lc_status enqueue_phase(lc_ctx* c) {
                use_gcache ? c->gcache : nullptr, use_gcache ? c->gcache_slots : 0,
                c->gcache_admit, c->d_hll, L);
     std::swap(r.keys, r.alt);
-    if (cudaMemcpyAsync(&c->ctr->emitted, &c->ctr->filtered, sizeof(unsigned long long),
-                        cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess)
-      return fail(c, LC_ERR_CUDA);
+    r.filtered = true;
     stamp_counters(c->ctr, ++c->tag, L);
     if (cudaMemcpyAsync(c->h_ctr, c->ctr, sizeof(Counters), cudaMemcpyDeviceToHost, c->stream) !=
             cudaSuccess ||
@@ -581,7 +587,7 @@ static lc_status enqueue_dedup(lc_ctx* c, const PassPlan& hplan, int hb, bool hi
   const uint64_t mi = r.mi;
   r.passes = c->dedup_sort ? 0u : (uint32_t)hplan.passes;
   if (!c->dedup_sort) {
-    int which = hash_dedup(r.keys, r.alt, &c->ctr->emitted, mi, hplan, hb, hist_ready, r.bits,
+    int which = hash_dedup(r.keys, r.alt, kept_count(c), mi, hplan, hb, hist_ready, r.bits,
                            c->flags, ni, c->bounds, &c->ctr->m_next, c->sort, err, L);
     r.part = which ? r.alt : r.keys;
     r.next = which ? r.keys : r.alt;
@@ -610,12 +616,12 @@ static lc_status enqueue_sort_dedup(lc_ctx* c) {
   RunState& r = c->rs;
   const Launch& L = c->L;
   unsigned* err = &c->ctr->err;
-  int w2 = radix_sort_u64(r.part, r.next, &c->ctr->emitted, r.mi, 2 * r.bits, c->sort, err,
+  int w2 = radix_sort_u64(r.part, r.next, kept_count(c), r.mi, 2 * r.bits, c->sort, err,
                           c->flags, r.bits, L);
   uint64_t* sorted = w2 ? r.next : r.part;
   r.next = w2 ? r.part : r.next;
   scan_flags(c->flags, r.lv.scan, r.ni, r.lv.mo, r.mo_next, &c->ctr->n_next, c->sort, err, L);
-  unique_rename(sorted, &c->ctr->emitted, r.mi, r.bits, r.lv.scan, r.ni, r.next,
+  unique_rename(sorted, kept_count(c), r.mi, r.bits, r.lv.scan, r.ni, r.next,
                 &c->ctr->m_next, c->sort, err, L);
   return LC_OK;
 }
@@ -649,6 +655,7 @@ static lc_status run_begin(lc_ctx* c, uint32_t* d_labels) {
   c->last_mp.clear();
   c->last_emitted.clear();
   c->last_passes.clear();
+  c->last_kept.clear();
   c->levels.clear();
   c->arena.reset();
   if (c->n == 0) {
@@ -727,10 +734,11 @@ static lc_status run_complete(lc_ctx* c) {
     // buckets of at most 1.5 kBucketTarget distinct keys on average (a 5%
     // margin on the estimate, whose standard error is 2.3%), which keeps the
     // bucket sets below three quarters full; never sized above the written keys
-    if (h.emitted > r.mi || h.mprime > r.mi)
+    if (h.emitted > r.mi || h.mprime > r.mi || (r.filtered && h.filtered > h.emitted))
       return report_internal(c, "inconsistent relabel counters");
+    const uint64_t kept = r.filtered ? h.filtered : h.emitted;
     const double est = hll_estimate(c->h_hll) * 1.05 / 1.5 + 1.0;
-    const uint64_t target = std::min<uint64_t>(std::max<uint64_t>(h.emitted, 1),
+    const uint64_t target = std::min<uint64_t>(std::max<uint64_t>(kept, 1),
                                                (uint64_t)std::min(est, (double)r.mi));
     PassPlan hplan{};
     const int hb = hash_plan(target, &hplan);
@@ -740,7 +748,7 @@ static lc_status run_complete(lc_ctx* c) {
     // a bucket held more distinct keys than its shared-memory set: redo this
     // phase's deduplication by a full sort of the intact keys
     ++c->fallbacks;
-    unmix_keys(r.part, &c->ctr->emitted, r.mi, c->L);
+    unmix_keys(r.part, kept_count(c), r.mi, c->L);
     if (cudaMemsetAsync(&c->ctr->m_next, 0, 2 * sizeof(unsigned long long), c->stream) !=
             cudaSuccess ||
         cudaMemsetAsync(&c->ctr->err, 0, sizeof(unsigned), c->stream) != cudaSuccess ||
@@ -765,6 +773,7 @@ static lc_status run_complete(lc_ctx* c) {
     c->last_mp.push_back(h.mprime);
     c->last_emitted.push_back(h.emitted);
     c->last_passes.push_back(r.passes);
+    c->last_kept.push_back(r.filtered ? h.filtered : h.emitted);
   }
   const bool finished_by_uf = !was_merge && c->finish_edges != 0 && r.mi <= c->finish_edges;
   c->levels.push_back(r.lv);
@@ -939,12 +948,14 @@ extern "C" lc_status lc_last_stats(const lc_ctx* c, uint32_t* rounds, uint64_t* 
   return LC_OK;
 }
 
-extern "C" lc_status lc_last_passes(const lc_ctx* c, uint32_t* rounds, uint32_t* passes_i,
-                                    uint32_t cap) {
+extern "C" lc_status lc_last_dedup(const lc_ctx* c, uint32_t* rounds, uint64_t* kept_i,
+                                   uint32_t* passes_i, uint32_t cap) {
   if (!c) return LC_ERR_INVALID;
   if (rounds) *rounds = c->last_rounds;
-  for (uint32_t i = 0; i < std::min<uint32_t>(cap, (uint32_t)c->last_passes.size()); ++i)
+  for (uint32_t i = 0; i < std::min<uint32_t>(cap, (uint32_t)c->last_passes.size()); ++i) {
+    if (kept_i) kept_i[i] = c->last_kept[i];
     if (passes_i) passes_i[i] = c->last_passes[i];
+  }
   return c->last_passes.size() > cap ? LC_ERR_INVALID : LC_OK;
 }
 

@@ -544,6 +544,30 @@ __global__ void __launch_bounds__(kThreads) k_relabel_first_half(
   }
 }
 
+// Middle pass of a relabel in more than two parts: endpoints of the
+// half-resolved edges in tmp that are still unresolved and lie in [lo, hi)
+// are replaced by their roots and flagged, in place.
+__global__ void __launch_bounds__(kThreads) k_relabel_mid(uint64_t* __restrict__ tmp, uint64_t m,
+                                                          uint32_t n, uint32_t lo, uint32_t hi,
+                                                          const uint32_t* __restrict__ root,
+                                                          unsigned* err) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += stride) {
+    const uint64_t x = tmp[j];
+    uint32_t a = (uint32_t)(x >> 32), b = (uint32_t)x;
+    bool changed = false;
+    if (!(a & kResolved) && a - lo < hi - lo && index_ok(err, kKRelabelSplit, a, n)) {
+      a = __ldg(root + a) | kResolved;
+      changed = true;
+    }
+    if (!(b & kResolved) && b - lo < hi - lo && index_ok(err, kKRelabelSplit, b, n)) {
+      b = __ldg(root + b) | kResolved;
+      changed = true;
+    }
+    if (changed) tmp[j] = ((uint64_t)a << 32) | b;
+  }
+}
+
 // kMode 0: uint32 src/dst; 1: packed (a << 32 | b); 2: packed half-resolved
 // (see k_relabel_first_half).
 template <int kMode>
@@ -813,12 +837,19 @@ void relabel(const uint32_t* src, const uint32_t* dst, const uint64_t* packed, u
                                                   keys_out, mprime, emitted, mix, pl, ghist,
                                                   err, gcache, gmask, admit);
   } else if (tmp != nullptr && n < kResolved && (uint64_t)n * 4 > window_bytes) {
-    // two passes, each gathering from one half of root (see k_relabel_first_half)
-    const uint32_t split = n / 2;
+    // one pass per L2-sized part of root (see k_relabel_first_half)
+    const uint64_t parts = std::min<uint64_t>(8, ((uint64_t)n * 4 + window_bytes - 1) /
+                                                     std::max<uint64_t>(window_bytes, 1));
+    auto cut = [&](uint64_t k) { return (uint32_t)((uint64_t)n * k / parts); };
     {
       KScope ks(L, kKRelabelSplit);
       k_relabel_first_half<<<grid_for(m, kThreads, L), kThreads, 0, L.stream>>>(src, dst, m, n,
-                                                                               split, root, tmp);
+                                                                               cut(1), root, tmp);
+    }
+    for (uint64_t k = 1; k + 1 < parts; ++k) {
+      KScope ks(L, kKRelabelSplit);
+      k_relabel_mid<<<grid_for(m, kThreads, L), kThreads, 0, L.stream>>>(tmp, m, n, cut(k),
+                                                                        cut(k + 1), root, err);
     }
     KScope ks(L, kKRelabelSoa);
     k_relabel<2><<<grid, kThreads, 0, L.stream>>>(nullptr, nullptr, tmp, m, n, root, bits,

@@ -25,7 +25,7 @@ LC_VARIANT_FOREST, LC_VARIANT_TWO_HOP, LC_VARIANT_TREE = 0, 1, 2
 # every symbol include/lc.h declares (checked by the CPU test suite)
 LC_DEDUP_HASH, LC_DEDUP_SORT = 0, 1
 EXPORTED = ("lc_create", "lc_configure", "lc_set_merge_to_large", "lc_set_dedup", "lc_set_param", "lc_run", "lc_run_host",
-            "lc_last_stats", "lc_last_passes", "lc_profile", "lc_kernel_stats", "lc_destroy", "lc_status_str",
+            "lc_last_stats", "lc_last_dedup", "lc_profile", "lc_kernel_stats", "lc_destroy", "lc_status_str",
             "lc_rank_probe", "lc_run_static", "lc_batch_create", "lc_batch_run",
             "lc_server_create", "lc_server_submit", "lc_server_wait", "lc_server_stats",
             "lc_server_destroy")
@@ -60,8 +60,8 @@ def load(path: str | None = None):
     lib.lc_run.argtypes = [p, p, pu32, pu64, pu64, u32]
     lib.lc_run_host.argtypes = [p, p, p, p, pu32, pu64, pu64, u32]
     lib.lc_last_stats.argtypes = [p, pu32, pu64, pu64, u32]
-    lib.lc_last_passes.argtypes = [p, pu32, pu32, u32]
-    lib.lc_last_passes.restype = i32
+    lib.lc_last_dedup.argtypes = [p, pu32, pu64, pu32, u32]
+    lib.lc_last_dedup.restype = i32
     lib.lc_profile.argtypes = [p, i32]
     lib.lc_kernel_stats.argtypes = [p, u32, ctypes.POINTER(ctypes.c_char_p), pu64,
                                     ctypes.POINTER(ctypes.c_double)]
@@ -156,12 +156,14 @@ def lc_run_host(ctx: int, h_src: np.ndarray, h_dst: np.ndarray, h_labels: np.nda
     return r, list(n_i[:r]), list(m_i[:r])
 
 
-def lc_last_passes(ctx: int, cap: int = 1024) -> list[int]:
-    """Partition passes of each phase's hashed dedup in the last run."""
+def lc_last_dedup(ctx: int, cap: int = 1024) -> tuple[list[int], list[int]]:
+    """(kept_i, passes_i) of each phase's deduplication in the last run."""
     R = ctypes.c_uint32(0)
-    out = (ctypes.c_uint32 * cap)()
-    _check(load().lc_last_passes(ctx, ctypes.byref(R), out, cap), "lc_last_passes")
-    return [int(out[i]) for i in range(min(R.value, cap))]
+    kept = (ctypes.c_uint64 * cap)()
+    passes = (ctypes.c_uint32 * cap)()
+    _check(load().lc_last_dedup(ctx, ctypes.byref(R), kept, passes, cap), "lc_last_dedup")
+    r = min(R.value, cap)
+    return [int(kept[i]) for i in range(r)], [int(passes[i]) for i in range(r)]
 
 
 def lc_last_stats(ctx: int, cap: int = 1024) -> tuple[list[int], list[int]]:
