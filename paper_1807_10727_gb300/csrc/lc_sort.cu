@@ -422,43 +422,50 @@ __global__ void k_bucket_bounds(const uint64_t* __restrict__ keys,
 constexpr int kTableSlots = 2 * kBucketTarget;  // per-bucket shared-memory hash set (32 KB)
 constexpr uint64_t kEmpty = ~0ull;  // never a mixed key (static_assert in lc_common.cuh)
 
-__device__ __forceinline__ void set_insert(uint64_t* table, uint64_t key, int* over) {
+// Insert into the open-addressing set; returns the slot when this call put
+// the key there (a new distinct key), else -1.  *over is set when the table
+// is full.
+__device__ __forceinline__ int set_insert(uint64_t* table, uint64_t key, int* over) {
   uint32_t slot = (uint32_t)key & (kTableSlots - 1);  // low bits of the mixed key
-  int probe = 0;
-  for (; probe < kTableSlots; ++probe) {
+  for (int probe = 0; probe < kTableSlots; ++probe) {
     uint64_t cur = *(volatile uint64_t*)&table[slot];
-    if (cur == key) return;
+    if (cur == key) return -1;
     if (cur == kEmpty) {
       uint64_t prev = atomicCAS((unsigned long long*)&table[slot], kEmpty, key);
-      if (prev == kEmpty || prev == key) return;
+      if (prev == kEmpty) return (int)slot;
+      if (prev == key) return -1;
     }
     slot = (slot + 1) & (kTableSlots - 1);
   }
   *over = 1;
+  return -1;
 }
 
 // One bucket per iteration (claimed by ticket): insert its keys into a
 // shared-memory open-addressing set (eight independent loads in flight per
-// thread), then append the distinct keys to `out` (one atomicAdd per bucket)
-// and mark both endpoints of each in `flags`.  Thread t owns table slots
-// t, t + 256, ... when collecting, so the scan is free of bank conflicts.
+// thread); each new distinct key also records its slot in a list, so the
+// collection walks the list (about 2048 entries) instead of all table slots.
+// The distinct keys are appended to `out` (one atomicAdd per bucket), both
+// endpoints of each are marked in `flags`, and their slots are cleared.
 __global__ void __launch_bounds__(kSortThreads) k_bucket_dedup(
     const uint64_t* __restrict__ keys, const uint32_t* __restrict__ bounds, uint32_t nb,
     uint64_t* __restrict__ out, uint64_t cap, unsigned long long* m_next, uint8_t* flags,
     uint32_t n, int half_bits, unsigned* ticket, unsigned* err) {
-  extern __shared__ __align__(16) uint64_t table[];  // [kTableSlots]
-  __shared__ uint32_t ws[kWarps];
-  __shared__ uint32_t s_b;
+  extern __shared__ __align__(16) uint64_t table[];  // [kTableSlots], then the slot list
+  uint16_t* list = reinterpret_cast<uint16_t*>(table + kTableSlots);  // [kTableSlots]
+  __shared__ uint32_t s_b, s_cnt;
   __shared__ unsigned long long s_base;
   __shared__ int s_over;
   const unsigned tid = threadIdx.x;
-  constexpr int kPer = kTableSlots / kSortThreads;
   constexpr int kIlp = 8;
   for (int i = tid; i < kTableSlots; i += kSortThreads) table[i] = kEmpty;
   if (tid == 0) s_over = 0;
   const uint64_t half_mask = (1ull << half_bits) - 1;
   for (;;) {
-    if (tid == 0) s_b = atomicAdd(ticket, 1u);
+    if (tid == 0) {
+      s_b = atomicAdd(ticket, 1u);
+      s_cnt = 0;
+    }
     __syncthreads();
     const uint32_t b = s_b;
     if (b >= nb) break;
@@ -471,15 +478,14 @@ __global__ void __launch_bounds__(kSortThreads) k_bucket_dedup(
         kk[j] = i < hi ? __ldcs(keys + i) : kEmpty;
       }
 #pragma unroll
-      for (int j = 0; j < kIlp; ++j)
-        if (kk[j] != kEmpty) set_insert(table, kk[j], &s_over);
+      for (int j = 0; j < kIlp; ++j) {
+        if (kk[j] == kEmpty) continue;
+        const int slot = set_insert(table, kk[j], &s_over);
+        if (slot >= 0) list[atomicAdd(&s_cnt, 1u)] = (uint16_t)slot;
+      }
     }
     __syncthreads();
-    uint32_t cnt = 0;
-#pragma unroll
-    for (int s = 0; s < kPer; ++s) cnt += table[s * kSortThreads + tid] != kEmpty;
-    uint32_t total;
-    uint32_t excl = block_exclusive_scan(cnt, ws, &total);
+    const uint32_t total = s_cnt;
     if (tid == 0) {
       s_base = total ? atomicAdd(m_next, (unsigned long long)total) : 0ull;
       if (s_over) {
@@ -488,21 +494,18 @@ __global__ void __launch_bounds__(kSortThreads) k_bucket_dedup(
       }
     }
     __syncthreads();
-    uint64_t pos = s_base + excl;
-#pragma unroll
-    for (int s = 0; s < kPer; ++s) {
-      uint64_t v = table[s * kSortThreads + tid];
-      if (v != kEmpty) {
-        if (index_ok(err, kKBucketDedup, pos, cap)) out[pos] = v;
-        ++pos;
-        uint64_t k = key_unmix(v);
-        const uint64_t a = k >> half_bits, b = k & half_mask;
-        if (index_ok(err, kKBucketDedup, a > b ? a : b, n)) {
-          flags[a] = 1;
-          flags[b] = 1;
-        }
-        table[s * kSortThreads + tid] = kEmpty;
+    for (uint32_t e = tid; e < total; e += kSortThreads) {
+      const uint32_t slot = list[e];
+      const uint64_t v = table[slot];
+      const uint64_t pos = s_base + e;
+      if (index_ok(err, kKBucketDedup, pos, cap)) out[pos] = v;
+      const uint64_t k = key_unmix(v);
+      const uint64_t a = k >> half_bits, c = k & half_mask;
+      if (index_ok(err, kKBucketDedup, a > c ? a : c, n)) {
+        flags[a] = 1;
+        flags[c] = 1;
       }
+      table[slot] = kEmpty;
     }
     // the next iteration's barrier orders these clears before new inserts
   }
@@ -673,7 +676,7 @@ static size_t sort_pass_smem(int rb) {
   return (size_t)kSortTile * 8 + (size_t)kWarps * (1u << rb) * 4 + (size_t)(1u << rb) * 4;
 }
 
-static size_t dedup_smem() { return (size_t)kTableSlots * 8; }
+static size_t dedup_smem() { return (size_t)kTableSlots * (8 + 2); }
 
 // Opt in to more than 48 KB of dynamic shared memory (a cheap host call,
 // repeated before each use so every device the library runs on sees it).
