@@ -474,7 +474,9 @@ static lc_status enqueue_phase(lc_ctx* c) {
       *q = reinterpret_cast<unsigned long long*>(c->arena.alloc(2ull * ni, &aerr));
       if (aerr != cudaSuccess) return fail(c, status_of(aerr));
     }
-    ms.ctrs = c->arena.alloc(2, &aerr);
+    ms.ctrs = c->arena.alloc(3, &aerr);
+    if (aerr != cudaSuccess) return fail(c, status_of(aerr));
+    ms.big = c->arena.alloc(merge_big_words(prev.n), &aerr);
     if (aerr != cudaSuccess) return fail(c, status_of(aerr));
     merge_to_large_names(prev.root, prev.scan, prev.n, rk, c->merge_alpha[i], r.packed, mi, ni,
                          r.lv.root, r.lv.mo, ms, err, L);

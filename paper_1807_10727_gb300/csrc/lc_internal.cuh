@@ -319,12 +319,19 @@ void union_find_names(const uint32_t* src, const uint32_t* dst, const uint64_t* 
 // Scratch of the MergeToLarge step: n' words for cnt, off, fill, list and
 // n' 64-bit words for prio, h1, h2 (n' = nodes of the contracted graph); n_i
 // words for members and n_i 64-bit words for cand (n_i = vertices of the
-// phase's input); two counter words.
+// phase's input); three counter words; the big-node tables.
 struct MergeScratch {
   uint32_t *cnt, *off, *fill, *list, *members;
   unsigned long long *cand, *prio, *h1, *h2;
-  unsigned* ctrs;
+  unsigned* ctrs;  // 3 words
+  uint32_t* big;   // merge_big_words(n_i) words: nodes of >= 2^15 members
 };
+
+// Words of MergeScratch::big for a phase input of n_i vertices.
+inline uint64_t merge_big_words(uint32_t n_i) {
+  const uint64_t nb = n_i / (1u << 15) + 1;
+  return nb * (1 + 256 + 1) + 1 + 2 * nb;
+}
 
 // MergeToLarge (Section 5) on the graph G' (n2 nodes, packed edges e[m])
 // that the last phase made from G_i (n_i vertices; root_i, scan_i its root

@@ -16,6 +16,9 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kSelThreads = 256;
 constexpr int kDigits = 256;
+// Large nodes with at least this many members take the first digit of their
+// select from the whole grid (k_m2l_big_*), not from one block.
+constexpr uint32_t kBigGroup = 1u << 15;
 
 inline int grid_for(uint64_t work, int per_block, const Launch& L, int blocks_per_sm = 8) {
   uint64_t b = (work + per_block - 1) / per_block;
@@ -48,14 +51,89 @@ __global__ void k_m2l_count(const uint32_t* __restrict__ root, const uint32_t* _
 // Large nodes: a segment [off[x], off[x] + cnt[x]) of the member array each
 // (segments in any order) and an entry in the list of large nodes.
 // ctrs[0] = member slots handed out, ctrs[1] = large nodes.
+// Nodes of at least kBigGroup members are also listed in big_list (ctrs[2]
+// of them, at most nbig_max).
 __global__ void k_m2l_large(const uint32_t* __restrict__ cnt, uint32_t n2, uint32_t alpha,
-                            uint32_t* off, uint32_t* list, unsigned* ctrs) {
+                            uint32_t* off, uint32_t* list, unsigned* ctrs, uint32_t* big_list,
+                            uint32_t nbig_max, unsigned* err) {
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n2; x += stride) {
     const uint32_t c = cnt[x];
     if (c >= alpha) {
       off[x] = atomicAdd(&ctrs[0], c);
       list[atomicAdd(&ctrs[1], 1u)] = (uint32_t)x;
+      if (c >= kBigGroup) {
+        const uint32_t j = atomicAdd(&ctrs[2], 1u);
+        if (index_ok(err, kKMergeGroup, j, nbig_max)) big_list[j] = (uint32_t)x;
+      }
+    }
+  }
+}
+
+// Big nodes, first digit over the whole grid: hist[j][d] = members of big
+// node j whose key's top byte is d.
+__global__ void __launch_bounds__(kSelThreads) k_m2l_big_hist(
+    const uint32_t* __restrict__ members, const uint32_t* __restrict__ cnt,
+    const uint32_t* __restrict__ off, const uint32_t* __restrict__ big_list, const unsigned* ctrs,
+    uint32_t nbig_max, uint64_t rk, uint32_t* __restrict__ hist) {
+  __shared__ uint32_t h[kDigits];
+  const uint32_t nbig = min(ctrs[2], nbig_max);
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint32_t j = 0; j < nbig; ++j) {
+    for (int d = threadIdx.x; d < kDigits; d += blockDim.x) h[d] = 0;
+    __syncthreads();
+    const uint32_t x = big_list[j], c = cnt[x], o = off[x];
+    for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < c; k += stride)
+      atomicAdd(&h[phase_key(rk, members[o + k]) >> 56], 1u);
+    __syncthreads();
+    for (int d = threadIdx.x; d < kDigits; d += blockDim.x)
+      if (h[d]) atomicAdd(&hist[(uint64_t)j * kDigits + d], h[d]);
+    __syncthreads();
+  }
+}
+
+// One thread per big node: the top digit of its alpha-th largest key, and the
+// rank still sought among the members that share it.  pick[j] = (digit, need).
+__global__ void k_m2l_big_pick(const uint32_t* __restrict__ hist, const unsigned* ctrs,
+                               uint32_t nbig_max, uint32_t alpha, uint2* pick, unsigned* err) {
+  const uint32_t nbig = min(ctrs[2], nbig_max);
+  for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < nbig;
+       j += gridDim.x * blockDim.x) {
+    uint32_t above = 0, sel = kDigits;
+    for (int d = kDigits - 1; d >= 0; --d) {
+      const uint32_t c = hist[(uint64_t)j * kDigits + d];
+      if (above + c >= alpha) {
+        sel = (uint32_t)d;
+        break;
+      }
+      above += c;
+    }
+    if (sel == kDigits) {  // fewer than alpha members: corrupted counts
+      index_ok(err, kKMergeSelect, alpha, above + 1);
+      sel = 0;
+      above = 0;
+    }
+    pick[j] = make_uint2(sel, alpha - above);
+  }
+}
+
+// The members of each big node whose top byte is the picked digit, as keys,
+// to the front of its cand segment (bigcnt[j] of them).
+__global__ void __launch_bounds__(kSelThreads) k_m2l_big_compact(
+    const uint32_t* __restrict__ members, const uint32_t* __restrict__ cnt,
+    const uint32_t* __restrict__ off, const uint32_t* __restrict__ big_list, const unsigned* ctrs,
+    uint32_t nbig_max, uint64_t rk, const uint2* __restrict__ pick, unsigned long long* cand,
+    uint32_t* bigcnt, unsigned* err) {
+  const uint32_t nbig = min(ctrs[2], nbig_max);
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint32_t j = 0; j < nbig; ++j) {
+    const uint32_t x = big_list[j], c = cnt[x], o = off[x], sel = pick[j].x;
+    for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < c; k += stride) {
+      const uint64_t key = phase_key(rk, members[o + k]);
+      if ((key >> 56) == sel) {
+        const uint32_t q = atomicAdd(&bigcnt[j], 1u);
+        if (index_ok(err, kKMergeSelect, q, c)) cand[o + q] = key;
+      }
     }
   }
 }
@@ -81,21 +159,32 @@ __global__ void k_m2l_scatter(const uint32_t* __restrict__ root, const uint32_t*
 // by one block per node.  The first digit is taken over all members; the
 // members that share it are copied (as keys) to cand, and the other seven
 // digits are taken over those.  prio[x] = key + 1 (0 marks a small node).
+// big_mode: only the big nodes, whose first digit, remaining rank and
+// candidates the k_m2l_big_* kernels produced.
 __global__ void __launch_bounds__(kSelThreads) k_m2l_select(
     const uint32_t* __restrict__ members, unsigned long long* cand,
     const uint32_t* __restrict__ cnt, const uint32_t* __restrict__ off,
     const uint32_t* __restrict__ list, const unsigned* ctrs, uint32_t alpha, uint64_t rk,
-    unsigned long long* prio, unsigned* err) {
+    unsigned long long* prio, unsigned* err, int big_mode, const uint32_t* __restrict__ big_list,
+    uint32_t nbig_max, const uint2* __restrict__ pick, const uint32_t* __restrict__ bigcnt) {
   __shared__ uint32_t hist[kDigits];
   __shared__ uint32_t s_digit, s_need, s_ncand;
-  const uint32_t nlarge = ctrs[1];
-  for (uint32_t j = blockIdx.x; j < nlarge; j += gridDim.x) {
-    const uint32_t x = list[j];
+  const uint32_t count = big_mode ? min(ctrs[2], nbig_max) : ctrs[1];
+  for (uint32_t j = blockIdx.x; j < count; j += gridDim.x) {
+    const uint32_t x = big_mode ? big_list[j] : list[j];
     const uint32_t c = cnt[x], o = off[x];
+    if (!big_mode && c >= kBigGroup) continue;  // selected in big mode
     uint64_t prefix = 0;
     uint32_t need = alpha;  // rank (1 = largest) still sought among the candidates
     uint32_t ncand = c;
-    for (int pass = 0; pass < 8; ++pass) {
+    int first = 0;
+    if (big_mode) {  // first digit already taken by the whole grid
+      prefix = (uint64_t)pick[j].x << 56;
+      need = pick[j].y;
+      ncand = bigcnt[j];
+      first = 1;
+    }
+    for (int pass = first; pass < 8; ++pass) {
       const int shift = 56 - 8 * pass;
       for (int d = threadIdx.x; d < kDigits; d += blockDim.x) hist[d] = 0;
       if (threadIdx.x == 0) s_ncand = 0;
@@ -201,7 +290,14 @@ void merge_to_large_names(const uint32_t* root_i, const uint32_t* scan_i, uint32
   if (n2 == 0) return;
   cudaMemsetAsync(s.cnt, 0, sizeof(uint32_t) * n2, L.stream);
   cudaMemsetAsync(s.fill, 0, sizeof(uint32_t) * n2, L.stream);
-  cudaMemsetAsync(s.ctrs, 0, sizeof(unsigned) * 2, L.stream);
+  cudaMemsetAsync(s.ctrs, 0, sizeof(unsigned) * 3, L.stream);
+  const uint32_t nbig_max = n_i / kBigGroup + 1;
+  uint32_t* big_list = s.big;
+  uint32_t* big_hist = big_list + nbig_max;
+  uint32_t* bigcnt = big_hist + (uint64_t)nbig_max * kDigits;
+  // 258 * nbig_max words precede it: 8-byte aligned
+  uint2* pick = reinterpret_cast<uint2*>(bigcnt + nbig_max);
+  cudaMemsetAsync(big_hist, 0, sizeof(uint32_t) * (uint64_t)nbig_max * (kDigits + 1), L.stream);
   cudaMemsetAsync(s.prio, 0, sizeof(unsigned long long) * n2, L.stream);
   {
     KScope ks(L, kKMergeGroup);
@@ -210,8 +306,8 @@ void merge_to_large_names(const uint32_t* root_i, const uint32_t* scan_i, uint32
   }
   {
     KScope ks(L, kKMergeGroup);
-    k_m2l_large<<<grid_for(n2, kThreads, L), kThreads, 0, L.stream>>>(s.cnt, n2, alpha, s.off,
-                                                                      s.list, s.ctrs);
+    k_m2l_large<<<grid_for(n2, kThreads, L), kThreads, 0, L.stream>>>(
+        s.cnt, n2, alpha, s.off, s.list, s.ctrs, big_list, nbig_max, err);
   }
   {
     KScope ks(L, kKMergeGroup);
@@ -224,7 +320,33 @@ void merge_to_large_names(const uint32_t* root_i, const uint32_t* scan_i, uint32
     const uint64_t most = std::max<uint64_t>(1, n2 / std::max<uint32_t>(alpha, 1));
     const int grid = (int)std::min<uint64_t>(most, (uint64_t)L.sms * 8);
     k_m2l_select<<<grid, kSelThreads, 0, L.stream>>>(s.members, s.cand, s.cnt, s.off, s.list,
-                                                     s.ctrs, alpha, rk, s.prio, err);
+                                                     s.ctrs, alpha, rk, s.prio, err, 0, big_list,
+                                                     nbig_max, pick, bigcnt);
+  }
+  if ((uint64_t)n_i >= kBigGroup && alpha <= n_i) {
+    // big nodes: first digit and compaction over the whole grid, then the
+    // remaining digits one block per node
+    const int grid = L.sms * 4;
+    {
+      KScope ks(L, kKMergeSelect);
+      k_m2l_big_hist<<<grid, kSelThreads, 0, L.stream>>>(s.members, s.cnt, s.off, big_list,
+                                                         s.ctrs, nbig_max, rk, big_hist);
+    }
+    {
+      KScope ks(L, kKMergeSelect);
+      k_m2l_big_pick<<<(nbig_max + 255) / 256, 256, 0, L.stream>>>(big_hist, s.ctrs, nbig_max,
+                                                                 alpha, pick, err);
+    }
+    {
+      KScope ks(L, kKMergeSelect);
+      k_m2l_big_compact<<<grid, kSelThreads, 0, L.stream>>>(s.members, s.cnt, s.off, big_list,
+                                                            s.ctrs, nbig_max, rk, pick, s.cand,
+                                                            bigcnt, err);
+    }
+    KScope ks(L, kKMergeSelect);
+    k_m2l_select<<<(int)std::min<uint32_t>(nbig_max, (uint32_t)L.sms * 8), kSelThreads, 0,
+                   L.stream>>>(s.members, s.cand, s.cnt, s.off, s.list, s.ctrs, alpha, rk, s.prio,
+                               err, 1, big_list, nbig_max, pick, bigcnt);
   }
   // best priority within distance 1, then within distance 2
   {
