@@ -504,8 +504,10 @@ static lc_status enqueue_phase(lc_ctx* c) {
       // second hop; names are label vertices, node minima in their own array
       uint32_t* nmo = c->arena.alloc(ni, &aerr);
       if (aerr != cudaSuccess) return fail(c, status_of(aerr));
-      two_hop_names(src0, dst0, r.packed, mi, ni, c->minkey, c->minkey2, r.lv.root, r.lv.mo, nmo,
-                    err, L);
+      uint32_t* fpar = c->arena.alloc(ni, &aerr);
+      if (aerr != cudaSuccess) return fail(c, status_of(aerr));
+      two_hop_names(src0, dst0, r.packed, mi, ni, rk, bp, c->minkey, c->minkey2, fpar, r.lv.root,
+                    r.lv.mo, nmo, err, L);
       r.lv.mo = nmo;
     } else {
       // (c): roots of the parent arborescences

@@ -299,15 +299,17 @@ void stamp_counters(Counters* ctr, uint64_t tag, const Launch& L);
 // Node names of the other phase variants (edges as in edge_min; root[v]
 // receives the name of v's node):
 //  - two_hop_names: published LocalContraction label, min key over N(N(v))
-//    (mk1 = closed-neighbourhood minima from edge_min; mk2 scratch); names
-//    need not be members of their group, so node minima go to nmo (n words).
+//    (mk1 = closed-neighbourhood minima from edge_min; mk2 and fpar, n words,
+//    scratch; rk / batch give the keys); names need not be members of their
+//    group, so node minima go to nmo (n words).
 //  - tree_names: TreeContraction, parent = low half of the open-neighbourhood
 //    minimum in minkey (edge_min with open; ~0 = no other neighbour), name =
 //    lower-key vertex of the terminal 2-cycle; node minima in mo in place.
 //  - union_find_names: every vertex named by its component's smallest id
 //    (the small-graph finish); parent is n words of scratch.
 void two_hop_names(const uint32_t* src, const uint32_t* dst, const uint64_t* packed, uint64_t m,
-                   uint32_t n, const unsigned long long* mk1, unsigned long long* mk2,
+                   uint32_t n, uint64_t rk, const BatchView* batch,
+                   const unsigned long long* mk1, unsigned long long* mk2, uint32_t* fpar,
                    uint32_t* root, const uint32_t* mo, uint32_t* nmo, unsigned* err,
                    const Launch& L);
 void tree_names(const unsigned long long* minkey, uint32_t* root, uint32_t* mo, uint32_t n,

@@ -308,13 +308,16 @@ __device__ __forceinline__ void two_hop_apply(uint32_t u, uint32_t v, unsigned l
 }
 
 // Edges as uint32 arrays (phase 0; `vec` = 16-byte aligned; ids >= n were
-// reported by edge_min and are skipped) or packed (a << 32 | b).  Four edges
-// per iteration, their eight mk1 gathers issued before any atomic.
+// reported by edge_min and are skipped) or packed (a << 32 | b).  mk1[u] is
+// the key of f(u), so the kernel gathers the 4-byte f (fpar, half the bytes
+// of mk1, so more of it stays in L2) and recomputes the keys.  Four edges per
+// iteration, their eight gathers issued before any update.
+template <class K>
 __global__ void __launch_bounds__(kThreads) k_two_hop(const uint32_t* __restrict__ src,
                                                       const uint32_t* __restrict__ dst,
                                                       const uint64_t* __restrict__ packed,
-                                                      uint64_t m, uint32_t n, int vec,
-                                                      const unsigned long long* __restrict__ mk1,
+                                                      uint64_t m, uint32_t n, int vec, K keys,
+                                                      const uint32_t* __restrict__ fpar,
                                                       unsigned long long* mk2, unsigned* err) {
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   const uint64_t gt = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -337,17 +340,21 @@ __global__ void __launch_bounds__(kThreads) k_two_hop(const uint32_t* __restrict
       v[0] = d.x; v[1] = d.y; v[2] = d.z; v[3] = d.w;
     }
     bool ok[4];
-    unsigned long long a[4], b[4];
+    uint32_t fu[4], fv[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       ok[i] = packed != nullptr ? index_ok(err, kKTwoHop, max(u[i], v[i]), n)
                                 : (u[i] < n && v[i] < n);
-      a[i] = ok[i] ? __ldg(mk1 + u[i]) : 0ull;
-      b[i] = ok[i] ? __ldg(mk1 + v[i]) : 0ull;
+      fu[i] = ok[i] ? __ldg(fpar + u[i]) : 0u;
+      fv[i] = ok[i] ? __ldg(fpar + v[i]) : 0u;
     }
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
-      if (ok[i]) two_hop_apply(u[i], v[i], a[i], b[i], mk2);
+    for (int i = 0; i < 4; ++i) {
+      if (!ok[i] || fu[i] == fv[i]) continue;
+      uint64_t a, b;
+      keys.pair(fu[i], fv[i], a, b);  // f(u), f(v) lie in u's graph
+      two_hop_apply(u[i], v[i], a, b, mk2);
+    }
   }
   for (uint64_t j = nq * 4 + gt; j < m; j += stride) {
     uint32_t u, v;
@@ -361,7 +368,11 @@ __global__ void __launch_bounds__(kThreads) k_two_hop(const uint32_t* __restrict
       v = __ldcs(dst + j);
       if (u >= n || v >= n) continue;
     }
-    two_hop_apply(u, v, __ldg(mk1 + u), __ldg(mk1 + v), mk2);
+    const uint32_t fu = __ldg(fpar + u), fv = __ldg(fpar + v);
+    if (fu == fv) continue;
+    uint64_t a, b;
+    keys.pair(fu, fv, a, b);
+    two_hop_apply(u, v, a, b, mk2);
   }
 }
 
@@ -400,11 +411,16 @@ struct UnionOp {
   }
 };
 
-__global__ void k_copy_u64(unsigned long long* __restrict__ dst,
-                           const unsigned long long* __restrict__ src, uint32_t n) {
+// mk2 = mk1, fpar = the low halves of mk1 (the parents f).
+__global__ void k_two_hop_init(unsigned long long* __restrict__ mk2,
+                               const unsigned long long* __restrict__ mk1,
+                               uint32_t* __restrict__ fpar, uint32_t n) {
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride)
-    dst[v] = src[v];
+  for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+    const unsigned long long k = mk1[v];
+    mk2[v] = k;
+    fpar[v] = (uint32_t)k;
+  }
 }
 
 // Two-hop names: root[v] = the label vertex low32(mk2[v]); nmo[name] = min of
@@ -886,21 +902,32 @@ static void for_edges(const uint32_t* src, const uint32_t* dst, const uint64_t* 
                                                                    err);
 }
 
+template <class K>
+static void two_hop_impl(const uint32_t* src, const uint32_t* dst, const uint64_t* packed,
+                         uint64_t m, uint32_t n, K keys, const uint32_t* fpar,
+                         unsigned long long* mk2, unsigned* err, const Launch& L) {
+  const int vec = ((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst)) & 15) == 0;
+  KScope ks(L, kKTwoHop);
+  k_two_hop<<<grid_for((m + 3) / 4, kThreads, L), kThreads, 0, L.stream>>>(
+      src, dst, packed, m, n, vec, keys, fpar, mk2, err);
+}
+
 void two_hop_names(const uint32_t* src, const uint32_t* dst, const uint64_t* packed, uint64_t m,
-                   uint32_t n, const unsigned long long* mk1, unsigned long long* mk2,
+                   uint32_t n, uint64_t rk, const BatchView* batch,
+                   const unsigned long long* mk1, unsigned long long* mk2, uint32_t* fpar,
                    uint32_t* root, const uint32_t* mo, uint32_t* nmo, unsigned* err,
                    const Launch& L) {
   if (n == 0) return;
   {
     KScope ks(L, kKTwoHop);
-    k_copy_u64<<<grid_for(n, kThreads, L), kThreads, 0, L.stream>>>(mk2, mk1, n);
+    k_two_hop_init<<<grid_for(n, kThreads, L), kThreads, 0, L.stream>>>(mk2, mk1, fpar, n);
   }
   if (m) {
-    const int vec =
-        ((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst)) & 15) == 0;
-    KScope ks(L, kKTwoHop);
-    k_two_hop<<<grid_for((m + 3) / 4, kThreads, L), kThreads, 0, L.stream>>>(
-        src, dst, packed, m, n, vec, mk1, mk2, err);
+    if (batch)
+      two_hop_impl(src, dst, packed, m, n, BatchKeys{batch->rk, batch->voff, batch->k}, fpar,
+                   mk2, err, L);
+    else
+      two_hop_impl(src, dst, packed, m, n, GraphKeys{rk}, fpar, mk2, err, L);
   }
   cudaMemsetAsync(nmo, 0xFF, sizeof(uint32_t) * n, L.stream);
   KScope ks(L, kKTwoHop);
