@@ -187,12 +187,19 @@ def test_relabel_cache_sizes(lc_lib, cuda, dedup):
         ctx.set_param("relabel_cache_slots", slots)
         labels, res = ctx.run()
         mp, em = lc.lc_last_stats(ctx.ctx)
+        kept, passes = lc.lc_last_dedup(ctx.ctx)
         ctx.close()
+        assert len(kept) == len(passes) == res.rounds
+        assert all(k <= e <= p for k, e, p in zip(kept, em, mp))
+        if slots == 0:
+            assert kept == em  # nothing drops keys after the relabel
+        if dedup == lc.LC_DEDUP_SORT:
+            assert not any(passes)
         assert res.rounds == ref.rounds
         assert list(zip(res.n_i, res.m_i)) == ref.sizes()
         assert mp == [int(x) for x in ref.mp_i]
         assert np.array_equal(labels.cpu().numpy().view(np.uint32), ref.labels)
-        emitted[slots] = em[0]
+        emitted[slots] = kept[0]
     assert emitted[1 << 20] <= emitted[0]
     for bad in (3, 512, 1 << 27):
         ctx = lc.LocalContraction(g.n, ts, td, seed=g.seed)
