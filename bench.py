@@ -16,7 +16,7 @@ Extra keys on the JSON line:
   cpu_baseline  the CPU oracle (single thread) on a bounded prefix sample.
 
 --impl reference times the CPU oracle on the same bounded sample per step
-(the "reference" of this build is the oracle written from the paper).
+(the reference arm is the oracle written from the paper).
 Multi-GPU (--gpus N under torchrun): the single-graph path does not shard, so
 every rank runs its own replica (weak scaling); value = all ranks' edges /
 the slowest rank's time.
