@@ -206,3 +206,23 @@ def test_relabel_cache_sizes(lc_lib, cuda, dedup):
         with pytest.raises(lc.LCError):
             ctx.set_param("relabel_cache_slots", bad)
         ctx.close()
+
+
+@pytest.mark.parametrize("name", ["er16", "rmat18", "gridmix_small"])
+def test_multi_part_relabel(lc_lib, cuda, name):
+    """Phase 0 relabels in parts when the root array is larger than the part
+    size: two parts and three parts (with a middle pass), forced here on
+    small graphs."""
+    g = synth.workload(name)
+    ref = oracle.lc_run(g.n, g.src, g.dst, g.seed)
+    ts, td = dev(g.src, cuda), dev(g.dst, cuda)
+    for part_bytes in (4 * g.n - 1, (4 * g.n) // 3):
+        ctx = lc.LocalContraction(g.n, ts, td, seed=g.seed)
+        ctx.set_param("relabel_window_bytes", part_bytes)
+        labels, res = ctx.run()
+        mp = ctx.mprime()
+        ctx.close()
+        assert res.rounds == ref.rounds
+        assert list(zip(res.n_i, res.m_i)) == ref.sizes()
+        assert mp == [int(x) for x in ref.mp_i]
+        assert np.array_equal(labels.cpu().numpy().view(np.uint32), ref.labels)
