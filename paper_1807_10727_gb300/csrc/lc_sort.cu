@@ -422,19 +422,16 @@ __global__ void k_bucket_bounds(const uint64_t* __restrict__ keys,
 constexpr int kTableSlots = 2 * kBucketTarget;  // per-bucket shared-memory hash set (32 KB)
 constexpr uint64_t kEmpty = ~0ull;  // never a mixed key (static_assert in lc_common.cuh)
 
-// Insert into the open-addressing set; returns the slot when this call put
-// the key there (a new distinct key), else -1.  *over is set when the table
-// is full.
+// Insert into the open-addressing set with one compare-and-swap per probe
+// (it also returns what the slot holds, so no separate read is needed);
+// returns the slot when this call put the key there (a new distinct key),
+// else -1.  *over is set when the table is full.
 __device__ __forceinline__ int set_insert(uint64_t* table, uint64_t key, int* over) {
   uint32_t slot = (uint32_t)key & (kTableSlots - 1);  // low bits of the mixed key
   for (int probe = 0; probe < kTableSlots; ++probe) {
-    uint64_t cur = *(volatile uint64_t*)&table[slot];
-    if (cur == key) return -1;
-    if (cur == kEmpty) {
-      uint64_t prev = atomicCAS((unsigned long long*)&table[slot], kEmpty, key);
-      if (prev == kEmpty) return (int)slot;
-      if (prev == key) return -1;
-    }
+    uint64_t prev = atomicCAS((unsigned long long*)&table[slot], kEmpty, key);
+    if (prev == kEmpty) return (int)slot;
+    if (prev == key) return -1;
     slot = (slot + 1) & (kTableSlots - 1);
   }
   *over = 1;
