@@ -71,7 +71,8 @@ typedef enum {
  *   stream   cudaStream_t as void*.
  *   out      receives the context.
  * Allocates all device scratch for a run (about 16*m + 40*n bytes plus sort
- * status words); returns LC_ERR_OOM if that fails.  Ids are validated on the
+ * status words, and 64 MiB more for m >= 2^22: see "relabel_cache_slots");
+ * returns LC_ERR_OOM if that fails.  Ids are validated on the
  * device during lc_run (LC_ERR_INVALID from lc_run). */
 lc_status lc_create(uint32_t n, const uint32_t* d_src, const uint32_t* d_dst, uint64_t m,
                     uint64_t seed, void* stream, lc_ctx** out);
