@@ -42,7 +42,7 @@ METRIC = "input edges/sec to final labels (1 GB300), HBM roofline %"
 # committed full-size ncu capture (profiles/traffic_rmat26.md); valid while
 # the kernels are unchanged and only for the R-MAT 26 workload.
 TRAFFIC_RATIO = {"relabel_soa": 2.435, "relabel_split": 2.369, "edge_min_soa": 1.742,
-                 "filter_hll": 1.342, "sort_pass": 1.031}
+                 "filter_hll": 1.342}
 UNIT = "edges/s"
 CPU_SAMPLE_EDGES = 1 << 24
 

@@ -151,6 +151,16 @@ lc_status lc_set_dedup(lc_ctx* ctx, lc_dedup mode);
  *   "relabel_cache_admit"  a key missing from that cache enters it at one in
  *                   2^value of its occurrences (0..16, default 3), so that
  *                   keys seen once rarely evict repeated ones.
+ *   "max_rounds"    phase cap (default 0: 64 + 4 log2 n, far above the
+ *                   O(log n) bound); a run that needs more phases returns
+ *                   LC_ERR_NO_CONVERGENCE.
+ *   "spin_limit"    bound (1..2^30, default 2^24 polls) of each wait of a
+ *                   partition pass on its predecessor tiles (decoupled
+ *                   look-back); a wait that runs out ends the run with
+ *                   LC_ERR_TIMEOUT, and the context stays usable.
+ *   "inject_lookback_stall"  1: in the next partition pass, tile 0 publishes
+ *                   nothing, so the waits behind it run out (a test of the
+ *                   timeout path that faults nothing; one shot).
  * Phases with at least 2^22 edges also size their deduplication buckets from
  * a HyperLogLog estimate (Flajolet et al. 2007) of the distinct relabelled
  * keys, read back after the relabel step; the others from m_i.

@@ -232,6 +232,7 @@ struct lc_ctx {
   uint64_t window_bytes = 192ull << 20;  // L2 budget of one phase-0 minimum pass
   uint64_t relabel_window_bytes = 160ull << 20;  // root-array size above which relabel splits
 
+  uint32_t max_rounds = 0;  // phase cap (0: 64 + 4 log2 n)
   uint32_t last_rounds = 0;
   std::vector<uint64_t> last_mp;
   std::vector<uint64_t> last_emitted;
@@ -731,9 +732,11 @@ static lc_status run_complete(lc_ctx* c) {
     return r.st;
   const Counters& h = *c->h_ctr;
   if (h.tag != c->tag) return report_internal(c, "stale counters");
+  // a wait that ran out leaves later steps with unknown offsets, whose index
+  // checks then fail too: the timeout is the cause to report
+  if (h.err & kErrTimeout) return fail(c, LC_ERR_TIMEOUT);
   if (h.err & kErrCorrupt) return report_corrupt(c);
   if (h.err & kErrBadVertex) return fail(c, LC_ERR_INVALID);
-  if (h.err & kErrTimeout) return fail(c, LC_ERR_TIMEOUT);
   if (r.state == RunState::kRelabel) {
     // buckets of at most 1.5 kBucketTarget distinct keys on average (a 5%
     // margin on the estimate, whose standard error is 2.3%), which keeps the
@@ -792,7 +795,8 @@ static lc_status run_complete(lc_ctx* c) {
     r.merge_step = true;
     return enqueue_phase(c);
   }
-  if (++r.i >= round_cap(c->n)) return fail(c, LC_ERR_NO_CONVERGENCE);
+  if (++r.i >= (c->max_rounds ? c->max_rounds : round_cap(c->n)))
+    return fail(c, LC_ERR_NO_CONVERGENCE);
   return enqueue_phase(c);
 }
 
@@ -975,6 +979,21 @@ extern "C" lc_status lc_set_param(lc_ctx* c, const char* name, uint64_t value) {
   if (std::strcmp(name, "window_bytes") == 0) {
     if (value < (1u << 20)) return LC_ERR_INVALID;
     c->window_bytes = value;
+    return LC_OK;
+  }
+  if (std::strcmp(name, "max_rounds") == 0) {
+    if (value > (1u << 20)) return LC_ERR_INVALID;
+    c->max_rounds = (uint32_t)value;
+    return LC_OK;
+  }
+  if (std::strcmp(name, "spin_limit") == 0) {
+    if (value == 0 || value > (1u << 30)) return LC_ERR_INVALID;
+    c->sort.spin_limit = (uint32_t)value;
+    return LC_OK;
+  }
+  if (std::strcmp(name, "inject_lookback_stall") == 0) {
+    if (value > 1) return LC_ERR_INVALID;
+    c->sort.stall_once = (int)value;
     return LC_OK;
   }
   if (std::strcmp(name, "relabel_window_bytes") == 0) {

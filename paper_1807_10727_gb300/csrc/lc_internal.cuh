@@ -135,6 +135,8 @@ struct SortScratch {
   uint32_t* hist = nullptr;       // [kMaxPasses * kRadixMax] global digit counts / offsets
   unsigned* tickets = nullptr;    // [16] dynamic tile counters
   uint32_t epoch = 0;             // last epoch used (1..2^30-1)
+  uint32_t spin_limit = kSpinLimit;  // bound of each partition-pass look-back wait
+  int stall_once = 0;             // test hook: the next partition pass's tile 0 stays silent
 };
 
 uint64_t sort_status_words(uint64_t max_keys);

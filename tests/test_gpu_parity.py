@@ -226,3 +226,41 @@ def test_multi_part_relabel(lc_lib, cuda, name):
         assert list(zip(res.n_i, res.m_i)) == ref.sizes()
         assert mp == [int(x) for x in ref.mp_i]
         assert np.array_equal(labels.cpu().numpy().view(np.uint32), ref.labels)
+
+
+def test_round_cap_and_wait_timeout(lc_lib, cuda):
+    """Failure paths that fault nothing: a phase cap below what the graph
+    needs gives LC_ERR_NO_CONVERGENCE, and a partition pass whose tile 0 never
+    publishes makes the look-back waits behind it run out (short limit) and
+    gives LC_ERR_TIMEOUT.  After each, the same context gives the oracle's
+    result again."""
+    n = 20000
+    perm = np.random.default_rng(3).permutation(n).astype(np.uint32)
+    s = np.arange(n - 1)
+    ps, pd = perm[s], perm[s + 1]
+    ref = oracle.lc_run(n, ps, pd, 5)
+    assert ref.rounds > 2
+    ts, td = dev(ps, cuda), dev(pd, cuda)
+    ctx = lc.LocalContraction(n, ts, td, seed=5)
+    ctx.set_param("max_rounds", 2)
+    with pytest.raises(lc.LCError) as ei:
+        ctx.run()
+    assert ei.value.code == lc.LC_ERR_NO_CONVERGENCE
+    ctx.set_param("max_rounds", 0)
+    labels, res = ctx.run()
+    assert res.rounds == ref.rounds
+    assert np.array_equal(labels.cpu().numpy().view(np.uint32), ref.labels)
+    ctx.close()
+
+    g = synth.workload("rmat14")  # 2^18 edges: phase 0 has a partition pass
+    ref = oracle.lc_run(g.n, g.src, g.dst, g.seed)
+    ctx = lc.LocalContraction(g.n, dev(g.src, cuda), dev(g.dst, cuda), seed=g.seed)
+    ctx.set_param("spin_limit", 1 << 12)
+    ctx.set_param("inject_lookback_stall", 1)
+    with pytest.raises(lc.LCError) as ei:
+        ctx.run()
+    assert ei.value.code == lc.LC_ERR_TIMEOUT
+    labels, res = ctx.run()  # the stall was one shot
+    assert res.rounds == ref.rounds and list(zip(res.n_i, res.m_i)) == ref.sizes()
+    assert np.array_equal(labels.cpu().numpy().view(np.uint32), ref.labels)
+    ctx.close()
