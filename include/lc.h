@@ -7,9 +7,9 @@
  * its closed neighbourhood N(v) (Section 2 defines N(v) to contain v), merges
  * the arborescences of that parent map, found by pointer jumping (Theorem
  * thm:tree-rounds), relabels, deduplicates and compacts the edges (the O(1)-round
- * contraction lemma; isolated nodes dropped as in Section 7), and repeats until
+ * contraction lemma; isolated nodes dropped as in Section 6, Empirical study), and repeats until
  * no edges remain (Section 3).  The per-phase maps are composed back down to the
- * input vertices (Section 7) and every vertex is labelled with the smallest
+ * input vertices (Section 6, Empirical study) and every vertex is labelled with the smallest
  * input id of its connected component.
  *
  * Conventions shared by every entry point:
@@ -46,8 +46,9 @@ typedef enum {
   LC_ERR_CUDA = 3,           /* a CUDA runtime call failed */
   LC_ERR_NO_CONVERGENCE = 4, /* more phases than the round cap (64 + 4*ceil(log2 n)) */
   LC_ERR_TIMEOUT = 5,        /* a bounded device-side wait gave up */
-  LC_ERR_INTERNAL = 6        /* an internal index check failed (corrupted state; the
+  LC_ERR_INTERNAL = 6,       /* an internal index check failed (corrupted state; the
                                 offending access was skipped and reported on stderr) */
+  LC_ERR_CANCELLED = 7       /* a server job was cancelled (lc_server_cancel) */
 } lc_status;
 
 typedef enum {
@@ -80,7 +81,7 @@ lc_status lc_create(uint32_t n, const uint32_t* d_src, const uint32_t* d_dst, ui
 /* Select the phase variant (default LC_VARIANT_FOREST) and the small-graph
  * finish: once 0 < m_i <= finish_edges, that phase merges each connected
  * component of G_i into one node (the paper's single-machine union-find finish,
- * Section 7).  finish_edges = 0 (default) disables it.  Both change the phase
+ * Section 6, Empirical study).  finish_edges = 0 (default) disables it.  Both change the phase
  * count and per-phase sizes, never the labels.
  *   LC_VARIANT_TWO_HOP  nodes are the classes of equal label l(v) = the
  *            min-key vertex of N(N(v)), each named by its label vertex (which
@@ -161,9 +162,44 @@ lc_status lc_set_dedup(lc_ctx* ctx, lc_dedup mode);
  *   "inject_lookback_stall"  1: in the next partition pass, tile 0 publishes
  *                   nothing, so the waits behind it run out (a test of the
  *                   timeout path that faults nothing; one shot).
- * Phases with at least 2^22 edges also size their deduplication buckets from
- * a HyperLogLog estimate (Flajolet et al. 2007) of the distinct relabelled
- * keys, read back after the relabel step; the others from m_i.
+ *   "bucket_blocks" phase-0 edge grouping: 0 (default) = automatic (graphs of
+ *                   at least "bucket_min_vertices" vertices, default 2^23),
+ *                   1 = off, 2..32 = forced with that many vertex blocks.
+ *                   The n ids are cut into near-equal blocks and the input
+ *                   edges are copied, grouped by (lower block, higher block),
+ *                   into a context buffer before phase 0's minimum and
+ *                   relabel, so that both gather from two blocks of the
+ *                   per-vertex arrays at a time, a slice that stays in L2.
+ *   "bucket_window_bytes"  automatic block count: the smallest (>= 2) for
+ *                   which two blocks of 8-byte minima fit this many bytes
+ *                   (>= 1 MiB, default 64 MiB).
+ *   "bucket_min_vertices"  see "bucket_blocks".
+ *   "late_min_edges"  phases with at least this many edges (>= 1024, default
+ *                   2^22) plan their deduplication after the relabel, below;
+ *                   lowering it below the context's edge count allocates the
+ *                   buffers those phases use.  Not while a run is in flight.
+ *   "seg_dedup"     1 (default) / 0: whether those phases deduplicate by
+ *                   segments (below) or by the bucket partition.
+ *   "table_slots"   cap (a power of two >= 2^14, or 0 = none) on the table slots
+ *                   the segmented deduplication uses; when the slices do not
+ *                   fit at once they are processed in groups, and when one
+ *                   slice does not fit the phase uses the bucket partition
+ *                   (a test hook; default 0).
+ *   "target_permille"  scale (1..10^6, default 1000) applied to the estimated
+ *                   distinct-key count before sizing the tables or buckets
+ *                   (a test hook: small values undersize them, which the
+ *                   full-sort fallback then repairs).
+ * Phases with at least "late_min_edges" edges size their deduplication from a
+ * HyperLogLog estimate (Flajolet et al. 2007) of the distinct relabelled keys,
+ * read back after a filter pass that drops keys found in the device-wide
+ * cache; the others plan from m_i.  With "seg_dedup" those phases split the
+ * keys into 256 segments by their top bits (the filter writes each kept key
+ * into its segment's region) and keep the distinct keys of each segment with
+ * an open-addressing table slice of about twice its estimated distinct keys
+ * (a table of up to 2^28 slots, 8 bytes each, allocated with the other
+ * buffers of these phases); segments are taken in order, so the slices in use
+ * stay in L2.  A slice or bucket that overflows sends that phase to the full
+ * sort (lc_dedup_fallbacks counts such phases).
  * Unknown names or out-of-range values give LC_ERR_INVALID. */
 lc_status lc_set_param(lc_ctx* ctx, const char* name, uint64_t value);
 
@@ -235,6 +271,12 @@ lc_status lc_last_stats(const lc_ctx* ctx, uint32_t* rounds, uint64_t* mp_i, uin
 lc_status lc_last_dedup(const lc_ctx* ctx, uint32_t* rounds, uint64_t* kept_i, uint32_t* passes_i,
                         uint32_t cap);
 
+/* Phases of all runs of the context so far whose hashed deduplication
+ * overflowed a table slice or bucket set and was redone by the full sort (no
+ * counterpart in the paper; the result is the same either way).  *count
+ * receives the number. */
+lc_status lc_dedup_fallbacks(const lc_ctx* ctx, uint64_t* count);
+
 /* Per-kernel instrumentation (no counterpart in the paper; used to measure
  * the kernels against the HBM roofline).  Launch counts of every kernel are
  * always kept.  lc_profile(ctx, 1) additionally records a CUDA event pair
@@ -273,15 +315,30 @@ lc_status lc_destroy(lc_ctx* ctx);
  *     passed, if timeout_s > 0: LC_ERR_TIMEOUT, the job stays pending);
  *     returns its status, its phase count and its latency (submission to
  *     labels on the host) in seconds; then forgets the job.
+ *   lc_server_result: lc_server_wait that also fills host uint64[cap] n_i,
+ *     m_i (either may be NULL) with the job's per-phase sizes, as lc_run does
+ *     (LC_ERR_INVALID after filling cap of them if the job ran more phases).
+ *   lc_server_cancel: a queued job is dropped at once; a running one stops
+ *     at its next phase boundary, once the work it has on the device
+ *     completes (its context is kept for later jobs).  Waiting on it then
+ *     returns LC_ERR_CANCELLED.  LC_ERR_INVALID for an unknown job or one
+ *     whose labels are already being copied out (it completes normally).
  *   lc_server_stats: jobs completed, the most jobs that ran at once, device
  *     bytes held.
- *   lc_server_destroy: finishes submitted jobs, then frees everything. */
+ *   lc_server_destroy: finishes submitted jobs, then frees everything.
+ * The contexts of a server take their device memory from a memory pool of the
+ * server, stream-ordered on their slot's stream, and their pinned host
+ * counters from blocks the server keeps, so that creating and releasing
+ * contexts never waits on the device while other jobs run. */
 typedef struct lc_server lc_server;
 lc_status lc_server_create(uint64_t budget_bytes, uint32_t slots, lc_server** out);
 lc_status lc_server_submit(lc_server* s, uint32_t n, const uint32_t* h_src, const uint32_t* h_dst,
                            uint64_t m, uint64_t seed, uint32_t* h_labels, uint64_t* job);
 lc_status lc_server_wait(lc_server* s, uint64_t job, double timeout_s, uint32_t* rounds,
                          double* latency_s);
+lc_status lc_server_result(lc_server* s, uint64_t job, double timeout_s, uint32_t* rounds,
+                           double* latency_s, uint64_t* n_i, uint64_t* m_i, uint32_t cap);
+lc_status lc_server_cancel(lc_server* s, uint64_t job);
 lc_status lc_server_stats(lc_server* s, uint64_t* completed, uint64_t* peak_active,
                           uint64_t* bytes_in_use);
 lc_status lc_server_destroy(lc_server* s);
@@ -306,6 +363,9 @@ lc_status lc_server_destroy(lc_server* s);
  *   - The first call on a device looks up the array's device address with that
  *     device current (once per device); make that first call before any
  *     stream capture.
+ *   - Like lc_run, the call blocks the host until the labels are on the
+ *     device: it waits for the stream once per phase and copies the phase
+ *     counters into host memory.
  *   - Every call on a device shares the array, which keeps the last call's
  *     contents (each call clears what it needs zeroed).  Calls whose GPU work
  *     overlaps (other streams, other host threads) race on it and give
@@ -318,6 +378,14 @@ lc_status lc_server_destroy(lc_server* s);
 lc_status lc_run_static(uint32_t n, const uint32_t* d_src, const uint32_t* d_dst, uint64_t m,
                         uint64_t seed, void* stream, uint32_t* d_labels, uint32_t* rounds,
                         uint64_t* n_i, uint64_t* m_i, uint32_t cap);
+
+/* Test hook for the allocation-failure paths (no counterpart in the paper):
+ * the k-th device or pinned-host allocation the library makes after this
+ * call fails as if memory were exhausted (one shot; k = 0 turns the hook
+ * off).  The pieces lc_run_static carves out of its static array count as
+ * allocations here (it still calls no allocator).  The call that made it returns LC_ERR_OOM and releases what it had
+ * allocated; the library stays usable.  Process-wide. */
+lc_status lc_fail_alloc(uint64_t k);
 
 /* Static text for a status code. */
 const char* lc_status_str(lc_status s);

@@ -28,14 +28,14 @@
 //    A vertex with no neighbour other than itself is its own node.
 //  * contraction: edges are relabelled through the node map, self-loops
 //    dropped, duplicates removed (proof of the O(1)-round contraction lemma);
-//    nodes left without an edge are isolated and dropped (Section 7); surviving
+//    nodes left without an edge are isolated and dropped (Section 6, Empirical study); surviving
 //    nodes get new dense ids in ascending order of their name.
 //  * the loop runs while edges remain (Section 3); R = number of phases run.
 //  * final label of v = the smallest original id in v's component, found by
-//    composing the per-phase maps c_i (Section 7).
+//    composing the per-phase maps c_i (Section 6, Empirical study).
 //  * optional finish (off by default): once 0 < m_i <= finish_edges, the phase
 //    merges each connected component of G_i into one node by union-find, as the
-//    paper's small-graph optimisation does on one machine (Section 7); that
+//    paper's small-graph optimisation does on one machine (Section 6, Empirical study); that
 //    phase is counted as a phase.
 //  * optional MergeToLarge step (off by default; Section 5, the step used by
 //    the O(log log n) analysis on random graphs): with parameter alpha_i for

@@ -2,6 +2,7 @@
 // phase loop of LocalContraction (arXiv 1807.10727, Section 3), one CUDA
 // stream, one device synchronisation per phase to read the phase's sizes.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <chrono>
@@ -28,7 +29,7 @@ const char* kernel_name(int id) {
       "unique_rename", "propagate",  "bucket_bounds",   "bucket_dedup",  "rename",
       "unmix",         "batch",      "two_hop",         "open_min",      "tree_names",
       "union_find",    "m2l_group",  "m2l_select",      "m2l_hop",       "m2l_target",
-      "identity",      "rank_probe", "filter_hll"};
+      "identity",      "rank_probe", "filter_hll",   "bucket_edges",  "seg_dedup"};
   static_assert(sizeof(names) / sizeof(names[0]) == kNumKernels, "one name per kernel");
   return (id >= 0 && id < kNumKernels) ? names[id] : "unknown";
 }
@@ -81,6 +82,53 @@ struct Level {
   uint32_t* scan;
 };
 
+// Test hook: the allocation with this number (counted from the last
+// lc_fail_alloc call) fails; 0 = off.
+std::atomic<uint64_t> g_fail_at{0};
+std::atomic<uint64_t> g_alloc_no{0};
+
+bool injected_failure() {
+  if (g_fail_at.load() == 0) return false;
+  const uint64_t no = g_alloc_no.fetch_add(1) + 1;
+  uint64_t at = no;
+  return g_fail_at.compare_exchange_strong(at, 0);  // one shot
+}
+
+// Where a context's device memory comes from: cudaMalloc, or (contexts of a
+// server) stream-ordered allocation from the server's memory pool, which
+// neither allocation nor release synchronises with the device.
+struct MemSource {
+  cudaMemPool_t pool = nullptr;
+  cudaStream_t stream = nullptr;  // pool allocations and releases are ordered here
+};
+
+template <class T>
+cudaError_t dev_alloc(const MemSource& ms, T** p, size_t bytes) {
+  *p = nullptr;
+  if (injected_failure()) return cudaErrorMemoryAllocation;
+  void* q = nullptr;
+  const cudaError_t e = ms.pool ? cudaMallocFromPoolAsync(&q, bytes, ms.pool, ms.stream)
+                                : cudaMalloc(&q, bytes);
+  if (e == cudaSuccess) *p = static_cast<T*>(q);
+  return e;
+}
+
+void dev_free(const MemSource& ms, const void* p) {
+  if (p == nullptr) return;
+  if (ms.pool) cudaFreeAsync(const_cast<void*>(p), ms.stream);
+  else cudaFree(const_cast<void*>(p));
+}
+
+template <class T>
+cudaError_t host_alloc(T** p, size_t bytes) {
+  *p = nullptr;
+  if (injected_failure()) return cudaErrorMemoryAllocation;
+  void* q = nullptr;
+  const cudaError_t e = cudaMallocHost(&q, bytes);
+  if (e == cudaSuccess) *p = static_cast<T*>(q);
+  return e;
+}
+
 // Bump arena for the per-phase arrays; grows by whole chunks when a run needs
 // more than the first chunk (only when the phases shrink slowly).
 struct Arena {
@@ -88,9 +136,10 @@ struct Arena {
   size_t cur = 0;
   uint64_t used = 0;
   bool fixed = false;  // never grow: running out is an allocation failure
+  const MemSource* ms = nullptr;
   cudaError_t init(uint64_t words) {
     uint32_t* p = nullptr;
-    cudaError_t e = cudaMalloc(&p, std::max<uint64_t>(words, 1024) * 4);
+    cudaError_t e = dev_alloc(*ms, &p, std::max<uint64_t>(words, 1024) * 4);
     if (e != cudaSuccess) return e;
     chunks.push_back({p, std::max<uint64_t>(words, 1024)});
     return cudaSuccess;
@@ -98,6 +147,10 @@ struct Arena {
   void reset() { cur = 0; used = 0; }
   uint32_t* alloc(uint64_t words, cudaError_t* err) {
     words = (words + 63) & ~63ull;  // 256-byte aligned pieces
+    if (fixed && injected_failure()) {  // a fixed arena's pieces count for the test hook
+      *err = cudaErrorMemoryAllocation;
+      return nullptr;
+    }
     while (cur < chunks.size()) {
       if (used + words <= chunks[cur].second) {
         uint32_t* p = chunks[cur].first + used;
@@ -113,7 +166,7 @@ struct Arena {
     }
     uint64_t sz = std::max<uint64_t>(words, chunks.empty() ? words : chunks.back().second);
     uint32_t* p = nullptr;
-    *err = cudaMalloc(&p, sz * 4);
+    *err = dev_alloc(*ms, &p, sz * 4);
     if (*err != cudaSuccess) return nullptr;
     chunks.push_back({p, sz});
     cur = chunks.size() - 1;
@@ -121,7 +174,7 @@ struct Arena {
     return p;
   }
   void release() {
-    for (auto& c : chunks) cudaFree(c.first);
+    for (auto& c : chunks) dev_free(*ms, c.first);
     chunks.clear();
   }
 };
@@ -166,6 +219,7 @@ struct RunState {
   bool merge_step = false;  // the level in flight is phase i's MergeToLarge step
   uint32_t passes = 0;      // partition passes planned for the level in flight
   bool filtered = false;    // the level's keys went through the filter pass
+  bool seg = false;         // the kept keys lie in segment regions (segmented dedup)
   uint32_t* d_labels = nullptr;
   uint32_t i = 0, ni = 0;
   uint64_t mi = 0;
@@ -199,6 +253,8 @@ struct lc_ctx {
   uint64_t seed = 0;
   cudaStream_t stream = nullptr;
   int device = 0;
+  MemSource mem;                // device memory source (stream follows `stream`)
+  unsigned char* pinned = nullptr;  // borrowed pinned block for h_ctr / h_hll (servers)
   Launch L{};
   Prof prof;
   lc_variant variant = LC_VARIANT_FOREST;
@@ -231,6 +287,16 @@ struct lc_ctx {
   bool dedup_sort = false;     // deduplicate by a full radix sort every phase
   uint64_t window_bytes = 192ull << 20;  // L2 budget of one phase-0 minimum pass
   uint64_t relabel_window_bytes = 160ull << 20;  // root-array size above which relabel splits
+  uint32_t* bucket_scratch = nullptr;            // counts and fill counters of the edge buckets
+  uint32_t bucket_blocks = 0;                    // phase-0 edge buckets: 0 auto, 1 off, else blocks
+  uint64_t bucket_window_bytes = 64ull << 20;    // auto: two blocks of minima fit in this
+  uint32_t bucket_min_vertices = 1u << 23;       // auto: bucket only graphs of this many vertices
+  uint64_t* dtable = nullptr;                    // slices of the segmented deduplication
+  uint64_t dtable_slots = 0;
+  uint64_t table_cap = 0;                        // slots the segmented dedup may use (0: all)
+  bool seg_dedup = true;                         // large phases deduplicate by table slices
+  uint32_t target_permille = 1000;               // scale of the distinct-key estimate (tests)
+  uint64_t late_min_edges = 1ull << 22;          // phases this large plan their dedup late
 
   uint32_t max_rounds = 0;  // phase cap (0: 64 + 4 log2 n)
   uint32_t last_rounds = 0;
@@ -261,70 +327,110 @@ static lc_status status_of(cudaError_t e) {
 
 static void free_ctx(lc_ctx* c) {
   if (!c) return;
-  cudaFree(c->own_src);
-  cudaFree(c->own_dst);
-  cudaFree(c->own_labels);
-  cudaFree(c->minkey);
-  cudaFree(c->minkey2);
-  cudaFree(c->gcache);
-  cudaFree(c->d_hll);
-  if (c->h_hll) cudaFreeHost(c->h_hll);
-  cudaFree(c->flags);
-  cudaFree(c->ebuf[0]);
-  cudaFree(c->ebuf[1]);
-  cudaFree(c->ctr);
-  if (c->h_ctr) cudaFreeHost(c->h_ctr);
+  dev_free(c->mem, c->own_src);
+  dev_free(c->mem, c->own_dst);
+  dev_free(c->mem, c->own_labels);
+  dev_free(c->mem, c->minkey);
+  dev_free(c->mem, c->minkey2);
+  dev_free(c->mem, c->gcache);
+  dev_free(c->mem, c->d_hll);
+  if (c->h_hll && !c->pinned) cudaFreeHost(c->h_hll);
+  dev_free(c->mem, c->flags);
+  dev_free(c->mem, c->ebuf[0]);
+  dev_free(c->mem, c->ebuf[1]);
+  dev_free(c->mem, c->ctr);
+  if (c->h_ctr && !c->pinned) cudaFreeHost(c->h_ctr);
   if (c->ev) cudaEventDestroy(c->ev);
   if (c->batch) {
-    cudaFree(c->batch->d_seeds);
-    cudaFree(c->batch->d_voff0);
-    cudaFree(c->batch->d_eoff);
-    cudaFree(c->batch->d_rk);
+    dev_free(c->mem, c->batch->d_seeds);
+    dev_free(c->mem, c->batch->d_voff0);
+    dev_free(c->mem, c->batch->d_eoff);
+    dev_free(c->mem, c->batch->d_rk);
     delete c->batch;
   }
-  cudaFree(c->sort.status);
-  cudaFree(c->sort.hist);
-  cudaFree(c->sort.tickets);
-  cudaFree(c->bounds);
+  dev_free(c->mem, c->sort.status);
+  dev_free(c->mem, c->sort.hist);
+  dev_free(c->mem, c->sort.tickets);
+  dev_free(c->mem, c->bounds);
+  dev_free(c->mem, c->bucket_scratch);
+  dev_free(c->mem, c->dtable);
   c->arena.release();
   c->prof.release();
   delete c;
+}
+
+// Slots of the segmented-deduplication table for up to m keys: twice m,
+// rounded up to a power of two, at least kSegs * 64, at most 2^28 (2 GB).
+static uint64_t table_slots_for(uint64_t m) {
+  uint64_t t = (uint64_t)kSegs * 64;
+  while (t < 2 * m && t < (1ull << 28)) t <<= 1;
+  return t;
+}
+
+// Buffers of the phases that plan their deduplication after the relabel:
+// the device-wide duplicate cache, the HyperLogLog registers (and their
+// pinned host copy) and the segmented-deduplication table.
+static cudaError_t alloc_late(lc_ctx* c) {
+  cudaError_t e = cudaSuccess;
+  if (c->gcache == nullptr) {
+    c->gcache_slots = kGCacheSlots;
+    e = dev_alloc(c->mem, &c->gcache, 8ull * c->gcache_slots);
+    if (e != cudaSuccess) {
+      c->gcache_slots = 0;
+      return e;
+    }
+  }
+  if (c->d_hll == nullptr && (e = dev_alloc(c->mem, &c->d_hll, 4ull * kHllRegs)) != cudaSuccess) return e;
+  if (c->h_hll == nullptr) {
+    if (c->pinned) c->h_hll = reinterpret_cast<uint32_t*>(c->pinned + 256);
+    else if ((e = host_alloc(&c->h_hll, 4ull * kHllRegs)) != cudaSuccess) return e;
+  }
+  if (c->dtable == nullptr) {
+    const uint64_t slots = table_slots_for(c->m_cap);
+    if ((e = dev_alloc(c->mem, &c->dtable, 8ull * slots)) != cudaSuccess) return e;
+    c->dtable_slots = slots;
+  }
+  return cudaSuccess;
 }
 
 static lc_status alloc_ctx(lc_ctx* c) {
   const uint64_t n = c->n, m = c->m;
   c->n_cap = c->n;
   c->m_cap = c->m;
-  LC_TRY(cudaMalloc(&c->minkey, std::max<uint64_t>(n, 1) * 8));
-  LC_TRY(cudaMalloc(&c->flags, ((n + 15) & ~15ull) + 16));
-  LC_TRY(cudaMalloc(&c->ebuf[0], std::max<uint64_t>(m, 2) * 8));
-  LC_TRY(cudaMalloc(&c->ebuf[1], std::max<uint64_t>(m, 2) * 8));
-  LC_TRY(cudaMalloc(&c->ctr, sizeof(Counters)));
+  LC_TRY(dev_alloc(c->mem, &c->minkey, std::max<uint64_t>(n, 1) * 8));
+  LC_TRY(dev_alloc(c->mem, &c->flags, ((n + 15) & ~15ull) + 16));
+  LC_TRY(dev_alloc(c->mem, &c->ebuf[0], std::max<uint64_t>(m, 2) * 8));
+  LC_TRY(dev_alloc(c->mem, &c->ebuf[1], std::max<uint64_t>(m, 2) * 8));
+  LC_TRY(dev_alloc(c->mem, &c->ctr, sizeof(Counters)));
   // initialisation is ordered on the context's stream, and lc_create waits
   // for it, so the context may then be used from any stream
   LC_TRY(cudaMemsetAsync(c->ctr, 0, sizeof(Counters), c->stream));
-  LC_TRY(cudaMallocHost(&c->h_ctr, sizeof(Counters)));
+  if (c->pinned) c->h_ctr = reinterpret_cast<Counters*>(c->pinned);
+  else LC_TRY(host_alloc(&c->h_ctr, sizeof(Counters)));
   LC_TRY(cudaEventCreateWithFlags(&c->ev, cudaEventDisableTiming));
   c->sort.status_words = std::max(sort_status_words(m), sort_status_words(n));
-  LC_TRY(cudaMalloc(&c->sort.status, c->sort.status_words * 8));
+  LC_TRY(dev_alloc(c->mem, &c->sort.status, c->sort.status_words * 8));
   LC_TRY(cudaMemsetAsync(c->sort.status, 0, c->sort.status_words * 8, c->stream));
-  LC_TRY(cudaMalloc(&c->sort.hist, sizeof(uint32_t) * kMaxPasses * kRadixMax));
-  LC_TRY(cudaMalloc(&c->sort.tickets, sizeof(unsigned) * 16));
-  LC_TRY(cudaMalloc(&c->bounds, sizeof(uint32_t) * ((1ull << hash_bits_for(m)) + 1)));
-  if (m >= kGCacheMinEdges) {
-    c->gcache_slots = kGCacheSlots;
-    LC_TRY(cudaMalloc(&c->gcache, 8ull * c->gcache_slots));
-    LC_TRY(cudaMalloc(&c->d_hll, 4ull * kHllRegs));
-    LC_TRY(cudaMallocHost(&c->h_hll, 4ull * kHllRegs));
-  }
+  LC_TRY(dev_alloc(c->mem, &c->sort.hist, sizeof(uint32_t) * kMaxPasses * kRadixMax));
+  LC_TRY(dev_alloc(c->mem, &c->sort.tickets, sizeof(unsigned) * 16));
+  LC_TRY(dev_alloc(c->mem, &c->bounds, sizeof(uint32_t) * ((1ull << hash_bits_for(m)) + 1)));
+  LC_TRY(dev_alloc(c->mem, &c->bucket_scratch, sizeof(uint32_t) * kBucketScratchWords));
+  if (m >= kGCacheMinEdges) LC_TRY(alloc_late(c));
   // first arena chunk: 3 arrays per level for levels whose sizes sum to 2n,
   // plus the next level's min-original-id array
   LC_TRY(c->arena.init(4 * (2 * n + 256)));
   return LC_OK;
 }
 
-extern "C" lc_status lc_create(uint32_t n, const uint32_t* d_src, const uint32_t* d_dst,
-                               uint64_t m, uint64_t seed, void* stream, lc_ctx** out) {
+// lc_create with a choice of memory source: `pool` non-null allocates the
+// context's device memory stream-ordered from that pool on `stream`, and
+// `pinned` (kPinnedBlock bytes) holds its host counters instead of its own
+// pinned allocation (both for the contexts of a server).
+constexpr size_t kPinnedBlock = 256 + 4 * kHllRegs;
+
+static lc_status create_ctx(uint32_t n, const uint32_t* d_src, const uint32_t* d_dst, uint64_t m,
+                            uint64_t seed, cudaStream_t stream, cudaMemPool_t pool,
+                            unsigned char* pinned, lc_ctx** out) {
   if (out == nullptr) return LC_ERR_INVALID;
   *out = nullptr;
   if ((d_src == nullptr) != (d_dst == nullptr)) return LC_ERR_INVALID;
@@ -335,7 +441,10 @@ extern "C" lc_status lc_create(uint32_t n, const uint32_t* d_src, const uint32_t
   c->n = n;
   c->m = m;
   c->seed = seed;
-  c->stream = (cudaStream_t)stream;
+  c->stream = stream;
+  c->mem = MemSource{pool, stream};
+  c->pinned = pinned;
+  c->arena.ms = &c->mem;
   if (cudaGetDevice(&c->device) != cudaSuccess) {
     delete c;
     return LC_ERR_CUDA;
@@ -350,9 +459,9 @@ extern "C" lc_status lc_create(uint32_t n, const uint32_t* d_src, const uint32_t
   c->dst = d_dst;
   lc_status st = alloc_ctx(c);
   if (st == LC_OK && d_src == nullptr) {
-    cudaError_t e = cudaMalloc(&c->own_src, std::max<uint64_t>(m, 1) * 4);
-    if (e == cudaSuccess) e = cudaMalloc(&c->own_dst, std::max<uint64_t>(m, 1) * 4);
-    if (e == cudaSuccess) e = cudaMalloc(&c->own_labels, std::max<uint64_t>(n, 1) * 4);
+    cudaError_t e = dev_alloc(c->mem, &c->own_src, std::max<uint64_t>(m, 1) * 4);
+    if (e == cudaSuccess) e = dev_alloc(c->mem, &c->own_dst, std::max<uint64_t>(m, 1) * 4);
+    if (e == cudaSuccess) e = dev_alloc(c->mem, &c->own_labels, std::max<uint64_t>(n, 1) * 4);
     st = status_of(e);
     c->src = c->own_src;
     c->dst = c->own_dst;
@@ -360,10 +469,22 @@ extern "C" lc_status lc_create(uint32_t n, const uint32_t* d_src, const uint32_t
   if (st == LC_OK) st = status_of(cudaStreamSynchronize(c->stream));
   if (st != LC_OK) {
     free_ctx(c);
+    if (pool) cudaStreamSynchronize(stream);  // the releases are ordered there
     cudaGetLastError();
     return st;
   }
   *out = c;
+  return LC_OK;
+}
+
+extern "C" lc_status lc_create(uint32_t n, const uint32_t* d_src, const uint32_t* d_dst,
+                               uint64_t m, uint64_t seed, void* stream, lc_ctx** out) {
+  return create_ctx(n, d_src, d_dst, m, seed, (cudaStream_t)stream, nullptr, nullptr, out);
+}
+
+extern "C" lc_status lc_fail_alloc(uint64_t k) {
+  g_alloc_no.store(0);
+  g_fail_at.store(k);
   return LC_OK;
 }
 
@@ -375,7 +496,7 @@ extern "C" lc_status lc_configure(lc_ctx* c, lc_variant variant, uint64_t finish
   if (finish_edges != 0 && c->batch != nullptr) return LC_ERR_INVALID;
   if (c->rs.state != RunState::kDone) return LC_ERR_INVALID;
   if (variant == LC_VARIANT_TWO_HOP && c->minkey2 == nullptr)
-    LC_TRY(cudaMalloc(&c->minkey2, std::max<uint64_t>(c->n_cap, 1) * 8));
+    LC_TRY(dev_alloc(c->mem, &c->minkey2, std::max<uint64_t>(c->n_cap, 1) * 8));
   c->variant = variant;
   c->finish_edges = finish_edges;
   return LC_OK;
@@ -419,6 +540,15 @@ static lc_status fail(lc_ctx* c, lc_status st) {
   return st;
 }
 
+// Vertex blocks of the phase-0 edge buckets for a graph of n vertices (1: the
+// input edges are read as given).
+static uint32_t bucket_blocks(const lc_ctx* c, uint32_t n) {
+  if (c->bucket_scratch == nullptr || c->bucket_blocks == 1) return 1;
+  if (c->bucket_blocks > 1) return std::min(c->bucket_blocks, std::max(n, 2u));
+  if (n < c->bucket_min_vertices) return 1;
+  return bucket_blocks_for(n, c->bucket_window_bytes);
+}
+
 // Enqueue phase rs.i on (rs.ni, rs.mi): steps (a)-(d) and the copy of the
 // phase counters to the host.
 static lc_status enqueue_phase(lc_ctx* c) {
@@ -457,6 +587,18 @@ static lc_status enqueue_phase(lc_ctx* c) {
   const bool first = i == 0 && !r.merge_step;
   const uint32_t* src0 = first ? c->src : nullptr;
   const uint32_t* dst0 = first ? c->dst : nullptr;
+  // current edges in packed form (phases >= 1, or phase 0's bucketed input)
+  const uint64_t* pk = r.packed;
+  const uint32_t nb = first ? bucket_blocks(c, ni) : 1u;
+  if (nb > 1 && mi > 0) {
+    // phase 0: group the input edges by vertex-block pair, so that the steps
+    // below gather from an L2-sized slice of the per-vertex arrays at a time;
+    // the grouped copy goes to the buffer the relabel does not write
+    uint64_t* grouped = c->ebuf[1];
+    bucket_edges(src0, dst0, mi, ni, nb, grouped, c->bucket_scratch, err, L);
+    src0 = dst0 = nullptr;
+    pk = grouped;
+  }
   if (r.merge_step) {
     // MergeToLarge on the graph that phase i just produced
     const Level& prev = c->levels.back();
@@ -489,25 +631,25 @@ static lc_status enqueue_phase(lc_ctx* c) {
     // names computed above
   } else if (c->finish_edges != 0 && mi <= c->finish_edges) {
     // small-graph finish: one node per connected component of G_i
-    union_find_names(src0, dst0, r.packed, mi, ni, reinterpret_cast<uint32_t*>(c->minkey),
+    union_find_names(src0, dst0, pk, mi, ni, reinterpret_cast<uint32_t*>(c->minkey),
                      r.lv.root, r.lv.mo, err, L);
   } else if (c->variant == LC_VARIANT_TREE) {
     // (b) + (c): open-neighbourhood parent, names from the terminal 2-cycles
     if (cudaMemsetAsync(c->minkey, 0xFF, sizeof(unsigned long long) * ni, c->stream) !=
         cudaSuccess)
       return fail(c, LC_ERR_CUDA);
-    edge_min(src0, dst0, r.packed, mi, ni, rk, c->minkey, err, c->window_bytes, bp, L, true);
+    edge_min(src0, dst0, pk, mi, ni, rk, c->minkey, err, c->window_bytes, bp, L, true);
     tree_names(c->minkey, r.lv.root, r.lv.mo, ni, rk, bp, err, L);
   } else {
     // (b): closed-neighbourhood minimum
-    edge_min(src0, dst0, r.packed, mi, ni, rk, c->minkey, err, c->window_bytes, bp, L);
+    edge_min(src0, dst0, pk, mi, ni, rk, c->minkey, err, c->window_bytes, bp, L);
     if (c->variant == LC_VARIANT_TWO_HOP) {
       // second hop; names are label vertices, node minima in their own array
       uint32_t* nmo = c->arena.alloc(ni, &aerr);
       if (aerr != cudaSuccess) return fail(c, status_of(aerr));
       uint32_t* fpar = c->arena.alloc(ni, &aerr);
       if (aerr != cudaSuccess) return fail(c, status_of(aerr));
-      two_hop_names(src0, dst0, r.packed, mi, ni, rk, bp, c->minkey, c->minkey2, fpar, r.lv.root,
+      two_hop_names(src0, dst0, pk, mi, ni, rk, bp, c->minkey, c->minkey2, fpar, r.lv.root,
                     r.lv.mo, nmo, err, L);
       r.lv.mo = nmo;
     } else {
@@ -522,13 +664,26 @@ static lc_status enqueue_phase(lc_ctx* c) {
   r.keys = (r.packed == c->ebuf[0]) ? c->ebuf[1] : c->ebuf[0];
   r.alt = (r.keys == c->ebuf[0]) ? c->ebuf[1] : c->ebuf[0];
   r.filtered = false;
-  const bool big = mi >= kGCacheMinEdges;
-  // large phases plan their buckets after the relabel, from the estimated
-  // number of distinct keys; the others from m_i, with the histogram fused
+  r.seg = false;
+  const bool big = mi >= c->late_min_edges;
+  // large phases plan their deduplication after the relabel, from the
+  // estimated number of distinct keys; the others from m_i, with the
+  // partition histogram fused into the relabel
   const bool late = !c->dedup_sort && big && c->d_hll != nullptr;
+  // large phases with a table deduplicate by segments: the relabel counts
+  // its keys per segment (the top kSegBits bits of the mixed key)
+  const bool seg = late && c->seg_dedup && c->dtable != nullptr;
   PassPlan hplan{};
   const int hb = late ? 0 : hash_plan(mi, &hplan);
   if (!c->dedup_sort && !late) hist_reset(c->sort, L);
+  PassPlan splan{};
+  if (seg) {
+    splan.passes = 1;
+    splan.shift[0] = 64 - kSegBits;
+    splan.bits[0] = kSegBits;
+    if (cudaMemsetAsync(c->bucket_scratch, 0, sizeof(uint32_t) * kSegs, c->stream) != cudaSuccess)
+      return fail(c, LC_ERR_CUDA);
+  }
   if (late && cudaMemsetAsync(c->d_hll, 0, 4ull * kHllRegs, c->stream) != cudaSuccess)
     return fail(c, LC_ERR_CUDA);
   // the device-wide duplicate cache: in the relabel itself with the full
@@ -538,9 +693,11 @@ static lc_status enqueue_phase(lc_ctx* c) {
       cudaMemsetAsync(c->gcache, 0xFF, 8ull * c->gcache_slots, c->stream) != cudaSuccess)
     return fail(c, LC_ERR_CUDA);
   const bool gcache_in_relabel = use_gcache && !late;
-  relabel(src0, dst0, r.packed, mi, ni, r.lv.root,
+  relabel(src0, dst0, pk, mi, ni, r.lv.root,
           r.bits, r.keys, &c->ctr->mprime, &c->ctr->emitted, !c->dedup_sort,
-          (c->dedup_sort || late) ? nullptr : &hplan, c->sort.hist, first ? r.alt : nullptr,
+          seg ? &splan : (c->dedup_sort || late) ? nullptr : &hplan,
+          seg ? c->bucket_scratch : c->sort.hist,
+          (first && pk == nullptr) ? r.alt : nullptr,
           c->relabel_window_bytes, gcache_in_relabel ? c->gcache : nullptr,
           gcache_in_relabel ? c->gcache_slots : 0, c->gcache_admit, err, L);
   if (late) {
@@ -549,11 +706,20 @@ static lc_status enqueue_phase(lc_ctx* c) {
     if (cudaMemsetAsync(&c->ctr->filtered, 0, sizeof(unsigned long long), c->stream) !=
         cudaSuccess)
       return fail(c, LC_ERR_CUDA);
-    filter_hll(r.keys, &c->ctr->emitted, mi, r.alt, &c->ctr->filtered,
-               use_gcache ? c->gcache : nullptr, use_gcache ? c->gcache_slots : 0,
-               c->gcache_admit, c->d_hll, L);
+    if (seg) {
+      // kept keys go straight to their segment's region
+      seg_begin(c->bucket_scratch, L);
+      filter_seg(r.keys, &c->ctr->emitted, mi, r.alt, &c->ctr->filtered,
+                 use_gcache ? c->gcache : nullptr, use_gcache ? c->gcache_slots : 0,
+                 c->gcache_admit, c->d_hll, c->bucket_scratch, err, L);
+    } else {
+      filter_hll(r.keys, &c->ctr->emitted, mi, r.alt, &c->ctr->filtered,
+                 use_gcache ? c->gcache : nullptr, use_gcache ? c->gcache_slots : 0,
+                 c->gcache_admit, c->d_hll, L);
+    }
     std::swap(r.keys, r.alt);
     r.filtered = true;
+    r.seg = seg;
     stamp_counters(c->ctr, ++c->tag, L);
     if (cudaMemcpyAsync(c->h_ctr, c->ctr, sizeof(Counters), cudaMemcpyDeviceToHost, c->stream) !=
             cudaSuccess ||
@@ -580,6 +746,38 @@ static double hll_estimate(const uint32_t* reg) {
   double e = (0.7213 / (1.0 + 1.079 / m)) * m * m / sum;
   if (e <= 2.5 * m && zeros > 0) e = m * std::log(m / zeros);
   return e;
+}
+
+// Steps (d2) and (d3) of a segmented phase: the kept keys of segment s lie in
+// its region of rs.keys; table slices of `slots` entries keep the distinct
+// ones (into rs.alt).  Returns false, with the keys made contiguous again
+// (rs.seg cleared), when the table cannot hold the slices.
+static bool enqueue_seg_dedup(lc_ctx* c, uint64_t slots) {
+  RunState& r = c->rs;
+  const Launch& L = c->L;
+  unsigned* err = &c->ctr->err;
+  const uint64_t usable =
+      c->table_cap ? std::min(c->table_cap, c->dtable_slots) : c->dtable_slots;
+  if (!seg_dedup(r.keys, c->bucket_scratch, r.mi, c->dtable, usable, slots, r.alt,
+                 &c->ctr->m_next, c->flags, r.ni, r.bits, c->sort.tickets + 11, err, L)) {
+    seg_compact(r.keys, c->bucket_scratch, r.alt, L);
+    std::swap(r.keys, r.alt);
+    r.seg = false;
+    return false;
+  }
+  r.passes = 0;
+  r.part = r.keys;
+  r.next = r.alt;
+  scan_flags(c->flags, r.lv.scan, r.ni, r.lv.mo, r.mo_next, &c->ctr->n_next, c->sort, err, L);
+  rename_edges(r.next, &c->ctr->m_next, r.mi, r.bits, r.lv.scan, r.ni, err, L);
+  r.state = RunState::kPhase;
+  stamp_counters(c->ctr, ++c->tag, L);
+  if (cudaMemcpyAsync(c->h_ctr, c->ctr, sizeof(Counters), cudaMemcpyDeviceToHost, c->stream) !=
+      cudaSuccess)
+    fail(c, LC_ERR_CUDA);
+  else if (record(c) != LC_OK)
+    fail(c, LC_ERR_CUDA);
+  return true;
 }
 
 // Steps (d2) and (d3) of phase rs.i on the relabelled keys in rs.keys, then
@@ -744,7 +942,17 @@ static lc_status run_complete(lc_ctx* c) {
     if (h.emitted > r.mi || h.mprime > r.mi || (r.filtered && h.filtered > h.emitted))
       return report_internal(c, "inconsistent relabel counters");
     const uint64_t kept = r.filtered ? h.filtered : h.emitted;
-    const double est = hll_estimate(c->h_hll) * 1.05 / 1.5 + 1.0;
+    const double distinct = hll_estimate(c->h_hll) * (c->target_permille / 1000.0);
+    if (r.seg) {
+      // slices of at least 2.1 slots per estimated distinct key of a segment
+      // (the estimate's standard error is 2.3%), a power of two each
+      const double want = 2.1 * std::min(distinct, (double)kept) / kSegs;
+      uint64_t slots = 64;
+      while ((double)slots < want && slots < (1ull << 40)) slots <<= 1;
+      if (enqueue_seg_dedup(c, slots)) return c->rs.state == RunState::kDone ? c->rs.st : LC_OK;
+      // no room for the slices: the keys are contiguous again, partition them
+    }
+    const double est = distinct * 1.05 / 1.5 + 1.0;
     const uint64_t target = std::min<uint64_t>(std::max<uint64_t>(kept, 1),
                                                (uint64_t)std::min(est, (double)r.mi));
     PassPlan hplan{};
@@ -755,6 +963,12 @@ static lc_status run_complete(lc_ctx* c) {
     // a bucket held more distinct keys than its shared-memory set: redo this
     // phase's deduplication by a full sort of the intact keys
     ++c->fallbacks;
+    if (r.seg) {
+      // the kept keys lie in segment regions: make them contiguous first
+      seg_compact(r.part, c->bucket_scratch, r.next, c->L);
+      std::swap(r.part, r.next);
+      r.seg = false;
+    }
     unmix_keys(r.part, kept_count(c), r.mi, c->L);
     if (cudaMemsetAsync(&c->ctr->m_next, 0, 2 * sizeof(unsigned long long), c->stream) !=
             cudaSuccess ||
@@ -882,10 +1096,10 @@ extern "C" lc_status lc_batch_create(uint32_t k, const uint32_t* h_n, const uint
   b->user_dst = d_dst;
   b->h_eoff.assign(h_eoff, h_eoff + k + 1);
   b->h_voff0 = voff;
-  cudaError_t e = cudaMalloc(&b->d_seeds, 8ull * k);
-  if (e == cudaSuccess) e = cudaMalloc(&b->d_voff0, 4ull * (k + 1));
-  if (e == cudaSuccess) e = cudaMalloc(&b->d_eoff, 8ull * (k + 1));
-  if (e == cudaSuccess) e = cudaMalloc(&b->d_rk, 8ull * k);
+  cudaError_t e = dev_alloc(c->mem, &b->d_seeds, 8ull * k);
+  if (e == cudaSuccess) e = dev_alloc(c->mem, &b->d_voff0, 4ull * (k + 1));
+  if (e == cudaSuccess) e = dev_alloc(c->mem, &b->d_eoff, 8ull * (k + 1));
+  if (e == cudaSuccess) e = dev_alloc(c->mem, &b->d_rk, 8ull * k);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(b->d_seeds, h_seeds, 8ull * k, cudaMemcpyHostToDevice, c->stream);
   if (e == cudaSuccess)
@@ -967,6 +1181,12 @@ extern "C" lc_status lc_last_dedup(const lc_ctx* c, uint32_t* rounds, uint64_t* 
   return c->last_passes.size() > cap ? LC_ERR_INVALID : LC_OK;
 }
 
+extern "C" lc_status lc_dedup_fallbacks(const lc_ctx* c, uint64_t* count) {
+  if (!c || !count) return LC_ERR_INVALID;
+  *count = c->fallbacks;
+  return LC_OK;
+}
+
 extern "C" lc_status lc_set_dedup(lc_ctx* c, lc_dedup mode) {
   if (!c) return LC_ERR_INVALID;
   if (mode != LC_DEDUP_HASH && mode != LC_DEDUP_SORT) return LC_ERR_INVALID;
@@ -996,6 +1216,48 @@ extern "C" lc_status lc_set_param(lc_ctx* c, const char* name, uint64_t value) {
     c->sort.stall_once = (int)value;
     return LC_OK;
   }
+  if (std::strcmp(name, "seg_dedup") == 0) {
+    if (value > 1) return LC_ERR_INVALID;
+    c->seg_dedup = value != 0;
+    return LC_OK;
+  }
+  if (std::strcmp(name, "table_slots") == 0) {
+    if (value != 0 && (value < (uint64_t)kSegs * 64 || (value & (value - 1)) != 0))
+      return LC_ERR_INVALID;
+    c->table_cap = value;
+    return LC_OK;
+  }
+  if (std::strcmp(name, "target_permille") == 0) {
+    if (value == 0 || value > 1000000) return LC_ERR_INVALID;
+    c->target_permille = (uint32_t)value;
+    return LC_OK;
+  }
+  if (std::strcmp(name, "late_min_edges") == 0) {
+    if (value < 1024) return LC_ERR_INVALID;
+    if (c->rs.state != RunState::kDone) return LC_ERR_INVALID;
+    if (value < c->m_cap && (c->d_hll == nullptr || c->dtable == nullptr)) {
+      DeviceGuard g(c->device);
+      LC_TRY(cudaStreamSynchronize(c->stream));
+      LC_TRY(alloc_late(c));
+    }
+    c->late_min_edges = value;
+    return LC_OK;
+  }
+  if (std::strcmp(name, "bucket_blocks") == 0) {
+    if (value > kBucketMaxBlocks) return LC_ERR_INVALID;
+    c->bucket_blocks = (uint32_t)value;
+    return LC_OK;
+  }
+  if (std::strcmp(name, "bucket_window_bytes") == 0) {
+    if (value < (1u << 20)) return LC_ERR_INVALID;
+    c->bucket_window_bytes = value;
+    return LC_OK;
+  }
+  if (std::strcmp(name, "bucket_min_vertices") == 0) {
+    if (value > 0xFFFFFFFFull) return LC_ERR_INVALID;
+    c->bucket_min_vertices = (uint32_t)value;
+    return LC_OK;
+  }
   if (std::strcmp(name, "relabel_window_bytes") == 0) {
     c->relabel_window_bytes = value;
     return LC_OK;
@@ -1011,11 +1273,11 @@ extern "C" lc_status lc_set_param(lc_ctx* c, const char* name, uint64_t value) {
     if (c->rs.state != RunState::kDone) return LC_ERR_INVALID;
     DeviceGuard g(c->device);
     LC_TRY(cudaStreamSynchronize(c->stream));
-    cudaFree(c->gcache);
+    dev_free(c->mem, c->gcache);
     c->gcache = nullptr;
     c->gcache_slots = 0;
     if (value != 0) {
-      LC_TRY(cudaMalloc(&c->gcache, 8ull * value));
+      LC_TRY(dev_alloc(c->mem, &c->gcache, 8ull * value));
       c->gcache_slots = (uint32_t)value;
     }
     return LC_OK;
@@ -1059,6 +1321,7 @@ extern "C" const char* lc_status_str(lc_status s) {
     case LC_ERR_NO_CONVERGENCE: return "phase count exceeded the round cap";
     case LC_ERR_TIMEOUT: return "a bounded device wait gave up";
     case LC_ERR_INTERNAL: return "internal consistency check failed";
+    case LC_ERR_CANCELLED: return "the job was cancelled";
   }
   return "unknown status";
 }
@@ -1199,10 +1462,12 @@ uint64_t ctx_bytes(uint64_t n, uint64_t m) {
   const uint64_t status = std::max(sort_status_words(m), sort_status_words(n)) * 8;
   const uint64_t bounds = 4 * ((1ull << hash_bits_for(m)) + 1);
   const uint64_t arena = 4 * std::max<uint64_t>(4 * (2 * n + 256), 1024);
-  const uint64_t gcache = m >= kGCacheMinEdges ? 8ull * kGCacheSlots + 4ull * kHllRegs : 0;
+  const uint64_t gcache =
+      m >= kGCacheMinEdges ? 8ull * kGCacheSlots + 4ull * kHllRegs + 8 * table_slots_for(m) : 0;
   return gcache + 8 * std::max<uint64_t>(n, 1) + n + 32 + 16 * std::max<uint64_t>(m, 2) + status +
          bounds + arena + 8 * std::max<uint64_t>(m, 1) + 4 * std::max<uint64_t>(n, 1) +
-         sizeof(Counters) + 4096 + 16 * 4 + 4ull * kMaxPasses * kRadixMax + (1u << 16);
+         sizeof(Counters) + 4096 + 16 * 4 + 4ull * kMaxPasses * kRadixMax + (1u << 16) +
+         4 * kBucketScratchWords;
 }
 
 struct Job {
@@ -1213,7 +1478,9 @@ struct Job {
   uint32_t* h_labels = nullptr;
   enum { kQueued, kRunning, kCopying, kDone } state = kQueued;
   lc_status status = LC_OK;
+  bool cancel = false;  // stop at the next phase boundary
   uint32_t rounds = 0;
+  std::vector<uint64_t> hn, hm;  // per-phase sizes of a finished run
   lc_ctx* ctx = nullptr;
   int slot = -1;
   std::chrono::steady_clock::time_point t_submit, t_done;
@@ -1224,6 +1491,8 @@ struct Job {
 struct lc_server {
   std::vector<lc_ctx*> in_use_ctx;  // contexts held by running jobs (consistency check)
   int device = 0;
+  cudaMemPool_t mempool = nullptr;  // device memory of the server's contexts
+  std::vector<unsigned char*> pinned_chunks, pinned_free;  // host counter blocks
   uint64_t budget = 0, in_use = 0;
   std::vector<cudaStream_t> streams;
   std::vector<int> free_slots;
@@ -1245,9 +1514,33 @@ static void ctx_rebind(lc_ctx* c, uint32_t n, uint64_t m, uint64_t seed, cudaStr
   c->m = m;
   c->seed = seed;
   c->stream = stream;
+  c->mem.stream = stream;
   c->L.stream = stream;
   c->src = c->own_src;
   c->dst = c->own_dst;
+}
+
+// A pinned block for a new context's host counters (the server allocates
+// them 64 at a time and never returns them before it is destroyed).
+static unsigned char* take_pinned(lc_server* s) {
+  if (s->pinned_free.empty()) {
+    constexpr int kPer = 64;
+    unsigned char* chunk = nullptr;
+    if (host_alloc(&chunk, kPinnedBlock * kPer) != cudaSuccess) return nullptr;
+    s->pinned_chunks.push_back(chunk);
+    for (int q = kPer - 1; q >= 0; --q) s->pinned_free.push_back(chunk + kPinnedBlock * q);
+  }
+  unsigned char* b = s->pinned_free.back();
+  s->pinned_free.pop_back();
+  return b;
+}
+
+// Release an idle (or failed) context of the server: all its work has
+// completed, so its memory goes back to the pool stream-ordered, without
+// waiting on the device.
+static void server_release(lc_server* s, lc_ctx* c) {
+  if (c->pinned) s->pinned_free.push_back(c->pinned);
+  free_ctx(c);
 }
 
 static void finish_job(lc_server* s, Job* j, lc_status st) {
@@ -1259,11 +1552,13 @@ static void finish_job(lc_server* s, Job* j, lc_status st) {
     if (it != s->in_use_ctx.end()) s->in_use_ctx.erase(it);
     if (std::find(s->pool.begin(), s->pool.end(), j->ctx) != s->pool.end())
       std::fprintf(stderr, "liblc: server: context returned to the pool twice\n");
-    if (st == LC_OK || st == LC_ERR_INVALID || st == LC_ERR_NO_CONVERGENCE) {
+    if (st == LC_OK || st == LC_ERR_INVALID || st == LC_ERR_NO_CONVERGENCE ||
+        st == LC_ERR_CANCELLED) {
+      j->ctx->rs.state = RunState::kDone;
       s->pool.push_back(j->ctx);  // the context is intact: keep it for reuse
     } else {
       s->in_use -= ctx_bytes(j->ctx->n_cap, j->ctx->m_cap);
-      lc_destroy(j->ctx);
+      server_release(s, j->ctx);
     }
     j->ctx = nullptr;
   }
@@ -1299,11 +1594,18 @@ static bool admit(lc_server* s) {
           return ctx_bytes(a->n_cap, a->m_cap) < ctx_bytes(b->n_cap, b->m_cap);
         });
         s->in_use -= ctx_bytes((*it)->n_cap, (*it)->m_cap);
-        lc_destroy(*it);
+        server_release(s, *it);
         s->pool.erase(it);
       }
       if (s->in_use + need > s->budget) break;  // wait for running jobs to free memory
-      lc_status st = lc_create(j->n, nullptr, nullptr, j->m, j->seed, nullptr, &c);
+      // created on the slot's stream, from the server's pool: no device-wide
+      // synchronisation on the worker's path
+      unsigned char* pin = take_pinned(s);
+      lc_status st = pin == nullptr ? LC_ERR_OOM
+                                    : create_ctx(j->n, nullptr, nullptr, j->m, j->seed,
+                                                 s->streams[s->free_slots.back()], s->mempool, pin,
+                                                 &c);
+      if (st != LC_OK && pin != nullptr) s->pinned_free.push_back(pin);
       if (st != LC_OK) {
         s->queue.pop_front();
         finish_job(s, j, st);
@@ -1352,13 +1654,20 @@ static bool progress(lc_server* s) {
     bool finished = false;
     if (j->state == Job::kRunning) {
       cudaError_t e = c->rs.state == RunState::kDone ? cudaSuccess : cudaEventQuery(c->ev);
-      if (e == cudaSuccess) {
+      if (e == cudaSuccess && j->cancel) {
+        // the work enqueued last has completed: stop at this phase boundary
+        finish_job(s, j, LC_ERR_CANCELLED);
+        finished = true;
+        any = true;
+      } else if (e == cudaSuccess) {
         lc_status st = c->rs.state == RunState::kDone ? c->rs.st : run_complete(c);
         if (st != LC_OK) {
           finish_job(s, j, st);
           finished = true;
         } else if (c->rs.state == RunState::kDone) {
           j->rounds = c->last_rounds;
+          j->hn = c->rs.hn;
+          j->hm = c->rs.hm;
           if (j->n > 0 &&
               (cudaMemcpyAsync(j->h_labels, c->own_labels, (uint64_t)j->n * 4,
                                cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
@@ -1428,10 +1737,22 @@ extern "C" lc_status lc_server_create(uint64_t budget_bytes, uint32_t slots, lc_
     budget_bytes = (uint64_t)(free_b * 0.8);
   }
   s->budget = budget_bytes;
+  cudaMemPoolProps props{};
+  props.allocType = cudaMemAllocationTypePinned;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = s->device;
+  if (cudaMemPoolCreate(&s->mempool, &props) != cudaSuccess) {
+    delete s;
+    return LC_ERR_CUDA;
+  }
+  // keep released memory in the pool for later contexts (up to the budget)
+  uint64_t keep = budget_bytes;
+  cudaMemPoolSetAttribute(s->mempool, cudaMemPoolAttrReleaseThreshold, &keep);
   for (uint32_t q = 0; q < slots; ++q) {
     cudaStream_t st = nullptr;
     if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
       for (auto x : s->streams) cudaStreamDestroy(x);
+      cudaMemPoolDestroy(s->mempool);
       delete s;
       return LC_ERR_CUDA;
     }
@@ -1474,8 +1795,31 @@ extern "C" lc_status lc_server_submit(lc_server* s, uint32_t n, const uint32_t* 
   return LC_OK;
 }
 
-extern "C" lc_status lc_server_wait(lc_server* s, uint64_t job, double timeout_s,
-                                    uint32_t* rounds, double* latency_s) {
+extern "C" lc_status lc_server_cancel(lc_server* s, uint64_t job) {
+  if (!s) return LC_ERR_INVALID;
+  {
+    std::lock_guard<std::mutex> lock(s->mu);
+    auto it = s->jobs.find(job);
+    if (it == s->jobs.end()) return LC_ERR_INVALID;
+    Job* j = it->second;
+    if (j->state == Job::kQueued) {
+      auto q = std::find(s->queue.begin(), s->queue.end(), j);
+      if (q != s->queue.end()) s->queue.erase(q);
+      finish_job(s, j, LC_ERR_CANCELLED);
+    } else if (j->state == Job::kRunning) {
+      j->cancel = true;
+    } else {
+      return LC_ERR_INVALID;  // its labels are already being copied out, or it is done
+    }
+  }
+  s->cv_work.notify_one();
+  s->cv_done.notify_all();
+  return LC_OK;
+}
+
+extern "C" lc_status lc_server_result(lc_server* s, uint64_t job, double timeout_s,
+                                      uint32_t* rounds, double* latency_s, uint64_t* n_i,
+                                      uint64_t* m_i, uint32_t cap) {
   if (!s) return LC_ERR_INVALID;
   std::unique_lock<std::mutex> lock(s->mu);
   auto it = s->jobs.find(job);
@@ -1491,9 +1835,21 @@ extern "C" lc_status lc_server_wait(lc_server* s, uint64_t job, double timeout_s
   if (rounds) *rounds = j->rounds;
   if (latency_s) *latency_s = std::chrono::duration<double>(j->t_done - j->t_submit).count();
   lc_status st = j->status;
+  if (st == LC_OK && (n_i || m_i)) {
+    for (size_t i = 0; i < std::min<size_t>(cap, j->hn.size()); ++i) {
+      if (n_i) n_i[i] = j->hn[i];
+      if (m_i) m_i[i] = j->hm[i];
+    }
+    if (j->hn.size() > cap) st = LC_ERR_INVALID;
+  }
   s->jobs.erase(it);
   delete j;
   return st;
+}
+
+extern "C" lc_status lc_server_wait(lc_server* s, uint64_t job, double timeout_s,
+                                    uint32_t* rounds, double* latency_s) {
+  return lc_server_result(s, job, timeout_s, rounds, latency_s, nullptr, nullptr, 0);
 }
 
 extern "C" lc_status lc_server_stats(lc_server* s, uint64_t* completed, uint64_t* peak_active,
@@ -1515,8 +1871,13 @@ extern "C" lc_status lc_server_destroy(lc_server* s) {
   s->cv_work.notify_all();
   if (s->worker.joinable()) s->worker.join();
   for (auto& kv : s->jobs) delete kv.second;
-  for (auto c : s->pool) lc_destroy(c);
-  for (auto x : s->streams) cudaStreamDestroy(x);
+  for (auto c : s->pool) server_release(s, c);
+  for (auto x : s->streams) {
+    cudaStreamSynchronize(x);
+    cudaStreamDestroy(x);
+  }
+  cudaMemPoolDestroy(s->mempool);
+  for (auto p : s->pinned_chunks) cudaFreeHost(p);
   delete s;
   return LC_OK;
 }

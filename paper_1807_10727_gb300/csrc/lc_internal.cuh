@@ -40,6 +40,8 @@ enum KernelId : int {
   kKIdentity,
   kKRankProbe,
   kKFilter,
+  kKBucketEdges,
+  kKSegDedup,
   kNumKernels
 };
 
@@ -166,6 +168,58 @@ int hash_plan(uint64_t max_count, PassPlan* plan);
 
 // Zero the digit counts of s.hist (before a producer accumulates them).
 void hist_reset(SortScratch& s, const Launch& L);
+
+// ------------------------------------------------- phase-0 edge buckets
+// The n vertex ids are cut into nb near-equal blocks (block of v =
+// min(umulhi(v, scale), nb - 1)); an edge belongs to the bucket (lower block,
+// higher block), numbered lo * nb + hi.  Grouping the input edges by bucket
+// (ascending bucket number, rows of one lower block together) means that, at
+// any moment, the edges in flight gather per-vertex data from about two
+// blocks, a slice of the vertex arrays that stays in L2.
+constexpr uint32_t kBucketMaxBlocks = 32;
+constexpr uint32_t kBucketMaxDigits = kBucketMaxBlocks * kBucketMaxBlocks;
+constexpr uint32_t kBucketFillStride = 32;  // words between fill counters (one line each)
+// scratch words: counts [0, kBucketMaxDigits), padded fill counters, then the
+// segment starts and tile prefixes of the segmented deduplication (below)
+constexpr uint64_t kSegStartOff = kBucketMaxDigits * (1 + kBucketFillStride);
+constexpr uint64_t kSegTileOff = kSegStartOff + 512;
+constexpr uint64_t kBucketScratchWords = kSegTileOff + 512;
+
+// Blocks used for n vertices so that two blocks of 8-byte per-vertex data
+// fit in window_bytes (at least 2, at most kBucketMaxBlocks).
+uint32_t bucket_blocks_for(uint32_t n, uint64_t window_bytes);
+
+// out[0, m) = the input edges (u << 32 | v) grouped by bucket (order inside a
+// bucket unspecified).  Ids >= n set kErrBadVertex and become the self-loop
+// (0, 0), which no step counts.  scratch: kBucketScratchWords words.
+void bucket_edges(const uint32_t* src, const uint32_t* dst, uint64_t m, uint32_t n, uint32_t nb,
+                  uint64_t* out, uint32_t* scratch, unsigned* err, const Launch& L);
+
+// -------------------------------------------- segmented deduplication
+// Large phases: the relabel counts its (mixed) keys per segment, the top
+// kSegBits bits, into scratch[0, kSegs); seg_begin turns the counts into
+// segment regions; filter_seg drops repeats (device-wide cache, as
+// filter_hll) and writes every kept key into its segment's region; seg_dedup
+// then keeps the distinct keys of each segment with an open-addressing table
+// slice of `slots` entries per segment, taking the segments in order so that
+// the slices in use stay in L2.  seg_compact copies the kept keys of all
+// segments into one contiguous array (before a full-sort fallback).
+constexpr int kSegBits = 8;
+constexpr uint32_t kSegs = 1u << kSegBits;
+
+void seg_begin(uint32_t* scratch, const Launch& L);
+void filter_seg(const uint64_t* in, const unsigned long long* d_in, uint64_t max_count,
+                uint64_t* out, unsigned long long* d_out, unsigned long long* gcache,
+                uint32_t gslots, int admit, uint32_t* hll, uint32_t* scratch, unsigned* err,
+                const Launch& L);
+// Returns false when the table cannot hold kSegs slices of `slots` entries
+// (the caller then compacts and uses hash_dedup).  Overflow of a slice sets
+// kErrOverflow (the caller falls back to the full sort).
+bool seg_dedup(const uint64_t* keys, uint32_t* scratch, uint64_t max_count, uint64_t* table,
+               uint64_t table_slots, uint64_t slots, uint64_t* out, unsigned long long* m_next,
+               uint8_t* flags, uint32_t n, int half_bits, unsigned* ticket, unsigned* err,
+               const Launch& L);
+void seg_compact(const uint64_t* keys, const uint32_t* scratch, uint64_t* out, const Launch& L);
 
 // Duplicate filter and distinct-count sketch of the *d_in mixed keys in `in`:
 // keys found in the device-wide cache (gcache, gslots slots, a power of two,

@@ -2,7 +2,7 @@
 // ranking and closed-neighbourhood parent (Section 2 N(v), Section 3 random
 // ordering), contraction of the parent arborescences by pointer jumping
 // (Theorem thm:tree-rounds), relabelling of the edges (O(1)-round contraction
-// lemma) and composition of the per-phase maps back to the input (Section 7).
+// lemma) and composition of the per-phase maps back to the input (Section 6, Empirical study).
 #include <algorithm>
 
 #include "lc_internal.cuh"
@@ -674,18 +674,18 @@ __global__ void __launch_bounds__(kThreads) k_relabel(
         }
       }
     }
-    // warp-level compaction offsets, then one block scan over warp totals
-    uint32_t mine = __popc(emitmask);
-    uint32_t incl = mine;
+    // warp totals, then one block scan over them; a warp writes the emitted
+    // keys of each item position as one contiguous run (coalesced stores)
+    uint32_t wtot = 0;
     uint32_t kept = __popc(keepmask);
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      uint32_t y = __shfl_up_sync(kFull, incl, o);
-      if (lane >= (unsigned)o) incl += y;
-      kept += __shfl_xor_sync(kFull, kept, o);
+    for (int i = 0; i < kRelItems; ++i) wtot += __popc(__ballot_sync(kFull, (emitmask >> i) & 1u));
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) kept += __shfl_xor_sync(kFull, kept, o);
+    if (lane == 0) {
+      ws[w] = wtot;
+      wk[w] = kept;
     }
-    if (lane == 31) ws[w] = incl;
-    if (lane == 0) wk[w] = kept;
     __syncthreads();
     if (tid == 0) {
       uint32_t run = 0, kall = 0;
@@ -699,10 +699,14 @@ __global__ void __launch_bounds__(kThreads) k_relabel(
       s_base = run ? atomicAdd(emitted, (unsigned long long)run) : 0ull;
     }
     __syncthreads();
-    uint64_t pos = s_base + ws[w] + (incl - mine);
+    uint64_t pos = s_base + ws[w];
+    const unsigned lt = lanemask_lt();
 #pragma unroll
-    for (int i = 0; i < kRelItems; ++i)
-      if (emitmask & (1u << i)) __stcs(keys_out + pos++, key[i]);
+    for (int i = 0; i < kRelItems; ++i) {
+      const unsigned b = __ballot_sync(kFull, (emitmask >> i) & 1u);
+      if ((emitmask >> i) & 1u) __stcs(keys_out + pos + __popc(b & lt), key[i]);
+      pos += __popc(b);
+    }
     __syncthreads();
   }
   for (int i = tid; i < plan.passes * kRadixMax; i += kThreads) {

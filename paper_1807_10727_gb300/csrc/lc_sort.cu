@@ -184,15 +184,12 @@ __global__ void __launch_bounds__(kSortThreads) k_filter_hll(
           rest ? (uint32_t)__clzll((long long)rest) + 1u : (uint32_t)(65 - kHllBits);
       atomicMax(&reg[(uint32_t)(k[i] >> (64 - kHllBits))], rank);
     }
-    // warp offsets, then one block scan over the warp totals
-    const uint32_t mine = __popc(keep);
-    uint32_t incl = mine;
+    // warp totals, then one block scan over them; a warp writes the kept
+    // keys of each item position as one contiguous run (coalesced stores)
+    uint32_t wtot = 0;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-      if (lane >= (unsigned)o) incl += y;
-    }
-    if (lane == 31) ws[w] = incl;
+    for (int i = 0; i < kFilterItems; ++i) wtot += __popc(__ballot_sync(kFull, (keep >> i) & 1u));
+    if (lane == 0) ws[w] = wtot;
     __syncthreads();
     if (tid == 0) {
       uint32_t run = 0;
@@ -204,10 +201,14 @@ __global__ void __launch_bounds__(kSortThreads) k_filter_hll(
       s_base = run ? atomicAdd(d_out, (unsigned long long)run) : 0ull;
     }
     __syncthreads();
-    uint64_t pos = s_base + ws[w] + (incl - mine);
+    uint64_t pos = s_base + ws[w];
+    const unsigned lt = lanemask_lt();
 #pragma unroll
-    for (int i = 0; i < kFilterItems; ++i)
-      if (keep & (1u << i)) __stcs(out + pos++, k[i]);
+    for (int i = 0; i < kFilterItems; ++i) {
+      const unsigned b = __ballot_sync(kFull, (keep >> i) & 1u);
+      if ((keep >> i) & 1u) __stcs(out + pos + __popc(b & lt), k[i]);
+      pos += __popc(b);
+    }
     __syncthreads();
   }
   for (int i = tid; i < kHllRegs; i += kSortThreads)
@@ -220,7 +221,11 @@ __global__ void __launch_bounds__(kSortThreads) k_filter_hll(
 // digit's tile count as an aggregate, walk back over the preceding tiles until
 // an inclusive prefix is found (all owned digits advance together, one load
 // each per step), publish the inclusive prefixes.  Returns false if a bounded
-// wait gave up.
+// wait gave up.  A tile whose wait gave up still publishes what it summed as
+// its inclusive prefix: that value is only a lower bound, so the tiles behind
+// it compute offsets that are too low (their writes stay inside the output,
+// which is bounds-checked) and the host, which sees kErrTimeout first,
+// discards the whole phase.
 template <int kPer>
 __device__ __forceinline__ bool look_back_digits(uint64_t* status, uint32_t tile, int stride,
                                                  const uint32_t* dig, const uint32_t* cnt,
@@ -257,7 +262,10 @@ __device__ __forceinline__ bool look_back_digits(uint64_t* status, uint32_t tile
         }
         if (flag == kFlagAgg) {
           prefix[q] += (uint32_t)wd;
-          --j[q];  // tile 0 always publishes a prefix, so j never wraps
+          // j stops at 0 at the latest: tile 0 publishes only prefixes, and
+          // when it publishes nothing (the stall hook) this wait runs out at
+          // j = 0 instead of moving past it
+          --j[q];
           spins = 0;
         }
       }
@@ -655,9 +663,517 @@ __global__ void __launch_bounds__(kSortThreads) k_unique_rename(
   if (base + kScanTile >= count && tid == 0) *m_next = (unsigned long long)s_excl + tile_total;
 }
 
+
+// ------------------------------------------------- phase-0 edge buckets
+
+struct EdgeBlocks {
+  uint32_t scale, nb;
+  __device__ __forceinline__ uint32_t blk(uint32_t v) const {
+    return min(__umulhi(v, scale), nb - 1u);
+  }
+  __device__ __forceinline__ uint32_t digit(uint32_t u, uint32_t v) const {
+    const uint32_t a = blk(u), b = blk(v);
+    return min(a, b) * nb + max(a, b);
+  }
+};
+
+constexpr int kBktItems = 16;
+constexpr int kBktTile = kSortThreads * kBktItems;  // edges per tile
+
+// Bucket counts of the input edges (ids >= n count as the loop (0, 0)).
+__global__ void __launch_bounds__(kSortThreads) k_bucket_hist(
+    const uint32_t* __restrict__ src, const uint32_t* __restrict__ dst, uint64_t m, uint32_t n,
+    int vec, EdgeBlocks eb, uint32_t* __restrict__ ghist, unsigned* err) {
+  __shared__ uint32_t h[kBucketMaxDigits];
+  const uint32_t nd = eb.nb * eb.nb;
+  for (uint32_t i = threadIdx.x; i < nd; i += blockDim.x) h[i] = 0;
+  __syncthreads();
+  bool bad = false;
+  auto count = [&](uint32_t u, uint32_t v) {
+    if (u >= n || v >= n) {
+      bad = true;
+      u = v = 0;
+    }
+    atomicAdd(&h[eb.digit(u, v)], 1u);
+  };
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  const uint64_t gt = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  uint64_t done = 0;
+  if (vec) {
+    const uint64_t nq = m / 4;
+    const uint4* s4 = reinterpret_cast<const uint4*>(src);
+    const uint4* d4 = reinterpret_cast<const uint4*>(dst);
+    for (uint64_t q = gt; q < nq; q += stride) {
+      const uint4 a = __ldcs(s4 + q), b = __ldcs(d4 + q);
+      count(a.x, b.x);
+      count(a.y, b.y);
+      count(a.z, b.z);
+      count(a.w, b.w);
+    }
+    done = nq * 4;
+  }
+  for (uint64_t j = done + gt; j < m; j += stride) count(__ldcs(src + j), __ldcs(dst + j));
+  if (bad) atomicOr(err, kErrBadVertex);
+  __syncthreads();
+  for (uint32_t i = threadIdx.x; i < nd; i += blockDim.x)
+    if (h[i]) atomicAdd(&ghist[i], h[i]);
+}
+
+// fill[d * kBucketFillStride] = first position of bucket d (exclusive scan of
+// the counts; one block, four buckets per thread).
+__global__ void __launch_bounds__(kSortThreads) k_bucket_starts(const uint32_t* __restrict__ ghist,
+                                                                uint32_t nd, uint32_t* fill) {
+  __shared__ uint32_t ws[kWarps];
+  constexpr int kPer = kBucketMaxDigits / kSortThreads;
+  uint32_t c[kPer], sum = 0;
+#pragma unroll
+  for (int q = 0; q < kPer; ++q) {
+    const uint32_t d = threadIdx.x * kPer + q;
+    c[q] = d < nd ? ghist[d] : 0u;
+    sum += c[q];
+  }
+  uint32_t total;
+  uint32_t e = block_exclusive_scan(sum, ws, &total);
+#pragma unroll
+  for (int q = 0; q < kPer; ++q) {
+    const uint32_t d = threadIdx.x * kPer + q;
+    if (d < nd) fill[d * kBucketFillStride] = e;
+    e += c[q];
+  }
+}
+
+// Scatter of the input edges into their buckets.  Order inside a bucket does
+// not matter, so a tile of kBktTile edges is ranked with shared-memory
+// atomics (no stable ranking, no look-back): each bucket's tile count is
+// reserved in the bucket with one global atomicAdd on its fill counter (the
+// counters sit one cache line apart), the tile is staged in shared memory in
+// bucket order and written out in runs.
+__global__ void __launch_bounds__(kSortThreads) k_bucket_scatter(
+    const uint32_t* __restrict__ src, const uint32_t* __restrict__ dst, uint64_t m, uint32_t n,
+    int vec, EdgeBlocks eb, uint32_t* fill, uint64_t* __restrict__ out, unsigned* err) {
+  __shared__ uint64_t stage[kBktTile];
+  __shared__ uint32_t s_cnt[kBucketMaxDigits];
+  __shared__ uint32_t s_off[kBucketMaxDigits];
+  __shared__ uint32_t s_gb[kBucketMaxDigits];
+  __shared__ uint32_t ws[kWarps];
+  constexpr int kPer = kBucketMaxDigits / kSortThreads;
+  const unsigned tid = threadIdx.x;
+  const uint32_t nd = eb.nb * eb.nb;
+  for (uint32_t i = tid; i < nd; i += kSortThreads) s_cnt[i] = 0;
+  __syncthreads();
+  const uint64_t ntiles = (m + kBktTile - 1) / kBktTile;
+  for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const uint64_t base = t * kBktTile;
+    uint32_t u[kBktItems], v[kBktItems];
+    if (vec && base + kBktTile <= m) {
+      // item 4*i + c is edge base + 4 * (i * kSortThreads + tid) + c
+      const uint4* s4 = reinterpret_cast<const uint4*>(src + base);
+      const uint4* d4 = reinterpret_cast<const uint4*>(dst + base);
+#pragma unroll
+      for (int i = 0; i < kBktItems / 4; ++i) {
+        const uint4 a = __ldcs(s4 + i * kSortThreads + tid), b = __ldcs(d4 + i * kSortThreads + tid);
+        u[4 * i] = a.x; u[4 * i + 1] = a.y; u[4 * i + 2] = a.z; u[4 * i + 3] = a.w;
+        v[4 * i] = b.x; v[4 * i + 1] = b.y; v[4 * i + 2] = b.z; v[4 * i + 3] = b.w;
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < kBktItems; ++i) {
+        const uint64_t j = base + (uint64_t)i * kSortThreads + tid;
+        u[i] = j < m ? __ldcs(src + j) : 0u;
+        v[i] = j < m ? __ldcs(dst + j) : 0u;
+      }
+    }
+    const uint32_t nvalid = (uint32_t)(m - base < (uint64_t)kBktTile ? m - base : (uint64_t)kBktTile);
+    // per item: bucket << 16 | rank inside the tile's run of that bucket
+    // (bucket 0xFFFF: not an item)
+    uint32_t dr[kBktItems];
+#pragma unroll
+    for (int i = 0; i < kBktItems; ++i) {
+      // every item of a full tile is valid; in the last tile the first nvalid
+      // positions are, whichever load form was used (the vector form needs a
+      // full tile)
+      const uint32_t pos = (vec && base + kBktTile <= m)
+                               ? 4u * ((i >> 2) * kSortThreads + tid) + (i & 3)
+                               : (uint32_t)i * kSortThreads + tid;
+      if (pos < nvalid) {
+        if (u[i] >= n || v[i] >= n) u[i] = v[i] = 0;  // reported by k_bucket_hist
+        const uint32_t d = eb.digit(u[i], v[i]);
+        dr[i] = (d << 16) | atomicAdd(&s_cnt[d], 1u);
+      } else {
+        dr[i] = 0xFFFF0000u;
+      }
+    }
+    __syncthreads();
+    // in-tile bucket offsets, and the tile's range in every bucket it feeds
+    uint32_t c[kPer], sum = 0;
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+      const uint32_t d = tid * kPer + q;
+      c[q] = d < nd ? s_cnt[d] : 0u;
+      sum += c[q];
+    }
+    uint32_t tot;
+    uint32_t e = block_exclusive_scan(sum, ws, &tot);
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+      const uint32_t d = tid * kPer + q;
+      if (d < nd) {
+        s_off[d] = e;
+        if (c[q]) s_gb[d] = atomicAdd(&fill[d * kBucketFillStride], c[q]);
+      }
+      e += c[q];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < kBktItems; ++i) {
+      if ((dr[i] >> 16) < nd) {
+        const uint32_t at = s_off[dr[i] >> 16] + (dr[i] & 0xFFFFu);
+        if (index_ok(err, kKBucketEdges, at, nvalid))
+          stage[at] = ((uint64_t)u[i] << 32) | v[i];
+      }
+    }
+    __syncthreads();
+    for (uint32_t j = tid; j < nvalid; j += kSortThreads) {
+      const uint64_t x = stage[j];
+      const uint32_t d = eb.digit((uint32_t)(x >> 32), (uint32_t)x);
+      const uint64_t pos = (uint64_t)s_gb[d] + (j - s_off[d]);
+      if (index_ok(err, kKBucketEdges, pos, m)) out[pos] = x;
+    }
+    __syncthreads();
+    for (uint32_t i = tid; i < nd; i += kSortThreads) s_cnt[i] = 0;
+    __syncthreads();
+  }
+}
+
+
+// ------------------------------------------------ segmented deduplication
+
+constexpr int kSegFilterItems = 8;
+constexpr int kSegFilterTile = kSortThreads * kSegFilterItems;
+constexpr int kSegInsItems = 8;
+constexpr int kSegInsTile = kSortThreads * kSegInsItems;
+
+__device__ __forceinline__ uint32_t seg_of(uint64_t y) { return (uint32_t)(y >> (64 - kSegBits)); }
+
+// starts[s] = exclusive scan of the per-segment key counts scratch[0, kSegs);
+// the fill counters start at the starts.
+__global__ void __launch_bounds__(kSortThreads) k_seg_starts(uint32_t* scratch) {
+  static_assert(kSegs == kSortThreads, "one segment per thread");
+  __shared__ uint32_t ws[kWarps];
+  const uint32_t c = scratch[threadIdx.x];
+  uint32_t total;
+  const uint32_t e = block_exclusive_scan(c, ws, &total);
+  scratch[kSegStartOff + threadIdx.x] = e;
+  scratch[kBucketMaxDigits + threadIdx.x * kBucketFillStride] = e;
+  if (threadIdx.x == 0) scratch[kSegStartOff + kSegs] = total;
+}
+
+// k_filter_hll whose kept keys go to their segment's region: a tile's kept
+// keys are ranked per segment in shared memory, each segment's share is
+// reserved with one atomicAdd on its fill counter, and the tile is staged in
+// segment order and written out in runs.
+__global__ void __launch_bounds__(kSortThreads) k_filter_seg(
+    const uint64_t* __restrict__ in, const unsigned long long* d_in, uint64_t* __restrict__ out,
+    uint64_t cap, unsigned long long* d_out, unsigned long long* gcache, uint32_t gmask, int admit,
+    uint32_t* __restrict__ ghll, uint32_t* scratch, unsigned* err) {
+  __shared__ uint32_t reg[kHllRegs];
+  __shared__ uint64_t stage[kSegFilterTile];
+  __shared__ uint32_t s_cnt[kSegs], s_off[kSegs], s_gb[kSegs];
+  __shared__ uint32_t ws[kWarps];
+  const unsigned tid = threadIdx.x, lane = lane_id(), w = tid >> 5;
+  uint32_t* fill = scratch + kBucketMaxDigits;
+  for (int i = tid; i < kHllRegs; i += kSortThreads) reg[i] = 0;
+  s_cnt[tid] = 0;
+  __syncthreads();
+  const uint64_t count = *d_in;
+  const uint64_t tiles = (count + kSegFilterTile - 1) / kSegFilterTile;
+  unsigned long long kept_total = 0;
+  for (uint64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+    const uint64_t base = t * kSegFilterTile + (uint64_t)w * 32 * kSegFilterItems;
+    uint64_t k[kSegFilterItems];
+    unsigned long long gv[kSegFilterItems];
+#pragma unroll
+    for (int i = 0; i < kSegFilterItems; ++i) {
+      const uint64_t j = base + (uint64_t)i * 32 + lane;
+      k[i] = j < count ? __ldcs(in + j) : 0ull;
+    }
+#pragma unroll
+    for (int i = 0; i < kSegFilterItems; ++i) {
+      const uint64_t j = base + (uint64_t)i * 32 + lane;
+      gv[i] = (j < count && gcache != nullptr) ? __ldcg(gcache + ((uint32_t)(k[i] >> 20) & gmask))
+                                               : 0ull;
+    }
+    uint32_t dr[kSegFilterItems];
+#pragma unroll
+    for (int i = 0; i < kSegFilterItems; ++i) {
+      const uint64_t j = base + (uint64_t)i * 32 + lane;
+      dr[i] = 0xFFFF0000u;
+      if (j >= count || (gcache != nullptr && gv[i] == k[i])) continue;
+      if (gcache != nullptr && (admit == 0 || ((j * kGamma) >> (64 - admit)) == 0))
+        __stcg(gcache + ((uint32_t)(k[i] >> 20) & gmask), (unsigned long long)k[i]);
+      const uint64_t rest = k[i] << kHllBits;
+      const uint32_t rank =
+          rest ? (uint32_t)__clzll((long long)rest) + 1u : (uint32_t)(65 - kHllBits);
+      atomicMax(&reg[(uint32_t)(k[i] >> (64 - kHllBits))], rank);
+      const uint32_t d = seg_of(k[i]);
+      dr[i] = (d << 16) | atomicAdd(&s_cnt[d], 1u);
+    }
+    __syncthreads();
+    const uint32_t c = s_cnt[tid];
+    uint32_t tot;
+    const uint32_t e = block_exclusive_scan(c, ws, &tot);
+    s_off[tid] = e;
+    if (c) s_gb[tid] = atomicAdd(&fill[tid * kBucketFillStride], c);
+    kept_total += tot;
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < kSegFilterItems; ++i) {
+      if ((dr[i] >> 16) < kSegs) {
+        const uint32_t at = s_off[dr[i] >> 16] + (dr[i] & 0xFFFFu);
+        if (index_ok(err, kKSegDedup, at, tot)) stage[at] = k[i];
+      }
+    }
+    __syncthreads();
+    for (uint32_t j = tid; j < tot; j += kSortThreads) {
+      const uint64_t x = stage[j];
+      const uint32_t d = seg_of(x);
+      const uint64_t pos = (uint64_t)s_gb[d] + (j - s_off[d]);
+      if (index_ok(err, kKSegDedup, pos, cap)) __stcg(out + pos, x);
+    }
+    __syncthreads();
+    s_cnt[tid] = 0;
+    __syncthreads();
+  }
+  if (tid == 0 && kept_total) atomicAdd(d_out, kept_total);
+  for (int i = tid; i < kHllRegs; i += kSortThreads)
+    if (reg[i]) atomicMax(&ghll[i], reg[i]);
+}
+
+// tile prefix of the segments: tiles[s] = sum over earlier segments of
+// ceil(kept_s / kSegInsTile), kept_s = fill_s - start_s.
+__global__ void __launch_bounds__(kSortThreads) k_seg_tiles(uint32_t* scratch) {
+  __shared__ uint32_t ws[kWarps];
+  const uint32_t s = threadIdx.x;
+  const uint32_t kept = scratch[kBucketMaxDigits + s * kBucketFillStride] - scratch[kSegStartOff + s];
+  const uint32_t nt = (kept + kSegInsTile - 1) / kSegInsTile;
+  uint32_t total;
+  const uint32_t e = block_exclusive_scan(nt, ws, &total);
+  scratch[kSegTileOff + s] = e;
+  if (s == 0) scratch[kSegTileOff + kSegs] = total;
+}
+
+// Distinct keys of segments [seg_lo, seg_hi): tiles claimed in order by
+// ticket; a key probes its segment's slice (slots entries, linear probing
+// from its low bits) with a read through L2 and, on an empty slot, a
+// compare-and-swap.  Slots only ever change from empty to a key, so a read
+// that returns the key itself settles the probe, and a stale empty only
+// costs the compare-and-swap.  Keys new to the table are staged per tile,
+// appended to `out` with one atomicAdd per tile, and both endpoints of each
+// are marked in flags.  A slice that fills up raises kErrOverflow.
+__global__ void __launch_bounds__(kSortThreads) k_seg_insert(
+    const uint64_t* __restrict__ keys, const uint32_t* __restrict__ scratch, uint32_t seg_lo,
+    uint32_t seg_hi, uint64_t slots, unsigned long long* table, uint64_t* __restrict__ out,
+    uint64_t cap, unsigned long long* m_next, uint8_t* flags, uint32_t n, int half_bits,
+    unsigned* ticket, unsigned* err) {
+  __shared__ uint64_t fresh[kSegInsTile];
+  __shared__ uint32_t s_new, s_t;
+  __shared__ unsigned long long s_base;
+  const unsigned tid = threadIdx.x;
+  const uint32_t* tiles = scratch + kSegTileOff;
+  const uint32_t* starts = scratch + kSegStartOff;
+  const uint32_t* fill = scratch + kBucketMaxDigits;
+  const uint32_t t0 = tiles[seg_lo], t1 = tiles[seg_hi];
+  const uint64_t half_mask = (1ull << half_bits) - 1;
+  const uint64_t smask = slots - 1;
+  if (tid == 0) s_new = 0;
+  for (;;) {
+    if (tid == 0) s_t = t0 + atomicAdd(ticket, 1u);
+    __syncthreads();
+    const uint32_t t = s_t;
+    if (t >= t1) break;
+    // segment of tile t: last s in [seg_lo, seg_hi) with tiles[s] <= t
+    uint32_t lo = seg_lo, hi = seg_hi - 1;
+    while (lo < hi) {
+      const uint32_t mid = (lo + hi + 1) >> 1;
+      if (tiles[mid] <= t) lo = mid;
+      else hi = mid - 1;
+    }
+    const uint32_t sg = lo;
+    const uint64_t kb = (uint64_t)starts[sg] + (uint64_t)(t - tiles[sg]) * kSegInsTile;
+    const uint64_t ke = fill[sg * kBucketFillStride];
+    unsigned long long* slice = table + (uint64_t)(sg - seg_lo) * slots;
+    uint64_t k[kSegInsItems];
+#pragma unroll
+    for (int i = 0; i < kSegInsItems; ++i) {
+      const uint64_t j = kb + (uint64_t)i * kSortThreads + tid;
+      k[i] = (j < ke && j < cap) ? __ldcs(keys + j) : kEmpty;
+    }
+#pragma unroll
+    for (int i = 0; i < kSegInsItems; ++i) {
+      if (k[i] == kEmpty) continue;
+      uint64_t slot = k[i] & smask;
+      bool done = false;
+      for (uint64_t probe = 0; probe < slots; ++probe) {
+        const unsigned long long cur = __ldcg(slice + slot);
+        if (cur == k[i]) {
+          done = true;
+          break;
+        }
+        if (cur == kEmpty) {
+          const unsigned long long old = atomicCAS(slice + slot, kEmpty, k[i]);
+          if (old == kEmpty) {
+            fresh[atomicAdd(&s_new, 1u)] = k[i];
+            done = true;
+            break;
+          }
+          if (old == k[i]) {
+            done = true;
+            break;
+          }
+        }
+        slot = (slot + 1) & smask;
+      }
+      if (!done) atomicOr(err, kErrOverflow);
+    }
+    __syncthreads();
+    const uint32_t nn = s_new;
+    if (tid == 0) s_base = nn ? atomicAdd(m_next, (unsigned long long)nn) : 0ull;
+    __syncthreads();
+    for (uint32_t e = tid; e < nn; e += kSortThreads) {
+      const uint64_t v = fresh[e];
+      const uint64_t pos = s_base + e;
+      if (index_ok(err, kKSegDedup, pos, cap)) out[pos] = v;
+      const uint64_t kk = key_unmix(v);
+      const uint64_t a = kk >> half_bits, b = kk & half_mask;
+      if (index_ok(err, kKSegDedup, a > b ? a : b, n)) {
+        flags[a] = 1;
+        flags[b] = 1;
+      }
+    }
+    __syncthreads();
+    if (tid == 0) s_new = 0;
+  }
+}
+
+// out[prefix of kept counts + j] = the j-th kept key of each segment.
+__global__ void k_seg_compact(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ scratch,
+                              uint64_t* __restrict__ out) {
+  const uint32_t* starts = scratch + kSegStartOff;
+  const uint32_t* fill = scratch + kBucketMaxDigits;
+  __shared__ uint64_t s_dst;
+  for (uint32_t sg = blockIdx.x; sg < kSegs; sg += gridDim.x) {
+    if (threadIdx.x == 0) {
+      uint64_t before = 0;
+      for (uint32_t q = 0; q < sg; ++q) before += fill[q * kBucketFillStride] - starts[q];
+      s_dst = before;
+    }
+    __syncthreads();
+    const uint64_t b = starts[sg], e = fill[sg * kBucketFillStride];
+    for (uint64_t j = b + threadIdx.x; j < e; j += blockDim.x) out[s_dst + (j - b)] = keys[j];
+    __syncthreads();
+  }
+}
+
 }  // namespace
 
 // ------------------------------------------------------------- host side
+
+uint32_t bucket_blocks_for(uint32_t n, uint64_t window_bytes) {
+  const uint64_t w = std::max<uint64_t>(window_bytes, 1);
+  const uint64_t nb = (16ull * n + w - 1) / w;
+  return (uint32_t)std::min<uint64_t>(kBucketMaxBlocks, std::max<uint64_t>(2, nb));
+}
+
+void bucket_edges(const uint32_t* src, const uint32_t* dst, uint64_t m, uint32_t n, uint32_t nb,
+                  uint64_t* out, uint32_t* scratch, unsigned* err, const Launch& L) {
+  if (m == 0) return;
+  nb = std::max<uint32_t>(2, std::min(nb, kBucketMaxBlocks));
+  // scale = ceil(nb * 2^32 / n); blocks are clamped to nb - 1 (needs n >= nb)
+  const uint64_t sc = (((uint64_t)nb << 32) + n - 1) / std::max<uint32_t>(n, nb);
+  const EdgeBlocks eb{(uint32_t)std::min<uint64_t>(sc, 0xFFFFFFFFull), nb};
+  const uint32_t nd = nb * nb;
+  const int vec = ((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst)) & 15) == 0;
+  uint32_t* hist = scratch;
+  uint32_t* fill = scratch + kBucketMaxDigits;
+  cudaMemsetAsync(hist, 0, sizeof(uint32_t) * nd, L.stream);
+  {
+    KScope ks(L, kKBucketEdges);
+    const int hgrid = (int)std::min<uint64_t>((m + 4095) / 4096, (uint64_t)L.sms * 8);
+    k_bucket_hist<<<hgrid, kSortThreads, 0, L.stream>>>(src, dst, m, n, vec, eb, hist, err);
+  }
+  {
+    KScope ks(L, kKBucketEdges);
+    k_bucket_starts<<<1, kSortThreads, 0, L.stream>>>(hist, nd, fill);
+  }
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bucket_scatter, kSortThreads, 0) !=
+          cudaSuccess ||
+      per_sm < 1)
+    per_sm = 1;
+  const int sgrid =
+      (int)std::min<uint64_t>((m + kBktTile - 1) / kBktTile, (uint64_t)L.sms * per_sm);
+  KScope ks(L, kKBucketEdges);
+  k_bucket_scatter<<<sgrid, kSortThreads, 0, L.stream>>>(src, dst, m, n, vec, eb, fill, out, err);
+}
+
+void seg_begin(uint32_t* scratch, const Launch& L) {
+  KScope ks(L, kKSegDedup);
+  k_seg_starts<<<1, kSortThreads, 0, L.stream>>>(scratch);
+}
+
+void filter_seg(const uint64_t* in, const unsigned long long* d_in, uint64_t max_count,
+                uint64_t* out, unsigned long long* d_out, unsigned long long* gcache,
+                uint32_t gslots, int admit, uint32_t* hll, uint32_t* scratch, unsigned* err,
+                const Launch& L) {
+  if (max_count == 0) return;
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_filter_seg, kSortThreads, 0) !=
+          cudaSuccess ||
+      per_sm < 1)
+    per_sm = 1;
+  const int grid = (int)std::min<uint64_t>((max_count + kSegFilterTile - 1) / kSegFilterTile,
+                                           (uint64_t)L.sms * per_sm);
+  KScope ks(L, kKFilter);
+  k_filter_seg<<<grid, kSortThreads, 0, L.stream>>>(in, d_in, out, max_count, d_out,
+                                                    gslots ? gcache : nullptr,
+                                                    gslots ? gslots - 1 : 0u, admit, hll, scratch,
+                                                    err);
+}
+
+bool seg_dedup(const uint64_t* keys, uint32_t* scratch, uint64_t max_count, uint64_t* table,
+               uint64_t table_slots, uint64_t slots, uint64_t* out, unsigned long long* m_next,
+               uint8_t* flags, uint32_t n, int half_bits, unsigned* ticket, unsigned* err,
+               const Launch& L) {
+  if (table == nullptr || slots == 0 || (slots & (slots - 1)) != 0 || slots > table_slots)
+    return false;
+  const uint32_t per_launch = (uint32_t)std::min<uint64_t>(kSegs, table_slots / slots);
+  {
+    KScope ks(L, kKSegDedup);
+    k_seg_tiles<<<1, kSortThreads, 0, L.stream>>>(scratch);
+  }
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_seg_insert, kSortThreads, 0) !=
+          cudaSuccess ||
+      per_sm < 1)
+    per_sm = 1;
+  const uint64_t max_tiles = (max_count + kSegInsTile - 1) / kSegInsTile + kSegs;
+  const int grid = (int)std::min<uint64_t>(max_tiles, (uint64_t)L.sms * per_sm);
+  for (uint32_t lo = 0; lo < kSegs; lo += per_launch) {
+    const uint32_t hi = std::min(kSegs, lo + per_launch);
+    cudaMemsetAsync(table, 0xFF, 8ull * slots * (hi - lo), L.stream);
+    cudaMemsetAsync(ticket, 0, sizeof(unsigned), L.stream);
+    KScope ks(L, kKSegDedup);
+    k_seg_insert<<<grid, kSortThreads, 0, L.stream>>>(
+        keys, scratch, lo, hi, slots, reinterpret_cast<unsigned long long*>(table), out,
+        max_count, m_next, flags, n, half_bits, ticket, err);
+  }
+  return true;
+}
+
+void seg_compact(const uint64_t* keys, const uint32_t* scratch, uint64_t* out, const Launch& L) {
+  KScope ks(L, kKSegDedup);
+  k_seg_compact<<<kSegs, kSortThreads, 0, L.stream>>>(keys, scratch, out);
+}
 
 uint64_t sort_status_words(uint64_t max_keys) {
   uint64_t tiles = (max_keys + kSortTile - 1) / kSortTile;

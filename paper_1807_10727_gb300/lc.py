@@ -19,16 +19,16 @@ import numpy as np
 from . import _build
 
 (LC_OK, LC_ERR_INVALID, LC_ERR_OOM, LC_ERR_CUDA, LC_ERR_NO_CONVERGENCE, LC_ERR_TIMEOUT,
- LC_ERR_INTERNAL) = range(7)
+ LC_ERR_INTERNAL, LC_ERR_CANCELLED) = range(8)
 LC_VARIANT_FOREST, LC_VARIANT_TWO_HOP, LC_VARIANT_TREE = 0, 1, 2
 
 # every symbol include/lc.h declares (checked by the CPU test suite)
 LC_DEDUP_HASH, LC_DEDUP_SORT = 0, 1
 EXPORTED = ("lc_create", "lc_configure", "lc_set_merge_to_large", "lc_set_dedup", "lc_set_param", "lc_run", "lc_run_host",
-            "lc_last_stats", "lc_last_dedup", "lc_profile", "lc_kernel_stats", "lc_destroy", "lc_status_str",
+            "lc_last_stats", "lc_last_dedup", "lc_dedup_fallbacks", "lc_profile", "lc_kernel_stats", "lc_destroy", "lc_status_str",
             "lc_rank_probe", "lc_run_static", "lc_batch_create", "lc_batch_run",
-            "lc_server_create", "lc_server_submit", "lc_server_wait", "lc_server_stats",
-            "lc_server_destroy")
+            "lc_server_create", "lc_server_submit", "lc_server_wait", "lc_server_result",
+            "lc_server_cancel", "lc_server_stats", "lc_server_destroy", "lc_fail_alloc")
 LC_STATIC_MAX_N, LC_STATIC_MAX_M = 131072, 524288
 
 _lib = None
@@ -62,6 +62,7 @@ def load(path: str | None = None):
     lib.lc_last_stats.argtypes = [p, pu32, pu64, pu64, u32]
     lib.lc_last_dedup.argtypes = [p, pu32, pu64, pu32, u32]
     lib.lc_last_dedup.restype = i32
+    lib.lc_dedup_fallbacks.argtypes = [p, pu64]
     lib.lc_profile.argtypes = [p, i32]
     lib.lc_kernel_stats.argtypes = [p, u32, ctypes.POINTER(ctypes.c_char_p), pu64,
                                     ctypes.POINTER(ctypes.c_double)]
@@ -75,6 +76,10 @@ def load(path: str | None = None):
     lib.lc_server_create.argtypes = [u64, u32, ctypes.POINTER(p)]
     lib.lc_server_submit.argtypes = [p, u32, p, p, u64, u64, p, pu64]
     lib.lc_server_wait.argtypes = [p, u64, ctypes.c_double, pu32, ctypes.POINTER(ctypes.c_double)]
+    lib.lc_server_result.argtypes = [p, u64, ctypes.c_double, pu32, ctypes.POINTER(ctypes.c_double),
+                                     pu64, pu64, u32]
+    lib.lc_server_cancel.argtypes = [p, u64]
+    lib.lc_fail_alloc.argtypes = [u64]
     lib.lc_server_stats.argtypes = [p, pu64, pu64, pu64]
     lib.lc_server_destroy.argtypes = [p]
     for name in EXPORTED:
@@ -174,6 +179,12 @@ def lc_last_stats(ctx: int, cap: int = 1024) -> tuple[list[int], list[int]]:
     _check(load().lc_last_stats(ctx, ctypes.byref(R), mp, em, cap), "lc_last_stats")
     r = min(R.value, cap)
     return list(mp[:r]), list(em[:r])
+
+
+def lc_dedup_fallbacks(ctx: int) -> int:
+    c = ctypes.c_uint64()
+    _check(load().lc_dedup_fallbacks(ctx, ctypes.byref(c)), "lc_dedup_fallbacks")
+    return int(c.value)
 
 
 def lc_profile(ctx: int, on: bool) -> None:
@@ -355,6 +366,9 @@ class BatchLocalContraction:
         rounds, n_i, m_i = lc_batch_run(self.ctx, self.k, _dev_ptr(labels, total, "labels"), cap)
         return labels, rounds, n_i, m_i
 
+    def set_param(self, name: str, value: int) -> None:
+        lc_set_param(self.ctx, name, value)
+
     def close(self) -> None:
         if getattr(self, "ctx", None):
             lc_destroy(self.ctx)
@@ -405,6 +419,25 @@ class Server:
         _check(st, "lc_server_wait")
         return h_labels[:n], int(R.value), float(lat.value)
 
+    def result(self, job: int, timeout_s: float = 0.0, cap: int = 1024):
+        """wait() plus the job's per-phase sizes: (labels, Result, latency_s)."""
+        R = ctypes.c_uint32()
+        lat = ctypes.c_double()
+        n_i = (ctypes.c_uint64 * cap)()
+        m_i = (ctypes.c_uint64 * cap)()
+        st = load().lc_server_result(self.srv, job, timeout_s, ctypes.byref(R), ctypes.byref(lat),
+                                     n_i, m_i, cap)
+        if st == LC_ERR_TIMEOUT:
+            raise LCError(st, "lc_server_result")
+        h_src, h_dst, h_labels, n = self._held.pop(job)
+        _check(st, "lc_server_result")
+        r = int(R.value)
+        return h_labels[:n], Result(r, list(n_i[:r]), list(m_i[:r])), float(lat.value)
+
+    def cancel(self, job: int) -> bool:
+        """True if the job will end cancelled; False if it is unknown or too far along."""
+        return load().lc_server_cancel(self.srv, job) == LC_OK
+
     def stats(self) -> dict:
         c, p, b = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
         _check(load().lc_server_stats(self.srv, ctypes.byref(c), ctypes.byref(p), ctypes.byref(b)),
@@ -421,6 +454,11 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def fail_alloc(k: int) -> None:
+    """Test hook: the k-th library allocation from now fails (0: off)."""
+    _check(load().lc_fail_alloc(k), "lc_fail_alloc")
 
 
 def connected_components(n: int, src, dst, seed: int = 0, stream=None):

@@ -1,4 +1,4 @@
-"""Seeded synthetic inputs shaped like the paper's workloads (Section 7, Table 1).
+"""Seeded synthetic inputs shaped like the paper's workloads (Section 6, Empirical study, Table 1).
 
 The paper evaluates on social and web graphs (Orkut, Friendster, Clueweb and two
 non-public graphs) that are not available here; these generators stand in for

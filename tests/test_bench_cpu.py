@@ -21,21 +21,41 @@ def test_reference_arm_prints_one_json_line():
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == bench.UNIT
     assert d["value"] > 0 and d["higher_is_better"] is True
-    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == 1
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["nproc"] >= 1 and cb["cpu_model"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
 
 
-def test_algorithmic_bytes_accounting():
-    n_i, m_i = [1000, 100, 10], [8000, 500, 20]
-    mp_i, em_i, kept_i, passes_i = [7000, 400, 15], [6000, 380, 15], [6000, 380, 15], [1, 0, 0]
-    per = bench.algorithmic_bytes(n_i, m_i, mp_i, em_i, kept_i, passes_i, 1, False)
-    # phase 0 reads its 8-byte edges in the minimum and the relabel
-    assert per["edge_min_soa"] == 8 * 8000 + 8 * 1000
-    assert per["relabel_soa"] == 8 * 8000 + 8 * 6000 + 4 * 1000
-    # one partition pass over the kept keys of phase 0 only
-    assert per["sort_pass"] == 16 * 6000
-    assert "filter_hll" not in per  # no phase reaches the late-planning size
-    assert all(v >= 0 for v in per.values())
+def test_step_bytes_accounting():
+    """Each step counts its edges once per phase, whatever the launch
+    structure; the steps add up to the path total."""
+    n_i, m_i, mp_i = [1000, 100, 10], [8000, 500, 20], [7000, 400, 15]
+    sb = bench.step_bytes(n_i, m_i, mp_i)
+    assert sb["parent"] == sum(8 * m + 8 * n for n, m in zip(n_i, m_i))
+    assert sb["relabel"] == sum(8 * m + 8 * p + 4 * n for n, m, p in zip(n_i, m_i, mp_i))
+    assert sb["dedup"] == 16 * sum(mp_i)
+    assert sb["compact"] == 8 * (500 + 20) + 4 * sum(n_i)
+    assert sb["labels"] == 8 * sum(n_i) + 8 * 1000
     total = bench.path_bytes(n_i, m_i, mp_i)
-    assert total > per["relabel_soa"]
+    assert total == sum(sb.values())
+    # the survey's per-phase figure: 16 m + 24 m' + 8 m_next + 28 n, plus the labels
+    assert total == sum(16 * m + 24 * p + 28 * n for n, m, p in zip(n_i, m_i, mp_i)) + \
+        8 * (500 + 20) + 8 * sum(n_i) + 8 * 1000
     assert bench.variant_path_bytes(1, 0, n_i, m_i, mp_i) > total  # two-hop adds an edge pass
+
+
+def test_step_report_and_roofline():
+    """The dominant step's fraction is recomputable from the reported bytes
+    and times."""
+    n_i, m_i, mp_i = [1000, 100], [8000, 500], [7000, 400]
+    kstats = {"edge_min_packed": (4, 2.0), "bucket_edges": (6, 1.0), "relabel_packed": (4, 6.0),
+              "sort_pass": (2, 1.0), "jump": (4, 0.4)}
+    steps = bench.step_report(kstats, 2, n_i, m_i, mp_i, 1000.0, "measured")
+    assert abs(steps["parent"]["ms"] - 1.5) < 1e-12
+    roof = bench.roofline_of(steps, 1000.0, "measured", "x")
+    assert roof["step"] == "relabel"
+    ach = steps["relabel"]["algorithmic_bytes"] / (3.0 / 1e3) / 1e9
+    assert abs(roof["achieved"] - ach) < 1e-9 and abs(roof["frac"] - ach / 1000.0) < 1e-12
+    assert roof["traffic"] is None  # no capture recorded for these sources
+    for names in bench.STEP_KERNELS.values():
+        assert len(names) == len(set(names))

@@ -121,3 +121,59 @@ def test_context_on_nonblocking_stream(lc_lib, cuda):
             c.close()
             assert res.rounds == ref.rounds
             assert np.array_equal(labels.cpu().numpy().view(np.uint32), ref.labels)
+
+
+def test_config_sized_mix_sizes_match_oracle(lc_lib, cuda):
+    """Jobs of the serving workload's largest sizes (n up to 2^20, up to 2^23
+    edges: their large phases take the filter, distinct-count estimate and
+    segmented deduplication inside the server) mixed with small ones; every
+    job's labels, phase count and per-phase (n_i, m_i) equal the oracle's."""
+    big = []
+    s, d = synth.rmat(20, 1 << 23, 909, 910)
+    big.append(synth.Graph(1 << 20, s, d, "rmat20", seed=11))
+    s, d = synth.er(1 << 20, 1 << 22, 911)
+    big.append(synth.Graph(1 << 20, s, d, "er20", seed=12))
+    s, d = synth.grid(1024, 1024)
+    synth.permute_ids(s, 1 << 20, 913)
+    synth.permute_ids(d, 1 << 20, 913)
+    big.append(synth.Graph(1 << 20, s, d, "grid1024", seed=13))
+    small = [r.graph for r in requests(12, seed=71, lo=8, hi=14)]
+    jobs = big + small
+    srv = lc.Server(slots=8)
+    ids = [srv.submit(g.n, g.src, g.dst, g.seed) for g in jobs]
+    out = [srv.result(j) for j in ids]
+    srv.close()
+    for g, (labels, res, lat) in zip(jobs, out):
+        ref = oracle.lc_run(g.n, g.src, g.dst, g.seed)
+        assert res.rounds == ref.rounds, g.name
+        assert list(zip(res.n_i, res.m_i)) == ref.sizes(), g.name
+        assert np.array_equal(labels, ref.labels), g.name
+
+
+def test_cancel_queued_and_running_jobs(lc_lib, cuda):
+    """One slot: a cancelled queued job ends LC_ERR_CANCELLED at once; a
+    running one stops at a phase boundary (or completes if it was already
+    copying its labels out); the other jobs and later ones are unaffected."""
+    g = synth.workload("rmat18")
+    small = [r.graph for r in requests(4, seed=83, lo=8, hi=12)]
+    srv = lc.Server(slots=1)
+    a = srv.submit(g.n, g.src, g.dst, g.seed)
+    b = srv.submit(small[0].n, small[0].src, small[0].dst, small[0].seed)
+    c = srv.submit(small[1].n, small[1].src, small[1].dst, small[1].seed)
+    assert srv.cancel(c)
+    srv.cancel(a)
+    with pytest.raises(lc.LCError) as ei:
+        srv.wait(c)
+    assert ei.value.code == lc.LC_ERR_CANCELLED
+    try:
+        labels, rounds, _ = srv.wait(a)
+        ref = oracle.lc_run(g.n, g.src, g.dst, g.seed)
+        assert rounds == ref.rounds and np.array_equal(labels, ref.labels)
+    except lc.LCError as e:
+        assert e.code == lc.LC_ERR_CANCELLED
+    assert not srv.cancel(12345)
+    for gg, j in [(small[0], b)] + [(x, srv.submit(x.n, x.src, x.dst, x.seed)) for x in small[2:]]:
+        labels, rounds, _ = srv.wait(j)
+        ref = oracle.lc_run(gg.n, gg.src, gg.dst, gg.seed)
+        assert rounds == ref.rounds and np.array_equal(labels, ref.labels)
+    srv.close()

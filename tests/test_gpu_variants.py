@@ -1,6 +1,6 @@
 """The other phase variants on the GPU against the oracle: the published
 two-hop LocalContraction label, TreeContraction, and the union-find finish of
-small graphs (Section 3 and Section 7).  Labels, phase count, every per-phase
+small graphs (Section 3 and Section 6, Empirical study).  Labels, phase count, every per-phase
 (n_i, m_i) and m'_i bit-exact, single graphs and batches."""
 import numpy as np
 import pytest
