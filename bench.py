@@ -422,7 +422,8 @@ def bench_batch(dev, stream, steps=5, k=4096, world=1, rank=0, barrier=None, red
 SERVING_RATES = (100.0, 300.0, 1000.0, 3000.0, 10000.0, 20000.0)
 
 
-def bench_serving(rates=SERVING_RATES, requests=1000, pool=200, slots=32, serial_max_s=20.0):
+def bench_serving(rates=SERVING_RATES, requests=1000, pool=200, slots=32, serial_max_s=20.0,
+                  world=1, rank=0, barrier=None, gather=None):
     """Config 5: Poisson arrivals of CC requests (ER / R-MAT / permuted grid,
     n log-uniform in [2^10, 2^22], average degree 4-32) served by the
     continuous-batching loop vs the serial plain path (one request at a time,
@@ -430,16 +431,22 @@ def bench_serving(rates=SERVING_RATES, requests=1000, pool=200, slots=32, serial
     Each rate point replays `requests` arrivals drawn cyclically from a pool
     of `pool` generated graphs (host memory bounds the distinct graphs); the
     serial path is measured at every rate it can sustain, up to serial_max_s
-    of arrivals."""
+    of arrivals.  With several ranks every rank sees the same arrival
+    sequence, routes it with shard.Router (no collective on the data path)
+    and serves its own requests on its own GPU; the latencies are gathered
+    on rank 0 after each rate point."""
     import threading
 
-    from paper_1807_10727_gb300 import lc, synth
+    from paper_1807_10727_gb300 import lc, shard, synth
     reqs = synth.serving_stream(1000.0, pool)
     log("serving: %d distinct requests generated" % pool)
     edges = int(sum(r.graph.m for r in reqs))
     # unit-rate Poisson arrival offsets, shared by every rate point
     u = synth.uniforms(515, requests)
     base = np.cumsum(-np.log1p(-u))
+    owner = shard.route_stream([reqs[k % pool].graph.m + reqs[k % pool].graph.n
+                                for k in range(requests)], world)
+    mine = [k for k in range(requests) if owner[k] == rank]
 
     def summarize(lat, t_first, t_last):
         lat = np.asarray(lat)
@@ -449,21 +456,23 @@ def bench_serving(rates=SERVING_RATES, requests=1000, pool=200, slots=32, serial
 
     out = {"workload": "%d arrivals per rate over %d distinct requests (ER/R-MAT/grid, n in "
                        "[2^10, 2^22], degree 4-32, %d edges in the pool)" % (requests, pool, edges),
-           "slots": slots, "rates": [], "serial": []}
+           "slots": slots, "ranks": world, "rates": [], "serial": []}
     srv = lc.Server(slots=slots)
     warm = [srv.submit(r.graph.n, r.graph.src, r.graph.dst, r.graph.seed) for r in reqs[:8]]
     for j in warm:
         srv.wait(j)
     for rate in rates:
         arr = base / rate
-        ids = [None] * requests
+        ids = {}
         ready = threading.Semaphore(0)
-        t0 = time.perf_counter() + 0.05
+        if barrier:
+            barrier()
+        t0 = time.time() + 0.05  # wall clock: the same arrival instants on every rank
 
         def producer():
-            for k in range(requests):
+            for k in mine:
                 r = reqs[k % pool]
-                d = t0 + arr[k] - time.perf_counter()
+                d = t0 + arr[k] - time.time()
                 if d > 0:
                     time.sleep(d)
                 ids[k] = srv.submit(r.graph.n, r.graph.src, r.graph.dst, r.graph.seed)
@@ -472,13 +481,19 @@ def bench_serving(rates=SERVING_RATES, requests=1000, pool=200, slots=32, serial
         th = threading.Thread(target=producer)
         th.start()
         lat, t_last = [], t0
-        for k in range(requests):
+        for k in mine:
             if not ready.acquire(timeout=300):
                 raise RuntimeError("serving: request %d was not submitted within 300 s" % k)
             _, _, l = srv.wait(ids[k], timeout_s=300.0)
             lat.append(l)
             t_last = max(t_last, t0 + arr[k] + l)
         th.join()
+        if gather is not None and world > 1:
+            parts = gather((lat, t_last))
+            if rank != 0:
+                continue
+            lat = [x for p in parts for x in p[0]]
+            t_last = max(p[1] for p in parts)
         row = summarize(lat, t0, t_last)
         row["rate_req_s"] = rate
         row["saturated"] = row["graphs_per_s"] < 0.9 * rate
@@ -487,8 +502,12 @@ def bench_serving(rates=SERVING_RATES, requests=1000, pool=200, slots=32, serial
             rate, row["graphs_per_s"], row["latency_ms_p50"], row["latency_ms_p99"]))
     out["peak_active"] = srv.stats()["peak_active"]
     srv.close()
+    if rank != 0:
+        return None
     sat = [r["rate_req_s"] for r in out["rates"] if r["saturated"]]
     out["saturation_req_s"] = min(sat) if sat else None
+    if world > 1:
+        return out
     # serial plain path: every rate up to the first one it cannot sustain
     for rate in rates:
         n_req = int(min(requests, max(50, serial_max_s * rate)))
@@ -708,10 +727,19 @@ def main():
         log("batched: %.0f graphs/s (one run per graph: %s graphs/s)" % (
             batched["batched_graphs_per_s"], batched.get("per_graph_graphs_per_s")))
     serving = None
-    if rank == 0 and not args.no_serving:
+    if not args.no_serving:
         torch.cuda.empty_cache()
-        serving = bench_serving()
-        log("serving: saturation %s req/s" % serving["saturation_req_s"])
+
+        def gather(obj):
+            if world == 1:
+                return [obj]
+            parts = [None] * world
+            dist.all_gather_object(parts, obj)
+            return parts
+
+        serving = bench_serving(world=world, rank=rank, barrier=barrier, gather=gather)
+        if rank == 0:
+            log("serving: saturation %s req/s" % serving["saturation_req_s"])
 
     if rank == 0:
         line = {

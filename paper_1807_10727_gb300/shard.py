@@ -5,7 +5,10 @@ min-reduce for the parents, pointer exchanges, an all-to-all shuffle of the
 relabelled edges), so it runs as replicas, one per rank.  Batches of
 independent graphs and serving streams shard without any data-path
 collective: each rank takes a size-balanced share of the graphs and only the
-per-rank results are gathered.
+per-rank results are gathered.  A batch is split up front (balance); a
+serving stream is routed request by request (Router), by a rule every rank
+evaluates identically on the same arrival sequence, so no rank has to tell
+another which requests it took.
 """
 from __future__ import annotations
 
@@ -48,3 +51,26 @@ def sub_batch(n, eoff, src, dst, seeds, idx):
     sd = np.concatenate([dst[int(eoff[g]):int(eoff[g + 1])] for g in idx]) if idx else \
         np.zeros(0, np.uint32)
     return sn, se, ss.astype(np.uint32), sd.astype(np.uint32), np.asarray(seeds)[idx]
+
+
+class Router:
+    """Online form of `balance` for a request stream: request k goes to the
+    rank with the least work routed so far (ties to the lowest rank).  Every
+    rank runs the same router over the same sequence of request sizes and
+    serves only the requests routed to itself."""
+
+    def __init__(self, world: int):
+        if world < 1:
+            raise ValueError("world must be >= 1")
+        self.load = [0.0] * world
+
+    def route(self, work: float) -> int:
+        r = min(range(len(self.load)), key=lambda q: (self.load[q], q))
+        self.load[r] += float(work)
+        return r
+
+
+def route_stream(works, world: int) -> list[int]:
+    """Rank of every request of a stream (Router applied in arrival order)."""
+    rt = Router(world)
+    return [rt.route(w) for w in works]

@@ -1,6 +1,8 @@
 """Multi-rank host path (CPU, gloo, world size 2): graphs of a batch are
-shared out by size, each rank processes its share, results gathered on rank 0
-cover every graph exactly once and agree with the oracle."""
+shared out by size, and the requests of a serving stream are routed online;
+each rank processes its share, results gathered on rank 0 cover every graph
+exactly once and agree with the oracle.  (On CPU the oracle stands in for
+each rank's GPU; the sharding and routing code is the product's.)"""
 import os
 import socket
 
@@ -75,6 +77,60 @@ def test_two_rank_sharded_batch():
     q = ctx.Queue()
     port = _free_port()
     procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(120)
+        assert p.exitcode == 0
+    assert q.get(timeout=10) is True
+
+
+def test_router_matches_offline_rule_and_balances():
+    rng = np.random.default_rng(5)
+    work = rng.pareto(1.2, 500) + 1
+    for world in (1, 2, 4):
+        ranks = shard.route_stream(work, world)
+        assert len(ranks) == len(work) and set(ranks) <= set(range(world))
+        loads = np.bincount(ranks, weights=work, minlength=world)
+        # online greedy: no rank exceeds another by more than the largest request
+        assert loads.max() - loads.min() <= work.max() + 1e-9
+        assert shard.route_stream(work, world) == ranks  # deterministic on every rank
+
+
+def _serve_worker(rank, world, port, q):
+    import oracle
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    reqs = synth.serving_stream(1000.0, 20, lo_exp=6, hi_exp=11, seed=29)
+    ranks = shard.route_stream([r.graph.m + r.graph.n for r in reqs], world)
+    results = {}
+    for r, owner in zip(reqs, ranks):
+        if owner != rank:
+            continue
+        g = r.graph
+        out = oracle.lc_run(g.n, g.src, g.dst, g.seed)
+        results[r.rid] = (out.rounds, out.labels.tolist())
+    gathered = [None] * world if rank == 0 else None
+    dist.gather_object(results, gathered, dst=0)
+    if rank == 0:
+        allres = {}
+        for part in gathered:
+            for k, v in part.items():
+                assert k not in allres
+                allres[k] = v
+        ok = sorted(allres) == [r.rid for r in reqs] and len(gathered[1]) > 0
+        for r in reqs:
+            ref = oracle.lc_run(r.graph.n, r.graph.src, r.graph.dst, r.graph.seed)
+            ok = ok and allres[r.rid] == (ref.rounds, ref.labels.tolist())
+        q.put(ok)
+    dist.destroy_process_group()
+
+
+def test_two_rank_routed_serving_stream():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_serve_worker, args=(r, 2, port, q)) for r in range(2)]
     for p in procs:
         p.start()
     for p in procs:
