@@ -372,24 +372,31 @@ def bench_batch(dev, stream, steps=5, k=4096, world=1, rank=0, barrier=None, red
     dst = torch.from_numpy(b.dst.view(np.int32)).to(dev)
     total = int(b.n.astype(np.int64).sum())
     labels = torch.empty(max(total, 1), dtype=torch.int32, device=dev)
-    bl = lc.BatchLocalContraction(b.n, b.eoff, src, dst, b.seeds, stream=stream)
-    for _ in range(2):
-        bl.run(labels)
-    torch.cuda.synchronize(dev)
-    if barrier:
-        barrier()
-    t0 = time.perf_counter()
-    for _ in range(steps):
-        _, rounds, _, _ = bl.run(labels)
-    torch.cuda.synchronize(dev)
-    batched_s = (time.perf_counter() - t0) / steps
-    if reduce_max:
-        batched_s = reduce_max(batched_s)
-    bl.close()
+    def time_batch(tuned):
+        bl = lc.BatchLocalContraction(b.n, b.eoff, src, dst, b.seeds, stream=stream, tuned=tuned)
+        for _ in range(2):
+            bl.run(labels)
+        torch.cuda.synchronize(dev)
+        if barrier:
+            barrier()
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            _, rounds, _, _ = bl.run(labels)
+        torch.cuda.synchronize(dev)
+        sec = (time.perf_counter() - t0) / steps
+        if reduce_max:
+            sec = reduce_max(sec)
+        params = dict(bl.params)
+        bl.close()
+        return sec, rounds, params
+
+    batched_s, rounds, params = time_batch(True)
+    default_s = time_batch(False)[0] if params else batched_s
     workload = "4096 graphs, n log-uniform [2^6, 2^16], ER deg 4 / R-MAT deg 16"
     if world > 1:
         return {"workload": workload, "graphs": k, "ranks": world, "graphs_this_rank": k_mine,
-                "batched_graphs_per_s": k / batched_s, "batched_ms": batched_s * 1e3}
+                "batched_graphs_per_s": k / batched_s, "batched_ms": batched_s * 1e3,
+                "tuned_params": params, "default_params_ms": default_s * 1e3}
     # one context and one lc_run per graph
     voff = np.concatenate([[0], np.cumsum(b.n.astype(np.int64))])
     ctxs = []
@@ -413,6 +420,7 @@ def bench_batch(dev, stream, steps=5, k=4096, world=1, rank=0, barrier=None, red
     return {"workload": workload, "graphs": k, "vertices": total, "edges": int(b.eoff[-1]),
             "max_rounds": int(rounds.max()),
             "batched_graphs_per_s": k / batched_s, "batched_ms": batched_s * 1e3,
+            "tuned_params": params, "default_params_ms": default_s * 1e3,
             "per_graph_graphs_per_s": k / serial_s, "per_graph_ms_total": serial_s * 1e3,
             "per_graph_latency_ms_p50": float(np.percentile(lat, 50) * 1e3),
             "per_graph_latency_ms_p99": float(np.percentile(lat, 99) * 1e3),
@@ -628,7 +636,7 @@ def main():
     dst = torch.from_numpy(g.dst.view(np.int32)).to(dev)
     labels = torch.empty(g.n, dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream(dev)
-    ctx = lc.LocalContraction(g.n, src, dst, seed=g.seed, stream=stream)
+    ctx = lc.LocalContraction(g.n, src, dst, seed=g.seed, stream=stream, tuned=not args.param)
     for kv in args.param:
         name, value = kv.split("=", 1)
         ctx.set_param(name, int(value))
@@ -676,6 +684,15 @@ def main():
     pb = path_bytes(res.n_i, res.m_i, mp)
     path_roof = {"bytes_per_step": pb, "achieved": pb / (ms / 1e3) / 1e9, "peak": peak,
                  "unit": "GB/s", "frac": pb / (ms / 1e3) / 1e9 / peak, "peak_kind": peak_kind}
+    # the autotuner's parameters against the library's fixed defaults
+    tuning = {"applied": dict(ctx.params), "tuned_ms_per_step": ms}
+    if ctx.params and not args.param:
+        dctx = lc.LocalContraction(g.n, src, dst, seed=g.seed, stream=stream, tuned=False)
+        for _ in range(warmup):
+            dctx.run(labels)
+        tuning["default_ms_per_step"] = time_steps(dctx, labels, stream, args.steps)
+        dctx.close()
+        log("tuning: %.2f ms tuned vs %.2f ms defaults" % (ms, tuning["default_ms_per_step"]))
 
     variants = None
     if rank == 0 and not args.no_variants:
@@ -751,7 +768,7 @@ def main():
                        "rounds": res.rounds, "parallelism": "replicas" if world > 1 else "single",
                        "params": args.param,
                        "l2": "inputs (8 B/edge) larger than L2; no flush"},
-            "roofline": roof, "path_roofline": path_roof, "steps": steps,
+            "roofline": roof, "path_roofline": path_roof, "steps": steps, "tuning": tuning,
             "profiled_ms_per_step": prof_ms,
             "e2e": e2e, "cpu_baseline": cpu, "gpu_launches": launches, "configs": configs,
             "batched": batched, "serving": serving, "variants": variants,

@@ -19,11 +19,13 @@ namespace {
 constexpr unsigned kFull = 0xFFFFFFFFu;
 constexpr int kWarps = kSortThreads / 32;
 
-// Exclusive block scan of one value per thread (kSortThreads threads).
-// `ws` must hold kWarps words; the call ends with a barrier so `ws` can be
-// reused afterwards.
+// Exclusive block scan of one value per thread (kThreadsT threads, at most
+// 1024).  `ws` must hold kThreadsT / 32 words; the call ends with a barrier
+// so `ws` can be reused afterwards.
+template <int kThreadsT = kSortThreads>
 __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* ws,
                                                          uint32_t* total) {
+  constexpr int kWarps = kThreadsT / 32;
   const unsigned lane = lane_id(), w = threadIdx.x >> 5;
   uint32_t x = v;
 #pragma unroll
@@ -848,10 +850,12 @@ __global__ void __launch_bounds__(kSortThreads) k_bucket_scatter(
 
 // ------------------------------------------------ segmented deduplication
 
+constexpr int kSegFilterThreads = 512;
 constexpr int kSegFilterItems = 8;
-constexpr int kSegFilterTile = kSortThreads * kSegFilterItems;
-constexpr int kSegInsItems = 8;
-constexpr int kSegInsTile = kSortThreads * kSegInsItems;
+constexpr int kSegFilterTile = kSegFilterThreads * kSegFilterItems;
+constexpr int kSegInsThreads = 512;
+constexpr int kSegInsItems = 4;
+constexpr int kSegInsTile = kSegInsThreads * kSegInsItems;
 
 __device__ __forceinline__ uint32_t seg_of(uint64_t y) { return (uint32_t)(y >> (64 - kSegBits)); }
 
@@ -872,18 +876,18 @@ __global__ void __launch_bounds__(kSortThreads) k_seg_starts(uint32_t* scratch) 
 // keys are ranked per segment in shared memory, each segment's share is
 // reserved with one atomicAdd on its fill counter, and the tile is staged in
 // segment order and written out in runs.
-__global__ void __launch_bounds__(kSortThreads) k_filter_seg(
+__global__ void __launch_bounds__(kSegFilterThreads) k_filter_seg(
     const uint64_t* __restrict__ in, const unsigned long long* d_in, uint64_t* __restrict__ out,
     uint64_t cap, unsigned long long* d_out, unsigned long long* gcache, uint32_t gmask, int admit,
     uint32_t* __restrict__ ghll, uint32_t* scratch, unsigned* err) {
   __shared__ uint32_t reg[kHllRegs];
   __shared__ uint64_t stage[kSegFilterTile];
   __shared__ uint32_t s_cnt[kSegs], s_off[kSegs], s_gb[kSegs];
-  __shared__ uint32_t ws[kWarps];
+  __shared__ uint32_t ws[kSegFilterThreads / 32];
   const unsigned tid = threadIdx.x, lane = lane_id(), w = tid >> 5;
   uint32_t* fill = scratch + kBucketMaxDigits;
-  for (int i = tid; i < kHllRegs; i += kSortThreads) reg[i] = 0;
-  s_cnt[tid] = 0;
+  for (int i = tid; i < kHllRegs; i += kSegFilterThreads) reg[i] = 0;
+  if (tid < kSegs) s_cnt[tid] = 0;
   __syncthreads();
   const uint64_t count = *d_in;
   const uint64_t tiles = (count + kSegFilterTile - 1) / kSegFilterTile;
@@ -919,11 +923,13 @@ __global__ void __launch_bounds__(kSortThreads) k_filter_seg(
       dr[i] = (d << 16) | atomicAdd(&s_cnt[d], 1u);
     }
     __syncthreads();
-    const uint32_t c = s_cnt[tid];
+    const uint32_t c = tid < kSegs ? s_cnt[tid] : 0u;
     uint32_t tot;
-    const uint32_t e = block_exclusive_scan(c, ws, &tot);
-    s_off[tid] = e;
-    if (c) s_gb[tid] = atomicAdd(&fill[tid * kBucketFillStride], c);
+    const uint32_t e = block_exclusive_scan<kSegFilterThreads>(c, ws, &tot);
+    if (tid < kSegs) {
+      s_off[tid] = e;
+      if (c) s_gb[tid] = atomicAdd(&fill[tid * kBucketFillStride], c);
+    }
     kept_total += tot;
     __syncthreads();
 #pragma unroll
@@ -934,18 +940,18 @@ __global__ void __launch_bounds__(kSortThreads) k_filter_seg(
       }
     }
     __syncthreads();
-    for (uint32_t j = tid; j < tot; j += kSortThreads) {
+    for (uint32_t j = tid; j < tot; j += kSegFilterThreads) {
       const uint64_t x = stage[j];
       const uint32_t d = seg_of(x);
       const uint64_t pos = (uint64_t)s_gb[d] + (j - s_off[d]);
       if (index_ok(err, kKSegDedup, pos, cap)) __stcg(out + pos, x);
     }
     __syncthreads();
-    s_cnt[tid] = 0;
+    if (tid < kSegs) s_cnt[tid] = 0;
     __syncthreads();
   }
   if (tid == 0 && kept_total) atomicAdd(d_out, kept_total);
-  for (int i = tid; i < kHllRegs; i += kSortThreads)
+  for (int i = tid; i < kHllRegs; i += kSegFilterThreads)
     if (reg[i]) atomicMax(&ghll[i], reg[i]);
 }
 
@@ -962,15 +968,19 @@ __global__ void __launch_bounds__(kSortThreads) k_seg_tiles(uint32_t* scratch) {
   if (s == 0) scratch[kSegTileOff + kSegs] = total;
 }
 
-// Distinct keys of segments [seg_lo, seg_hi): tiles claimed in order by
-// ticket; a key probes its segment's slice (slots entries, linear probing
-// from its low bits) with a read through L2 and, on an empty slot, a
-// compare-and-swap.  Slots only ever change from empty to a key, so a read
-// that returns the key itself settles the probe, and a stale empty only
-// costs the compare-and-swap.  Keys new to the table are staged per tile,
-// appended to `out` with one atomicAdd per tile, and both endpoints of each
-// are marked in flags.  A slice that fills up raises kErrOverflow.
-__global__ void __launch_bounds__(kSortThreads) k_seg_insert(
+// Distinct keys of segments [seg_lo, seg_hi): tiles are claimed in order by
+// ticket, so the tiles in flight stay within a segment or two; a key probes
+// its segment's slice (slots entries, linear probing from its low bits) with
+// a read through L2 and, on an empty slot, a compare-and-swap.  Slots only
+// ever change from empty to a key, so a read that returns the key itself
+// settles the probe, and a stale empty only costs the compare-and-swap.  A
+// thread's keys probe in rounds: every round issues the pending keys' reads
+// together, then their compare-and-swaps together, so their latencies
+// overlap.  Keys new to the table are staged per tile (one shared-memory
+// reservation per warp and item), appended to `out` with one atomicAdd per
+// tile, and both endpoints of each are marked in flags.  A slice that fills
+// up raises kErrOverflow.
+__global__ void __launch_bounds__(kSegInsThreads) k_seg_insert(
     const uint64_t* __restrict__ keys, const uint32_t* __restrict__ scratch, uint32_t seg_lo,
     uint32_t seg_hi, uint64_t slots, unsigned long long* table, uint64_t* __restrict__ out,
     uint64_t cap, unsigned long long* m_next, uint8_t* flags, uint32_t n, int half_bits,
@@ -978,13 +988,14 @@ __global__ void __launch_bounds__(kSortThreads) k_seg_insert(
   __shared__ uint64_t fresh[kSegInsTile];
   __shared__ uint32_t s_new, s_t;
   __shared__ unsigned long long s_base;
-  const unsigned tid = threadIdx.x;
+  const unsigned tid = threadIdx.x, lane = lane_id();
+  const unsigned lt = lanemask_lt();
   const uint32_t* tiles = scratch + kSegTileOff;
   const uint32_t* starts = scratch + kSegStartOff;
   const uint32_t* fill = scratch + kBucketMaxDigits;
   const uint32_t t0 = tiles[seg_lo], t1 = tiles[seg_hi];
   const uint64_t half_mask = (1ull << half_bits) - 1;
-  const uint64_t smask = slots - 1;
+  const uint32_t smask = (uint32_t)(slots - 1);
   if (tid == 0) s_new = 0;
   for (;;) {
     if (tid == 0) s_t = t0 + atomicAdd(ticket, 1u);
@@ -1003,43 +1014,66 @@ __global__ void __launch_bounds__(kSortThreads) k_seg_insert(
     const uint64_t ke = fill[sg * kBucketFillStride];
     unsigned long long* slice = table + (uint64_t)(sg - seg_lo) * slots;
     uint64_t k[kSegInsItems];
+    uint32_t slot[kSegInsItems];
+    uint32_t pending = 0, fresh_mask = 0;
 #pragma unroll
     for (int i = 0; i < kSegInsItems; ++i) {
-      const uint64_t j = kb + (uint64_t)i * kSortThreads + tid;
+      const uint64_t j = kb + (uint64_t)i * kSegInsThreads + tid;
       k[i] = (j < ke && j < cap) ? __ldcs(keys + j) : kEmpty;
+      slot[i] = (uint32_t)k[i] & smask;
+      if (k[i] != kEmpty) pending |= 1u << i;
     }
+    for (uint64_t probe = 0; pending != 0; ++probe) {
+      if (probe >= slots) {
+        atomicOr(err, kErrOverflow);
+        break;
+      }
+      unsigned long long cur[kSegInsItems];
+#pragma unroll
+      for (int i = 0; i < kSegInsItems; ++i)
+        cur[i] = ((pending >> i) & 1u) ? __ldcg(slice + slot[i]) : 0ull;
+      uint32_t want = 0;
+#pragma unroll
+      for (int i = 0; i < kSegInsItems; ++i) {
+        if (!((pending >> i) & 1u)) continue;
+        if (cur[i] == k[i]) pending &= ~(1u << i);  // already in the table
+        else if (cur[i] == kEmpty) want |= 1u << i;
+      }
+#pragma unroll
+      for (int i = 0; i < kSegInsItems; ++i)
+        cur[i] = ((want >> i) & 1u) ? atomicCAS(slice + slot[i], kEmpty, k[i]) : 0ull;
+#pragma unroll
+      for (int i = 0; i < kSegInsItems; ++i) {
+        if (!((pending >> i) & 1u)) continue;
+        if ((want >> i) & 1u) {
+          if (cur[i] == kEmpty) {
+            fresh_mask |= 1u << i;
+            pending &= ~(1u << i);
+            continue;
+          }
+          if (cur[i] == k[i]) {
+            pending &= ~(1u << i);
+            continue;
+          }
+        }
+        slot[i] = (slot[i] + 1) & smask;  // taken by another key: next slot
+      }
+    }
+    // stage the new keys: one shared-memory reservation per warp and item
 #pragma unroll
     for (int i = 0; i < kSegInsItems; ++i) {
-      if (k[i] == kEmpty) continue;
-      uint64_t slot = k[i] & smask;
-      bool done = false;
-      for (uint64_t probe = 0; probe < slots; ++probe) {
-        const unsigned long long cur = __ldcg(slice + slot);
-        if (cur == k[i]) {
-          done = true;
-          break;
-        }
-        if (cur == kEmpty) {
-          const unsigned long long old = atomicCAS(slice + slot, kEmpty, k[i]);
-          if (old == kEmpty) {
-            fresh[atomicAdd(&s_new, 1u)] = k[i];
-            done = true;
-            break;
-          }
-          if (old == k[i]) {
-            done = true;
-            break;
-          }
-        }
-        slot = (slot + 1) & smask;
-      }
-      if (!done) atomicOr(err, kErrOverflow);
+      const unsigned b = __ballot_sync(kFull, (fresh_mask >> i) & 1u);
+      if (b == 0) continue;
+      uint32_t base = 0;
+      if (lane == (unsigned)(__ffs(b) - 1)) base = atomicAdd(&s_new, (uint32_t)__popc(b));
+      base = __shfl_sync(kFull, base, __ffs(b) - 1);
+      if ((fresh_mask >> i) & 1u) fresh[base + __popc(b & lt)] = k[i];
     }
     __syncthreads();
     const uint32_t nn = s_new;
     if (tid == 0) s_base = nn ? atomicAdd(m_next, (unsigned long long)nn) : 0ull;
     __syncthreads();
-    for (uint32_t e = tid; e < nn; e += kSortThreads) {
+    for (uint32_t e = tid; e < nn; e += kSegInsThreads) {
       const uint64_t v = fresh[e];
       const uint64_t pos = s_base + e;
       if (index_ok(err, kKSegDedup, pos, cap)) out[pos] = v;
@@ -1127,14 +1161,14 @@ void filter_seg(const uint64_t* in, const unsigned long long* d_in, uint64_t max
                 const Launch& L) {
   if (max_count == 0) return;
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_filter_seg, kSortThreads, 0) !=
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_filter_seg, kSegFilterThreads, 0) !=
           cudaSuccess ||
       per_sm < 1)
     per_sm = 1;
   const int grid = (int)std::min<uint64_t>((max_count + kSegFilterTile - 1) / kSegFilterTile,
                                            (uint64_t)L.sms * per_sm);
   KScope ks(L, kKFilter);
-  k_filter_seg<<<grid, kSortThreads, 0, L.stream>>>(in, d_in, out, max_count, d_out,
+  k_filter_seg<<<grid, kSegFilterThreads, 0, L.stream>>>(in, d_in, out, max_count, d_out,
                                                     gslots ? gcache : nullptr,
                                                     gslots ? gslots - 1 : 0u, admit, hll, scratch,
                                                     err);
@@ -1152,7 +1186,7 @@ bool seg_dedup(const uint64_t* keys, uint32_t* scratch, uint64_t max_count, uint
     k_seg_tiles<<<1, kSortThreads, 0, L.stream>>>(scratch);
   }
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_seg_insert, kSortThreads, 0) !=
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_seg_insert, kSegInsThreads, 0) !=
           cudaSuccess ||
       per_sm < 1)
     per_sm = 1;
@@ -1163,7 +1197,7 @@ bool seg_dedup(const uint64_t* keys, uint32_t* scratch, uint64_t max_count, uint
     cudaMemsetAsync(table, 0xFF, 8ull * slots * (hi - lo), L.stream);
     cudaMemsetAsync(ticket, 0, sizeof(unsigned), L.stream);
     KScope ks(L, kKSegDedup);
-    k_seg_insert<<<grid, kSortThreads, 0, L.stream>>>(
+    k_seg_insert<<<grid, kSegInsThreads, 0, L.stream>>>(
         keys, scratch, lo, hi, slots, reinterpret_cast<unsigned long long*>(table), out,
         max_count, m_next, flags, n, half_bits, ticket, err);
   }

@@ -260,6 +260,20 @@ class Result:
     m_i: list
 
 
+def _apply_tuned(ctx: int, n: int, m: int) -> dict:
+    """Speed parameters measured by the autotuner (tune.py) for the size class
+    nearest to (n, m), set on the context; {} when the table has none."""
+    from . import tune
+    applied = {}
+    for name, value in tune.params_for(n, m).items():
+        try:
+            lc_set_param(ctx, name, int(value))
+            applied[name] = int(value)
+        except LCError:
+            pass  # a value this context cannot take (it changes speed only)
+    return applied
+
+
 class LocalContraction:
     """One graph resident on the device.
 
@@ -270,7 +284,7 @@ class LocalContraction:
 
     def __init__(self, n: int, src=None, dst=None, m: int | None = None, seed: int = 0,
                  stream=None, variant: int = LC_VARIANT_FOREST, finish_edges: int = 0,
-                 dedup: int = LC_DEDUP_HASH, merge_alpha=()):
+                 dedup: int = LC_DEDUP_HASH, merge_alpha=(), tuned: bool = True):
         if src is None:
             if m is None:
                 raise ValueError("m is required when the context owns its inputs")
@@ -290,6 +304,7 @@ class LocalContraction:
             lc_set_dedup(self.ctx, dedup)
         if len(merge_alpha):
             lc_set_merge_to_large(self.ctx, merge_alpha)
+        self.params = _apply_tuned(self.ctx, self.n, self.m) if tuned else {}
 
     def run(self, labels=None, cap: int = 1024):
         import torch
@@ -343,7 +358,8 @@ class BatchLocalContraction:
     32-bit tensors src/dst (local ids); seeds: uint64[k] rank seeds.
     """
 
-    def __init__(self, n, eoff, src, dst, seeds, stream=None, variant: int = LC_VARIANT_FOREST):
+    def __init__(self, n, eoff, src, dst, seeds, stream=None, variant: int = LC_VARIANT_FOREST,
+                 tuned: bool = True):
         self.n = np.ascontiguousarray(n, dtype=np.uint32)
         self.k = int(self.n.shape[0])
         self.eoff = np.ascontiguousarray(eoff, dtype=np.uint64)
@@ -356,6 +372,7 @@ class BatchLocalContraction:
                                    _stream_handle(stream))
         if variant != LC_VARIANT_FOREST:
             lc_configure(self.ctx, variant, 0)
+        self.params = _apply_tuned(self.ctx, int(self.voff[-1]), m) if tuned else {}
 
     def run(self, labels=None, cap: int = 256):
         import torch
