@@ -178,6 +178,10 @@ lc_status lc_set_dedup(lc_ctx* ctx, lc_dedup mode);
  *                   2^22) plan their deduplication after the relabel, below;
  *                   lowering it below the context's edge count allocates the
  *                   buffers those phases use.  Not while a run is in flight.
+ *   "cache_in_relabel"  0 (default) / 1: in segmented phases, whether the
+ *                   device-wide cache is probed by the relabel itself (the
+ *                   filter pass then only sketches and scatters) instead of
+ *                   by the filter pass.
  *   "seg_dedup"     1 (default) / 0: whether those phases deduplicate by
  *                   segments (below) or by the bucket partition.
  *   "table_slots"   cap (a power of two >= 2^14, or 0 = none) on the table slots

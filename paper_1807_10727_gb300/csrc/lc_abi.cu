@@ -297,6 +297,7 @@ struct lc_ctx {
   bool seg_dedup = true;                         // large phases deduplicate by table slices
   uint32_t target_permille = 1000;               // scale of the distinct-key estimate (tests)
   uint64_t late_min_edges = 1ull << 22;          // phases this large plan their dedup late
+  bool cache_in_relabel = false;                 // segmented phases probe the cache in the relabel
 
   uint32_t max_rounds = 0;  // phase cap (0: 64 + 4 log2 n)
   uint32_t last_rounds = 0;
@@ -692,7 +693,7 @@ static lc_status enqueue_phase(lc_ctx* c) {
   if (use_gcache &&
       cudaMemsetAsync(c->gcache, 0xFF, 8ull * c->gcache_slots, c->stream) != cudaSuccess)
     return fail(c, LC_ERR_CUDA);
-  const bool gcache_in_relabel = use_gcache && !late;
+  const bool gcache_in_relabel = use_gcache && (!late || (seg && c->cache_in_relabel));
   relabel(src0, dst0, pk, mi, ni, r.lv.root,
           r.bits, r.keys, &c->ctr->mprime, &c->ctr->emitted, !c->dedup_sort,
           seg ? &splan : (c->dedup_sort || late) ? nullptr : &hplan,
@@ -709,8 +710,9 @@ static lc_status enqueue_phase(lc_ctx* c) {
     if (seg) {
       // kept keys go straight to their segment's region
       seg_begin(c->bucket_scratch, L);
+      const bool fcache = use_gcache && !gcache_in_relabel;
       filter_seg(r.keys, &c->ctr->emitted, mi, r.alt, &c->ctr->filtered,
-                 use_gcache ? c->gcache : nullptr, use_gcache ? c->gcache_slots : 0,
+                 fcache ? c->gcache : nullptr, fcache ? c->gcache_slots : 0,
                  c->gcache_admit, c->d_hll, c->bucket_scratch, err, L);
     } else {
       filter_hll(r.keys, &c->ctr->emitted, mi, r.alt, &c->ctr->filtered,
@@ -1214,6 +1216,11 @@ extern "C" lc_status lc_set_param(lc_ctx* c, const char* name, uint64_t value) {
   if (std::strcmp(name, "inject_lookback_stall") == 0) {
     if (value > 1) return LC_ERR_INVALID;
     c->sort.stall_once = (int)value;
+    return LC_OK;
+  }
+  if (std::strcmp(name, "cache_in_relabel") == 0) {
+    if (value > 1) return LC_ERR_INVALID;
+    c->cache_in_relabel = value != 0;
     return LC_OK;
   }
   if (std::strcmp(name, "seg_dedup") == 0) {

@@ -853,9 +853,8 @@ __global__ void __launch_bounds__(kSortThreads) k_bucket_scatter(
 constexpr int kSegFilterThreads = 512;
 constexpr int kSegFilterItems = 8;
 constexpr int kSegFilterTile = kSegFilterThreads * kSegFilterItems;
-constexpr int kSegInsThreads = 512;
-constexpr int kSegInsItems = 4;
-constexpr int kSegInsTile = kSegInsThreads * kSegInsItems;
+constexpr int kSegInsItems = 8;
+constexpr int kSegInsTile = kSortThreads * kSegInsItems;
 
 __device__ __forceinline__ uint32_t seg_of(uint64_t y) { return (uint32_t)(y >> (64 - kSegBits)); }
 
@@ -968,19 +967,17 @@ __global__ void __launch_bounds__(kSortThreads) k_seg_tiles(uint32_t* scratch) {
   if (s == 0) scratch[kSegTileOff + kSegs] = total;
 }
 
-// Distinct keys of segments [seg_lo, seg_hi): tiles are claimed in order by
-// ticket, so the tiles in flight stay within a segment or two; a key probes
-// its segment's slice (slots entries, linear probing from its low bits) with
-// a read through L2 and, on an empty slot, a compare-and-swap.  Slots only
-// ever change from empty to a key, so a read that returns the key itself
-// settles the probe, and a stale empty only costs the compare-and-swap.  A
-// thread's keys probe in rounds: every round issues the pending keys' reads
-// together, then their compare-and-swaps together, so their latencies
-// overlap.  Keys new to the table are staged per tile (one shared-memory
-// reservation per warp and item), appended to `out` with one atomicAdd per
-// tile, and both endpoints of each are marked in flags.  A slice that fills
-// up raises kErrOverflow.
-__global__ void __launch_bounds__(kSegInsThreads) k_seg_insert(
+// Distinct keys of segments [seg_lo, seg_hi): tiles claimed in order by
+// ticket (so the tiles in flight stay within a segment or two and their
+// slices stay in L2; a fixed tile-to-block assignment lets the blocks drift
+// apart until the slices in use no longer fit); a key probes its segment's
+// slice (slots entries, linear probing from its low bits) with a read
+// through L2 and, on an empty slot, a compare-and-swap.  Slots only ever change from empty to a key, so a read
+// that returns the key itself settles the probe, and a stale empty only
+// costs the compare-and-swap.  Keys new to the table are staged per tile,
+// appended to `out` with one atomicAdd per tile, and both endpoints of each
+// are marked in flags.  A slice that fills up raises kErrOverflow.
+__global__ void __launch_bounds__(kSortThreads) k_seg_insert(
     const uint64_t* __restrict__ keys, const uint32_t* __restrict__ scratch, uint32_t seg_lo,
     uint32_t seg_hi, uint64_t slots, unsigned long long* table, uint64_t* __restrict__ out,
     uint64_t cap, unsigned long long* m_next, uint8_t* flags, uint32_t n, int half_bits,
@@ -988,14 +985,13 @@ __global__ void __launch_bounds__(kSegInsThreads) k_seg_insert(
   __shared__ uint64_t fresh[kSegInsTile];
   __shared__ uint32_t s_new, s_t;
   __shared__ unsigned long long s_base;
-  const unsigned tid = threadIdx.x, lane = lane_id();
-  const unsigned lt = lanemask_lt();
+  const unsigned tid = threadIdx.x;
   const uint32_t* tiles = scratch + kSegTileOff;
   const uint32_t* starts = scratch + kSegStartOff;
   const uint32_t* fill = scratch + kBucketMaxDigits;
   const uint32_t t0 = tiles[seg_lo], t1 = tiles[seg_hi];
   const uint64_t half_mask = (1ull << half_bits) - 1;
-  const uint32_t smask = (uint32_t)(slots - 1);
+  const uint64_t smask = slots - 1;
   if (tid == 0) s_new = 0;
   for (;;) {
     if (tid == 0) s_t = t0 + atomicAdd(ticket, 1u);
@@ -1014,66 +1010,43 @@ __global__ void __launch_bounds__(kSegInsThreads) k_seg_insert(
     const uint64_t ke = fill[sg * kBucketFillStride];
     unsigned long long* slice = table + (uint64_t)(sg - seg_lo) * slots;
     uint64_t k[kSegInsItems];
-    uint32_t slot[kSegInsItems];
-    uint32_t pending = 0, fresh_mask = 0;
 #pragma unroll
     for (int i = 0; i < kSegInsItems; ++i) {
-      const uint64_t j = kb + (uint64_t)i * kSegInsThreads + tid;
+      const uint64_t j = kb + (uint64_t)i * kSortThreads + tid;
       k[i] = (j < ke && j < cap) ? __ldcs(keys + j) : kEmpty;
-      slot[i] = (uint32_t)k[i] & smask;
-      if (k[i] != kEmpty) pending |= 1u << i;
     }
-    for (uint64_t probe = 0; pending != 0; ++probe) {
-      if (probe >= slots) {
-        atomicOr(err, kErrOverflow);
-        break;
-      }
-      unsigned long long cur[kSegInsItems];
 #pragma unroll
-      for (int i = 0; i < kSegInsItems; ++i)
-        cur[i] = ((pending >> i) & 1u) ? __ldcg(slice + slot[i]) : 0ull;
-      uint32_t want = 0;
-#pragma unroll
-      for (int i = 0; i < kSegInsItems; ++i) {
-        if (!((pending >> i) & 1u)) continue;
-        if (cur[i] == k[i]) pending &= ~(1u << i);  // already in the table
-        else if (cur[i] == kEmpty) want |= 1u << i;
-      }
-#pragma unroll
-      for (int i = 0; i < kSegInsItems; ++i)
-        cur[i] = ((want >> i) & 1u) ? atomicCAS(slice + slot[i], kEmpty, k[i]) : 0ull;
-#pragma unroll
-      for (int i = 0; i < kSegInsItems; ++i) {
-        if (!((pending >> i) & 1u)) continue;
-        if ((want >> i) & 1u) {
-          if (cur[i] == kEmpty) {
-            fresh_mask |= 1u << i;
-            pending &= ~(1u << i);
-            continue;
+    for (int i = 0; i < kSegInsItems; ++i) {
+      if (k[i] == kEmpty) continue;
+      uint64_t slot = k[i] & smask;
+      bool done = false;
+      for (uint64_t probe = 0; probe < slots; ++probe) {
+        const unsigned long long cur = __ldcg(slice + slot);
+        if (cur == k[i]) {
+          done = true;
+          break;
+        }
+        if (cur == kEmpty) {
+          const unsigned long long old = atomicCAS(slice + slot, kEmpty, k[i]);
+          if (old == kEmpty) {
+            fresh[atomicAdd(&s_new, 1u)] = k[i];
+            done = true;
+            break;
           }
-          if (cur[i] == k[i]) {
-            pending &= ~(1u << i);
-            continue;
+          if (old == k[i]) {
+            done = true;
+            break;
           }
         }
-        slot[i] = (slot[i] + 1) & smask;  // taken by another key: next slot
+        slot = (slot + 1) & smask;
       }
-    }
-    // stage the new keys: one shared-memory reservation per warp and item
-#pragma unroll
-    for (int i = 0; i < kSegInsItems; ++i) {
-      const unsigned b = __ballot_sync(kFull, (fresh_mask >> i) & 1u);
-      if (b == 0) continue;
-      uint32_t base = 0;
-      if (lane == (unsigned)(__ffs(b) - 1)) base = atomicAdd(&s_new, (uint32_t)__popc(b));
-      base = __shfl_sync(kFull, base, __ffs(b) - 1);
-      if ((fresh_mask >> i) & 1u) fresh[base + __popc(b & lt)] = k[i];
+      if (!done) atomicOr(err, kErrOverflow);
     }
     __syncthreads();
     const uint32_t nn = s_new;
     if (tid == 0) s_base = nn ? atomicAdd(m_next, (unsigned long long)nn) : 0ull;
     __syncthreads();
-    for (uint32_t e = tid; e < nn; e += kSegInsThreads) {
+    for (uint32_t e = tid; e < nn; e += kSortThreads) {
       const uint64_t v = fresh[e];
       const uint64_t pos = s_base + e;
       if (index_ok(err, kKSegDedup, pos, cap)) out[pos] = v;
@@ -1186,7 +1159,7 @@ bool seg_dedup(const uint64_t* keys, uint32_t* scratch, uint64_t max_count, uint
     k_seg_tiles<<<1, kSortThreads, 0, L.stream>>>(scratch);
   }
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_seg_insert, kSegInsThreads, 0) !=
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_seg_insert, kSortThreads, 0) !=
           cudaSuccess ||
       per_sm < 1)
     per_sm = 1;
@@ -1197,7 +1170,7 @@ bool seg_dedup(const uint64_t* keys, uint32_t* scratch, uint64_t max_count, uint
     cudaMemsetAsync(table, 0xFF, 8ull * slots * (hi - lo), L.stream);
     cudaMemsetAsync(ticket, 0, sizeof(unsigned), L.stream);
     KScope ks(L, kKSegDedup);
-    k_seg_insert<<<grid, kSegInsThreads, 0, L.stream>>>(
+    k_seg_insert<<<grid, kSortThreads, 0, L.stream>>>(
         keys, scratch, lo, hi, slots, reinterpret_cast<unsigned long long*>(table), out,
         max_count, m_next, flags, n, half_bits, ticket, err);
   }

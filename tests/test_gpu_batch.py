@@ -1,5 +1,7 @@
 """Batched runs: every graph of a batch must get exactly what its own lc_run
 gives (labels, phase count, per-phase sizes), and what the oracle gives."""
+import os
+
 import numpy as np
 import pytest
 
@@ -86,3 +88,36 @@ def test_batch_local_id_out_of_range(lc_lib, cuda):
         b.run()
     assert ei.value.code == lc.LC_ERR_INVALID
     b.close()
+
+
+@pytest.mark.slow
+def test_config4_batch_at_size(lc_lib, cuda):
+    """The batched workload at its stated size: 4096 graphs, n log-uniform in
+    [2^6, 2^16], half ER (degree 4) and half R-MAT (degree 16), about 3.9e7
+    vertices and 1.9e8 edges in one context.  Phase 0 of the batch then
+    takes the large-phase path (edge buckets, duplicate filter, distinct-key
+    estimate, segmented deduplication).  Every graph's labels, phase count
+    and per-phase (n_i, m_i) are compared with the oracle (run on the host's
+    cores in parallel)."""
+    from concurrent.futures import ThreadPoolExecutor
+    b = synth.batch(k=4096)
+    assert int(b.eoff[-1]) >= 1 << 22 and int(b.n.max()) <= 1 << 16
+    ts, td = to_dev(b.src, cuda), to_dev(b.dst, cuda)
+    bl = lc.BatchLocalContraction(b.n, b.eoff, ts, td, b.seeds)
+    labels, rounds, n_i, m_i = bl.run(cap=64)
+    bl.close()
+    labels = labels.cpu().numpy().view(np.uint32)
+    voff = np.concatenate([[0], np.cumsum(b.n.astype(np.int64))])
+
+    def ref(g):
+        gr = b.graph(g)
+        return oracle.lc_run(gr.n, gr.src, gr.dst, gr.seed)
+
+    refs = [ref(0)]  # loads the oracle library before the threads share it
+    with ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 1)) as ex:
+        refs += list(ex.map(ref, range(1, b.k)))
+    for g, r in enumerate(refs):
+        R = int(rounds[g])
+        assert R == r.rounds, g
+        assert list(zip(n_i[g, :R].tolist(), m_i[g, :R].tolist())) == r.sizes(), g
+        assert np.array_equal(labels[voff[g]:voff[g + 1]], r.labels), g
