@@ -143,6 +143,9 @@ __device__ __forceinline__ void min_edge_packed(uint64_t x, const K& keys,
                                                 unsigned* err) {
   const uint32_t a = (uint32_t)(x >> 32), b = (uint32_t)x;
   if (!index_ok(err, kOpen ? kKOpenMin : kKEdgeMinPacked, max(a, b), n)) return;
+  // a self-loop (phase 0's grouped input keeps them) offers no other
+  // neighbour: it must not reach the open-neighbourhood minimum
+  if (kOpen && a == b) return;
   uint64_t ka, kb;
   keys.pair(a, b, ka, kb);
   if (kOpen) {

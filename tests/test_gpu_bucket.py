@@ -118,3 +118,18 @@ def test_bucket_param_rejections(lc_lib, cuda):
         with pytest.raises(lc.LCError):
             ctx.set_param(name, bad)
     ctx.close()
+
+
+@pytest.mark.parametrize("variant", [oracle.FOREST, oracle.TWO_HOP, oracle.TREE])
+def test_bucketed_self_loops(lc_lib, cuda, variant):
+    """Phase 0 reads the raw input, self-loops included, through the grouped
+    edges: a loop must not count as a neighbour in the open-neighbourhood
+    minimum of TreeContraction (nor change anything elsewhere)."""
+    rng = np.random.default_rng(21)
+    for n, m, loops in [(2000, 6000, 0.3), (50000, 150000, 0.1), (300, 2000, 0.9)]:
+        s = rng.integers(0, n, m, dtype=np.uint32)
+        d = rng.integers(0, n, m, dtype=np.uint32)
+        pick = rng.random(m) < loops
+        d[pick] = s[pick]
+        for blocks in (2, 7):
+            check(n, s, d, int(rng.integers(0, 1 << 40)), cuda, blocks, variant=variant)
