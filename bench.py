@@ -466,7 +466,9 @@ def bench_serving(rates=SERVING_RATES, requests=1000, pool=200, slots=32, serial
                        "[2^10, 2^22], degree 4-32, %d edges in the pool)" % (requests, pool, edges),
            "slots": slots, "ranks": world, "rates": [], "serial": []}
     srv = lc.Server(slots=slots)
-    warm = [srv.submit(r.graph.n, r.graph.src, r.graph.dst, r.graph.seed) for r in reqs[:8]]
+    # warm-up: every distinct request once, so the timed arrivals find idle
+    # contexts of every size in the server's pool (steady state)
+    warm = [srv.submit(r.graph.n, r.graph.src, r.graph.dst, r.graph.seed) for r in reqs]
     for j in warm:
         srv.wait(j)
     for rate in rates:

@@ -679,7 +679,7 @@ struct EdgeBlocks {
   }
 };
 
-constexpr int kBktItems = 16;
+constexpr int kBktItems = 8;
 constexpr int kBktTile = kSortThreads * kBktItems;  // edges per tile
 
 // Bucket counts of the input edges (ids >= n count as the loop (0, 0)).

@@ -56,11 +56,11 @@ def test_bucketed_variants(lc_lib, cuda, variant, finish):
 
 
 def test_bucketed_ragged_and_small(lc_lib, cuda):
-    """Edge counts around the 4096-edge tile and the 4-edge vector loads,
+    """Edge counts around the 2048-edge tile and the 4-edge vector loads,
     graphs smaller than the block count, one vertex."""
     rng = np.random.default_rng(11)
-    for n, m in [(1, 3), (2, 1), (5, 7), (40, 4095), (300, 4096), (300, 4097),
-                 (1000, 8191), (70000, 12289), (70000, 4 * 4096 + 3)]:
+    for n, m in [(1, 3), (2, 1), (5, 7), (40, 2047), (300, 2048), (300, 2049), (40, 4095),
+                 (300, 4096), (300, 4097), (1000, 8191), (70000, 12289), (70000, 4 * 4096 + 3)]:
         s = rng.integers(0, n, m, dtype=np.uint32)
         d = rng.integers(0, n, m, dtype=np.uint32)
         for blocks in (2, 32):
