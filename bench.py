@@ -13,7 +13,7 @@ Extra keys on the JSON line:
                  compact, labels; each the sum of its kernels): its
                  algorithmic bytes per run / its device time per run (CUDA
                  events, profiled pass), against the measured HBM copy peak.
-  steps          the same figures for every step, with the kernels each holds.
+  step_rooflines the same figures for every step, with the kernels each holds.
   path_roofline  all algorithmic bytes of a run / the headline step time.
   e2e            the same metric through lc_run_host (pinned host buffers;
                  host->device copy of the edges and device->host copy of the
@@ -80,7 +80,8 @@ STEP_KERNELS = {
 # algorithmic byte of a step, measured on R-MAT 23 with one-kernel captures
 # of phase 0, keyed by the hash of the CUDA sources they were taken on: a
 # changed kernel invalidates them (the line then reports traffic null).
-TRAFFIC = {"sources": None, "workload": "rmat23", "per_alg_byte": {}}
+TRAFFIC = {"sources": "97d569a219aa8bf6", "workload": "rmat23",
+           "per_alg_byte": {"parent": 3.83, "relabel": 0.89, "dedup": 0.88}}
 
 
 def sources_hash() -> str:
@@ -793,7 +794,7 @@ def main():
                        "rounds": res.rounds, "parallelism": "replicas" if world > 1 else "single",
                        "params": args.param,
                        "l2": "inputs (8 B/edge) larger than L2; no flush"},
-            "roofline": roof, "path_roofline": path_roof, "steps": steps, "tuning": tuning,
+            "roofline": roof, "path_roofline": path_roof, "step_rooflines": steps, "tuning": tuning,
             "profiled_ms_per_step": prof_ms,
             "e2e": e2e, "cpu_baseline": cpu, "gpu_launches": launches, "configs": configs,
             "batched": batched, "serving": serving, "variants": variants,

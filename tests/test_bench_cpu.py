@@ -56,7 +56,13 @@ def test_step_report_and_roofline():
     assert roof["step"] == "relabel"
     ach = steps["relabel"]["algorithmic_bytes"] / (3.0 / 1e3) / 1e9
     assert abs(roof["achieved"] - ach) < 1e-9 and abs(roof["frac"] - ach / 1000.0) < 1e-12
-    assert roof["traffic"] is None  # no capture recorded for these sources
+    # DRAM traffic: the captured ratio for this step times its algorithmic
+    # bytes, only while the CUDA sources are the ones the captures were taken on
+    ratio = bench.TRAFFIC["per_alg_byte"].get("relabel")
+    if ratio and bench.TRAFFIC["sources"] == bench.sources_hash():
+        assert abs(roof["traffic"] - ratio * steps["relabel"]["algorithmic_bytes"]) < 1e-6
+    else:
+        assert roof["traffic"] is None
     for names in bench.STEP_KERNELS.values():
         assert len(names) == len(set(names))
 
