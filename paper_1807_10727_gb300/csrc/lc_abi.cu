@@ -274,7 +274,7 @@ struct lc_ctx {
   int gcache_admit = kGCacheAdmit;        // log2 of the cache's admission period
   uint32_t* d_hll = nullptr;              // HyperLogLog registers of the relabel's keys
   uint32_t* h_hll = nullptr;              // (pinned host copy)
-  uint8_t* flags = nullptr;
+  uint32_t* flags = nullptr;  // bitmap, flag_words(n) words
   uint64_t* ebuf[2] = {nullptr, nullptr};
   Counters* ctr = nullptr;
   Counters* h_ctr = nullptr;
@@ -399,7 +399,7 @@ static lc_status alloc_ctx(lc_ctx* c) {
   c->n_cap = c->n;
   c->m_cap = c->m;
   LC_TRY(dev_alloc(c->mem, &c->minkey, std::max<uint64_t>(n, 1) * 8));
-  LC_TRY(dev_alloc(c->mem, &c->flags, ((n + 15) & ~15ull) + 16));
+  LC_TRY(dev_alloc(c->mem, &c->flags, 4 * (flag_words(n) + 4)));
   LC_TRY(dev_alloc(c->mem, &c->ebuf[0], std::max<uint64_t>(m, 2) * 8));
   LC_TRY(dev_alloc(c->mem, &c->ebuf[1], std::max<uint64_t>(m, 2) * 8));
   LC_TRY(dev_alloc(c->mem, &c->ctr, sizeof(Counters)));
@@ -660,7 +660,7 @@ static lc_status enqueue_phase(lc_ctx* c) {
   }
   // (d): relabel, drop loops, deduplicate, compact
   if (cudaMemsetAsync(c->ctr, 0, 4 * sizeof(unsigned long long), c->stream) != cudaSuccess ||
-      cudaMemsetAsync(c->flags, 0, ni, c->stream) != cudaSuccess)
+      cudaMemsetAsync(c->flags, 0, 4 * flag_words(ni), c->stream) != cudaSuccess)
     return fail(c, LC_ERR_CUDA);
   r.keys = (r.packed == c->ebuf[0]) ? c->ebuf[1] : c->ebuf[0];
   r.alt = (r.keys == c->ebuf[0]) ? c->ebuf[1] : c->ebuf[0];
@@ -975,7 +975,7 @@ static lc_status run_complete(lc_ctx* c) {
     if (cudaMemsetAsync(&c->ctr->m_next, 0, 2 * sizeof(unsigned long long), c->stream) !=
             cudaSuccess ||
         cudaMemsetAsync(&c->ctr->err, 0, sizeof(unsigned), c->stream) != cudaSuccess ||
-        cudaMemsetAsync(c->flags, 0, r.ni, c->stream) != cudaSuccess)
+        cudaMemsetAsync(c->flags, 0, 4 * flag_words(r.ni), c->stream) != cudaSuccess)
       return fail(c, LC_ERR_CUDA);
     r.state = RunState::kSortPhase;
     lc_status st = enqueue_sort_dedup(c);
@@ -1365,7 +1365,7 @@ constexpr uint64_t align256(uint64_t x) { return (x + 255) & ~255ull; }
 constexpr uint64_t kSN = LC_STATIC_MAX_N, kSM = LC_STATIC_MAX_M;
 constexpr uint64_t kOffMinkey = 0;
 constexpr uint64_t kOffFlags = align256(kOffMinkey + 8 * kSN);
-constexpr uint64_t kOffEbuf0 = align256(kOffFlags + kSN + 16);
+constexpr uint64_t kOffEbuf0 = align256(kOffFlags + 4 * (flag_words(kSN) + 4));
 constexpr uint64_t kOffEbuf1 = align256(kOffEbuf0 + 8 * kSM);
 constexpr uint64_t kOffCtr = align256(kOffEbuf1 + 8 * kSM);
 constexpr uint64_t kStatusWords = (kSM + kSortTile - 1) / kSortTile * kRadixMax + 1024;
@@ -1427,7 +1427,7 @@ extern "C" lc_status lc_run_static(uint32_t n, const uint32_t* d_src, const uint
   c.src = d_src;
   c.dst = d_dst;
   c.minkey = reinterpret_cast<unsigned long long*>(base + kOffMinkey);
-  c.flags = base + kOffFlags;
+  c.flags = reinterpret_cast<uint32_t*>(base + kOffFlags);
   c.ebuf[0] = reinterpret_cast<uint64_t*>(base + kOffEbuf0);
   c.ebuf[1] = reinterpret_cast<uint64_t*>(base + kOffEbuf1);
   c.ctr = reinterpret_cast<Counters*>(base + kOffCtr);
@@ -1471,7 +1471,7 @@ uint64_t ctx_bytes(uint64_t n, uint64_t m) {
   const uint64_t arena = 4 * std::max<uint64_t>(4 * (2 * n + 256), 1024);
   const uint64_t gcache =
       m >= kGCacheMinEdges ? 8ull * kGCacheSlots + 4ull * kHllRegs + 8 * table_slots_for(m) : 0;
-  return gcache + 8 * std::max<uint64_t>(n, 1) + n + 32 + 16 * std::max<uint64_t>(m, 2) + status +
+  return gcache + 8 * std::max<uint64_t>(n, 1) + 4 * (flag_words(n) + 4) + 16 * std::max<uint64_t>(m, 2) + status +
          bounds + arena + 8 * std::max<uint64_t>(m, 1) + 4 * std::max<uint64_t>(n, 1) +
          sizeof(Counters) + 4096 + 16 * 4 + 4ull * kMaxPasses * kRadixMax + (1u << 16) +
          4 * kBucketScratchWords;

@@ -125,6 +125,21 @@ __device__ __forceinline__ bool index_ok(unsigned* err, uint32_t kernel, uint64_
   return false;
 }
 
+// Node flags ("keeps an edge") are a bitmap: bit v & 31 of word v >> 5.  At
+// one bit per node the array of a 2^26-node phase is 8 MB and stays in L2
+// while the random marks land on it; byte flags (64 MB) did not.  A mark
+// reads the word first: skewed graphs mark their hubs once per edge, and
+// atomics on one address serialise, while a read of a set bit is a cache
+// hit.  A stale read (another block set the bit since) only costs the atomic.
+__host__ __device__ __forceinline__ constexpr uint64_t flag_words(uint64_t n) {
+  return (n + 31) >> 5;
+}
+__device__ __forceinline__ void mark_flag(uint32_t* flags, uint64_t v) {
+  uint32_t* w = flags + (v >> 5);
+  const uint32_t bit = 1u << (v & 31);
+  if ((*w & bit) == 0u) atomicOr(w, bit);
+}
+
 __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
 
 __device__ __forceinline__ unsigned lanemask_lt() {

@@ -151,12 +151,12 @@ uint32_t next_epoch(SortScratch& s, const Launch& L);
 // digits (onesweep: one histogram pass, then one single-pass scatter per digit
 // with decoupled look-back).  `max_count` bounds *d_count and sizes the grids.
 // The sorted keys end in keys or alt; the return value says which (0 = keys).
-// When mark_flags is non-null the last pass also sets mark_flags[a] =
-// mark_flags[b] = 1 for every key (a << half_bits | b) (used to find the nodes
-// that keep an edge).
+// When mark_flags is non-null the last pass also sets the bits of a and b in
+// the mark_flags bitmap for every key (a << half_bits | b) (used to find the
+// nodes that keep an edge).
 int radix_sort_u64(uint64_t* keys, uint64_t* alt, const unsigned long long* d_count,
                    uint64_t max_count, int key_bits, SortScratch& s, unsigned* err,
-                   uint8_t* mark_flags, int half_bits, const Launch& L);
+                   uint32_t* mark_flags, int half_bits, const Launch& L);
 
 // Bucket-hash bits used for max_count keys (0 when one bucket suffices).
 int hash_bits_for(uint64_t max_count);
@@ -217,7 +217,7 @@ void filter_seg(const uint64_t* in, const unsigned long long* d_in, uint64_t max
 // kErrOverflow (the caller falls back to the full sort).
 bool seg_dedup(const uint64_t* keys, uint32_t* scratch, uint64_t max_count, uint64_t* table,
                uint64_t table_slots, uint64_t slots, uint64_t* out, unsigned long long* m_next,
-               uint8_t* flags, uint32_t n, int half_bits, unsigned* ticket, unsigned* err,
+               uint32_t* flags, uint32_t n, int half_bits, unsigned* ticket, unsigned* err,
                const Launch& L);
 void seg_compact(const uint64_t* keys, const uint32_t* scratch, uint64_t* out, const Launch& L);
 
@@ -246,7 +246,7 @@ void filter_hll(const uint64_t* in, const unsigned long long* d_in, uint64_t max
 // `bounds` holds (1 << hb) + 1 words.
 int hash_dedup(uint64_t* keys, uint64_t* alt, const unsigned long long* d_count,
                uint64_t max_count, const PassPlan& plan, int hb, bool hist_ready,
-               int half_bits, uint8_t* flags, uint32_t n, uint32_t* bounds,
+               int half_bits, uint32_t* flags, uint32_t n, uint32_t* bounds,
                unsigned long long* m_next, SortScratch& s, unsigned* err, const Launch& L);
 
 // e[j] = (newid[a] << 32 | newid[b]) for each mixed key
@@ -259,10 +259,10 @@ void rename_edges(uint64_t* e, const unsigned long long* d_count, uint64_t max_c
 void unmix_keys(uint64_t* e, const unsigned long long* d_count, uint64_t max_count,
                 const Launch& L);
 
-// In-place exclusive scan of flags[0, n) (values 0/1 as uint8) into
+// In-place exclusive scan of the flag bits 0..n-1 (bitmap, see flag_words) into
 // out[0, n] (uint32, out[n] = total); for every kept r (flag set) also copies
 // mo_in[r] to mo_out[out[r]] when mo_out is non-null.  *total gets the sum.
-void scan_flags(const uint8_t* flags, uint32_t* out, uint32_t n, const uint32_t* mo_in,
+void scan_flags(const uint32_t* flags, uint32_t* out, uint32_t n, const uint32_t* mo_in,
                 uint32_t* mo_out, unsigned long long* total, SortScratch& s, unsigned* err,
                 const Launch& L);
 

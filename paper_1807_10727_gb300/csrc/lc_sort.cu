@@ -296,7 +296,7 @@ template <int kRB>
 __global__ void __launch_bounds__(kSortThreads, 3) k_sort_pass(
     const uint64_t* __restrict__ in, uint64_t* __restrict__ out, const unsigned long long* d_count,
     DigitFn dg, int bits, const uint32_t* __restrict__ digit_offset, uint64_t* status,
-    uint32_t epoch, unsigned* ticket, unsigned* err, uint8_t* mark_flags, int half_bits,
+    uint32_t epoch, unsigned* ticket, unsigned* err, uint32_t* mark_flags, int half_bits,
     uint32_t spin_limit, int stall) {
   constexpr int kR = 1 << kRB;
   constexpr int kPer = kR / kSortThreads;
@@ -407,8 +407,8 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_sort_pass(
     uint64_t gpos = (uint64_t)gofs[dg(key)] + j;
     if (gpos < count) __stcs(out + gpos, key);
     if (mark_flags != nullptr && (j == 0 || sk[j - 1] != key)) {
-      mark_flags[key >> half_bits] = 1;
-      mark_flags[key & half_mask] = 1;
+      mark_flag(mark_flags, key >> half_bits);
+      mark_flag(mark_flags, key & half_mask);
     }
   }
 }
@@ -460,7 +460,7 @@ __device__ __forceinline__ int set_insert(uint64_t* table, uint64_t key, int* ov
 // endpoints of each are marked in `flags`, and their slots are cleared.
 __global__ void __launch_bounds__(kSortThreads) k_bucket_dedup(
     const uint64_t* __restrict__ keys, const uint32_t* __restrict__ bounds, uint32_t nb,
-    uint64_t* __restrict__ out, uint64_t cap, unsigned long long* m_next, uint8_t* flags,
+    uint64_t* __restrict__ out, uint64_t cap, unsigned long long* m_next, uint32_t* flags,
     uint32_t n, int half_bits, unsigned* ticket, unsigned* err) {
   extern __shared__ __align__(16) uint64_t table[];  // [kTableSlots], then the slot list
   uint16_t* list = reinterpret_cast<uint16_t*>(table + kTableSlots);  // [kTableSlots]
@@ -513,8 +513,8 @@ __global__ void __launch_bounds__(kSortThreads) k_bucket_dedup(
       const uint64_t k = key_unmix(v);
       const uint64_t a = k >> half_bits, c = k & half_mask;
       if (index_ok(err, kKBucketDedup, a > c ? a : c, n)) {
-        flags[a] = 1;
-        flags[c] = 1;
+        mark_flag(flags, a);
+        mark_flag(flags, c);
       }
       table[slot] = kEmpty;
     }
@@ -552,7 +552,7 @@ constexpr int kScanItems = 16;
 constexpr int kScanTile = kSortThreads * kScanItems;
 
 __global__ void __launch_bounds__(kSortThreads) k_scan_flags(
-    const uint8_t* __restrict__ flags, uint32_t* __restrict__ out, uint32_t n,
+    const uint32_t* __restrict__ flags, uint32_t* __restrict__ out, uint32_t n,
     const uint32_t* __restrict__ mo_in, uint32_t* __restrict__ mo_out,
     unsigned long long* total_out, uint64_t* status, uint32_t epoch, unsigned* ticket,
     unsigned* err) {
@@ -565,16 +565,12 @@ __global__ void __launch_bounds__(kSortThreads) k_scan_flags(
   const uint64_t base = (uint64_t)tile * kScanTile;
   if (base >= n) return;
   const uint64_t i0 = base + (uint64_t)tid * kScanItems;
+  // i0 is a multiple of kScanItems (16): a thread's bits are one half word
+  static_assert(32 % kScanItems == 0, "a thread's flag bits must not straddle words");
+  const uint32_t w = (i0 < n) ? (flags[i0 >> 5] >> (i0 & 31)) : 0u;
   uint8_t f[kScanItems];
-  if (i0 + kScanItems <= n) {
-    uint4 q = *reinterpret_cast<const uint4*>(flags + i0);
-    const uint8_t* b = reinterpret_cast<const uint8_t*>(&q);
 #pragma unroll
-    for (int i = 0; i < kScanItems; ++i) f[i] = b[i] ? 1 : 0;
-  } else {
-#pragma unroll
-    for (int i = 0; i < kScanItems; ++i) f[i] = (i0 + i < n && flags[i0 + i]) ? 1 : 0;
-  }
+  for (int i = 0; i < kScanItems; ++i) f[i] = (i0 + i < n) ? ((w >> i) & 1u) : 0u;
   uint32_t sum = 0;
 #pragma unroll
   for (int i = 0; i < kScanItems; ++i) sum += f[i];
@@ -972,15 +968,15 @@ __global__ void __launch_bounds__(kSortThreads) k_seg_tiles(uint32_t* scratch) {
 // slices stay in L2; a fixed tile-to-block assignment lets the blocks drift
 // apart until the slices in use no longer fit); a key probes its segment's
 // slice (slots entries, linear probing from its low bits) with a read
-// through L2 and, on an empty slot, a compare-and-swap.  Slots only ever change from empty to a key, so a read
-// that returns the key itself settles the probe, and a stale empty only
-// costs the compare-and-swap.  Keys new to the table are staged per tile,
+// through L2 and, on an empty slot, a compare-and-swap.  Slots only ever
+// change from empty to a key, so a read that returns the key itself settles
+// the probe, and a stale empty only costs the compare-and-swap.  Keys new to the table are staged per tile,
 // appended to `out` with one atomicAdd per tile, and both endpoints of each
 // are marked in flags.  A slice that fills up raises kErrOverflow.
 __global__ void __launch_bounds__(kSortThreads) k_seg_insert(
     const uint64_t* __restrict__ keys, const uint32_t* __restrict__ scratch, uint32_t seg_lo,
     uint32_t seg_hi, uint64_t slots, unsigned long long* table, uint64_t* __restrict__ out,
-    uint64_t cap, unsigned long long* m_next, uint8_t* flags, uint32_t n, int half_bits,
+    uint64_t cap, unsigned long long* m_next, uint32_t* flags, uint32_t n, int half_bits,
     unsigned* ticket, unsigned* err) {
   __shared__ uint64_t fresh[kSegInsTile];
   __shared__ uint32_t s_new, s_t;
@@ -1053,8 +1049,8 @@ __global__ void __launch_bounds__(kSortThreads) k_seg_insert(
       const uint64_t kk = key_unmix(v);
       const uint64_t a = kk >> half_bits, b = kk & half_mask;
       if (index_ok(err, kKSegDedup, a > b ? a : b, n)) {
-        flags[a] = 1;
-        flags[b] = 1;
+        mark_flag(flags, a);
+        mark_flag(flags, b);
       }
     }
     __syncthreads();
@@ -1149,7 +1145,7 @@ void filter_seg(const uint64_t* in, const unsigned long long* d_in, uint64_t max
 
 bool seg_dedup(const uint64_t* keys, uint32_t* scratch, uint64_t max_count, uint64_t* table,
                uint64_t table_slots, uint64_t slots, uint64_t* out, unsigned long long* m_next,
-               uint8_t* flags, uint32_t n, int half_bits, unsigned* ticket, unsigned* err,
+               uint32_t* flags, uint32_t n, int half_bits, unsigned* ticket, unsigned* err,
                const Launch& L) {
   if (table == nullptr || slots == 0 || (slots & (slots - 1)) != 0 || slots > table_slots)
     return false;
@@ -1219,7 +1215,7 @@ void hist_reset(SortScratch& s, const Launch& L) {
 // producer of the keys); otherwise a histogram pass reads the keys first.
 static int run_passes(uint64_t* keys, uint64_t* alt, const unsigned long long* d_count,
                       uint64_t max_count, const PassPlan& plan, bool hist_ready, SortScratch& s,
-                      unsigned* err, uint8_t* mark_flags, int half_bits, const Launch& L) {
+                      unsigned* err, uint32_t* mark_flags, int half_bits, const Launch& L) {
   if (max_count == 0 || plan.passes == 0) return 0;
   set_smem_limits();
   cudaMemsetAsync(s.tickets, 0, sizeof(unsigned) * 8, L.stream);
@@ -1253,7 +1249,7 @@ static int run_passes(uint64_t* keys, uint64_t* alt, const unsigned long long* d
 
 int radix_sort_u64(uint64_t* keys, uint64_t* alt, const unsigned long long* d_count,
                    uint64_t max_count, int key_bits, SortScratch& s, unsigned* err,
-                   uint8_t* mark_flags, int half_bits, const Launch& L) {
+                   uint32_t* mark_flags, int half_bits, const Launch& L) {
   PassPlan plan{};
   plan.passes = (std::max(key_bits, 1) + kRadixBits - 1) / kRadixBits;
   for (int p = 0; p < plan.passes; ++p) {
@@ -1297,7 +1293,7 @@ int hash_plan(uint64_t max_count, PassPlan* plan) {
 
 int hash_dedup(uint64_t* keys, uint64_t* alt, const unsigned long long* d_count,
                uint64_t max_count, const PassPlan& plan, int hb, bool hist_ready,
-               int half_bits, uint8_t* flags, uint32_t n, uint32_t* bounds,
+               int half_bits, uint32_t* flags, uint32_t n, uint32_t* bounds,
                unsigned long long* m_next, SortScratch& s, unsigned* err, const Launch& L) {
   if (max_count == 0) return 0;
   int which =
@@ -1338,7 +1334,7 @@ void rename_edges(uint64_t* e, const unsigned long long* d_count, uint64_t max_c
   k_rename<<<g, 256, 0, L.stream>>>(e, d_count, max_count, half_bits, newid, n, err);
 }
 
-void scan_flags(const uint8_t* flags, uint32_t* out, uint32_t n, const uint32_t* mo_in,
+void scan_flags(const uint32_t* flags, uint32_t* out, uint32_t n, const uint32_t* mo_in,
                 uint32_t* mo_out, unsigned long long* total, SortScratch& s, unsigned* err,
                 const Launch& L) {
   if (n == 0) return;

@@ -177,13 +177,16 @@ def test_output_cap_too_small(lc_lib, cuda):
 @pytest.mark.parametrize("dedup", [lc.LC_DEDUP_HASH, lc.LC_DEDUP_SORT])
 def test_relabel_cache_sizes(lc_lib, cuda, dedup):
     """The device-wide relabel cache (phases of >= 2^22 edges) at sizes from
-    heavy collisions to none: results never change, and it only drops keys."""
+    heavy collisions to none: results never change, and it only drops keys.
+    The library defaults (not the tuned table, whose rmat18 entry plans
+    phases of fewer than 2^24 edges early, without the cache) keep phase 0's
+    2^22 edges on the cached path."""
     g = synth.workload("rmat18")
     ref = oracle.lc_run(g.n, g.src, g.dst, g.seed)
     ts, td = dev(g.src, cuda), dev(g.dst, cuda)
     emitted = {}
     for slots in (0, 1024, 1 << 16, 1 << 20, 1 << 24):
-        ctx = lc.LocalContraction(g.n, ts, td, seed=g.seed, dedup=dedup)
+        ctx = lc.LocalContraction(g.n, ts, td, seed=g.seed, dedup=dedup, tuned=False)
         ctx.set_param("relabel_cache_slots", slots)
         labels, res = ctx.run()
         mp, em = lc.lc_last_stats(ctx.ctx)
