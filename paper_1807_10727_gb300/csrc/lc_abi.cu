@@ -700,7 +700,7 @@ static lc_status enqueue_phase(lc_ctx* c) {
           seg ? c->bucket_scratch : c->sort.hist,
           (first && pk == nullptr) ? r.alt : nullptr,
           c->relabel_window_bytes, gcache_in_relabel ? c->gcache : nullptr,
-          gcache_in_relabel ? c->gcache_slots : 0, c->gcache_admit, err, L);
+          gcache_in_relabel ? c->gcache_slots : 0, c->gcache_admit, c->sort.tickets + 13, err, L);
   if (late) {
     // drop repeats through the device-wide cache while sketching the distinct
     // count; the kept keys (counted in `filtered`) replace the relabelled ones

@@ -334,12 +334,13 @@ void jump(unsigned long long* minkey, uint32_t* root, uint32_t* mo, uint32_t n, 
 // gslots 64-bit slots, a power of two, all ~0 when the phase's relabel
 // starts; nullptr / 0 = no such cache; a missing key enters it at one in
 // 2^admit of its occurrences).  The written keys hold every distinct key.
+// Tiles are claimed in order through the device word `ticket` (cleared here).
 void relabel(const uint32_t* src, const uint32_t* dst, const uint64_t* packed, uint64_t m,
              uint32_t n, const uint32_t* root, int bits, uint64_t* keys_out,
              unsigned long long* mprime, unsigned long long* emitted, bool mix,
              const PassPlan* plan, uint32_t* ghist, uint64_t* tmp, uint64_t window_bytes,
-             unsigned long long* gcache, uint32_t gslots, int admit, unsigned* err,
-             const Launch& L);
+             unsigned long long* gcache, uint32_t gslots, int admit, unsigned* ticket,
+             unsigned* err, const Launch& L);
 
 // labels_out[v] = kept(root[v]) ? labels_up[scan[root[v]]] : mo[root[v]], with
 // kept(r) = scan[r+1] > scan[r].  labels_out may alias root.

@@ -595,19 +595,29 @@ __global__ void __launch_bounds__(kThreads) k_relabel(
     const uint64_t* __restrict__ packed, uint64_t m, uint32_t n, const uint32_t* __restrict__ root,
     int bits, uint64_t* __restrict__ keys_out, unsigned long long* mprime,
     unsigned long long* emitted, int mix, PassPlan plan, uint32_t* __restrict__ ghist,
-    unsigned* mprime_err, unsigned long long* gcache, uint32_t gmask, int admit) {
+    unsigned* mprime_err, unsigned long long* gcache, uint32_t gmask, int admit,
+    unsigned* ticket) {
   __shared__ uint64_t cache[kRelCache];
   __shared__ uint32_t hist[3][kRadixMax];
   __shared__ uint32_t ws[kThreads / 32];
   __shared__ uint32_t wk[kThreads / 32];
   __shared__ unsigned long long s_base;
+  __shared__ uint32_t s_t;
   const uint64_t tile_edges = (uint64_t)kThreads * kRelItems;
   const uint64_t ntiles = (m + tile_edges - 1) / tile_edges;
   const unsigned tid = threadIdx.x, lane = lane_id(), w = tid >> 5;
   for (int i = tid; i < kRelCache; i += kThreads) cache[i] = ~0ull;
   for (int i = tid; i < 3 * kRadixMax; i += kThreads) (&hist[0][0])[i] = 0;
   __syncthreads();
-  for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+  for (;;) {
+    // tiles claimed in order by ticket, so the tiles in flight stay close in
+    // the edge order (on grouped edges: one pair of vertex blocks, whose
+    // roots stay in L2); the previous tile's closing barrier orders this
+    // write after every thread's read of s_t
+    if (tid == 0) s_t = atomicAdd(ticket, 1u);
+    __syncthreads();
+    const uint64_t t = s_t;
+    if (t >= ntiles) break;
     // thread item i handles edge base + w*32*kRelItems + i*32 + lane (coalesced)
     const uint64_t base = t * tile_edges + (uint64_t)w * 32 * kRelItems;
     uint64_t key[kRelItems];
@@ -846,19 +856,20 @@ void relabel(const uint32_t* src, const uint32_t* dst, const uint64_t* packed, u
              uint32_t n, const uint32_t* root, int bits, uint64_t* keys_out,
              unsigned long long* mprime, unsigned long long* emitted, bool mix,
              const PassPlan* plan, uint32_t* ghist, uint64_t* tmp, uint64_t window_bytes,
-             unsigned long long* gcache, uint32_t gslots, int admit, unsigned* err,
-             const Launch& L) {
+             unsigned long long* gcache, uint32_t gslots, int admit, unsigned* ticket,
+             unsigned* err, const Launch& L) {
   const uint32_t gmask = gslots ? gslots - 1 : 0;
   if (gslots == 0) gcache = nullptr;
   PassPlan pl{};
   if (plan != nullptr) pl = *plan;  // passes == 0: no histogram
   if (m == 0) return;
   int grid = grid_for(m, kThreads * kRelItems, L, 4);
+  cudaMemsetAsync(ticket, 0, sizeof(unsigned), L.stream);
   if (packed != nullptr) {
     KScope ks(L, kKRelabelPacked);
     k_relabel<1><<<grid, kThreads, 0, L.stream>>>(nullptr, nullptr, packed, m, n, root, bits,
                                                   keys_out, mprime, emitted, mix, pl, ghist,
-                                                  err, gcache, gmask, admit);
+                                                  err, gcache, gmask, admit, ticket);
   } else if (tmp != nullptr && n < kResolved && (uint64_t)n * 4 > window_bytes) {
     // one pass per L2-sized part of root (see k_relabel_first_half)
     const uint64_t parts = std::min<uint64_t>(8, ((uint64_t)n * 4 + window_bytes - 1) /
@@ -877,12 +888,12 @@ void relabel(const uint32_t* src, const uint32_t* dst, const uint64_t* packed, u
     KScope ks(L, kKRelabelSoa);
     k_relabel<2><<<grid, kThreads, 0, L.stream>>>(nullptr, nullptr, tmp, m, n, root, bits,
                                                   keys_out, mprime, emitted, mix, pl, ghist,
-                                                  err, gcache, gmask, admit);
+                                                  err, gcache, gmask, admit, ticket);
   } else {
     KScope ks(L, kKRelabelSoa);
     k_relabel<0><<<grid, kThreads, 0, L.stream>>>(src, dst, nullptr, m, n, root, bits, keys_out,
                                                   mprime, emitted, mix, pl, ghist, err, gcache,
-                                                  gmask, admit);
+                                                  gmask, admit, ticket);
   }
 }
 
