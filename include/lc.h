@@ -174,6 +174,8 @@ lc_status lc_set_dedup(lc_ctx* ctx, lc_dedup mode);
  *                   which two blocks of 8-byte minima fit this many bytes
  *                   (>= 1 MiB, default 64 MiB).
  *   "bucket_min_vertices"  see "bucket_blocks".
+ *   "host_chunk_edges"  lc_run_host: edges per input copy (>= 1, default
+ *                   2^25); see lc_run_host.
  *   "late_min_edges"  phases with at least this many edges (>= 1024, default
  *                   2^22) plan their deduplication after the relabel, below;
  *                   lowering it below the context's edge count allocates the
@@ -223,7 +225,15 @@ lc_status lc_run(lc_ctx* ctx, uint32_t* d_labels, uint32_t* rounds, uint64_t* n_
 /* End-to-end variant for a context created with NULL edge pointers: copies the
  * host edge arrays h_src/h_dst (uint32[m]) to the device, runs the phase loop
  * and copies the labels to host h_labels (uint32[n]); other arguments as in
- * lc_run. */
+ * lc_run.  For a single graph whose phase 0 takes the closed-neighbourhood
+ * minimum (forest and two-hop variants, no union-find finish in phase 0) the
+ * copy overlaps phase 0: the edges go over in chunks of "host_chunk_edges"
+ * on a second stream of the context, and each chunk gets phase 0's bucket
+ * counts and its share of the minimum (Section 2's parent over N(v); a
+ * minimum of atomic updates, the same in any order) as soon as it has
+ * arrived.  The result is the one lc_run gives on the same edges.  Pinned
+ * host buffers give full copy speed; pageable ones are staged by the CUDA
+ * runtime. */
 lc_status lc_run_host(lc_ctx* ctx, const uint32_t* h_src, const uint32_t* h_dst,
                       uint32_t* h_labels, uint32_t* rounds, uint64_t* n_i, uint64_t* m_i,
                       uint32_t cap);

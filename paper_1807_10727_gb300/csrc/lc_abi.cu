@@ -220,6 +220,8 @@ struct RunState {
   uint32_t passes = 0;      // partition passes planned for the level in flight
   bool filtered = false;    // the level's keys went through the filter pass
   bool seg = false;         // the kept keys lie in segment regions (segmented dedup)
+  bool pre0 = false;        // phase 0's ranks, bucket counts and minimum ran as the input
+                            // arrived (lc_run_host)
   uint32_t* d_labels = nullptr;
   uint32_t i = 0, ni = 0;
   uint64_t mi = 0;
@@ -259,6 +261,9 @@ struct lc_ctx {
   Prof prof;
   lc_variant variant = LC_VARIANT_FOREST;
   uint64_t finish_edges = 0;
+  cudaStream_t copy_stream = nullptr;  // lc_run_host: input copies, chunk by chunk
+  cudaEvent_t copy_ev = nullptr;       // lc_run_host: the last chunk copied
+  uint64_t host_chunk_edges = 1ull << 25;
   std::vector<uint32_t> merge_alpha;  // MergeToLarge parameter of phase i (0: off)
 
   const uint32_t* src = nullptr;
@@ -342,6 +347,8 @@ static void free_ctx(lc_ctx* c) {
   dev_free(c->mem, c->ctr);
   if (c->h_ctr && !c->pinned) cudaFreeHost(c->h_ctr);
   if (c->ev) cudaEventDestroy(c->ev);
+  if (c->copy_ev) cudaEventDestroy(c->copy_ev);
+  if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
   if (c->batch) {
     dev_free(c->mem, c->batch->d_seeds);
     dev_free(c->mem, c->batch->d_voff0);
@@ -596,7 +603,10 @@ static lc_status enqueue_phase(lc_ctx* c) {
     // below gather from an L2-sized slice of the per-vertex arrays at a time;
     // the grouped copy goes to the buffer the relabel does not write
     uint64_t* grouped = c->ebuf[1];
-    bucket_edges(src0, dst0, mi, ni, nb, grouped, c->bucket_scratch, err, L);
+    if (r.pre0)
+      bucket_place(src0, dst0, mi, ni, nb, grouped, c->bucket_scratch, err, L);
+    else
+      bucket_edges(src0, dst0, mi, ni, nb, grouped, c->bucket_scratch, err, L);
     src0 = dst0 = nullptr;
     pk = grouped;
   }
@@ -624,6 +634,9 @@ static lc_status enqueue_phase(lc_ctx* c) {
     if (aerr != cudaSuccess) return fail(c, status_of(aerr));
     merge_to_large_names(prev.root, prev.scan, prev.n, rk, c->merge_alpha[i], r.packed, mi, ni,
                          r.lv.root, r.lv.mo, ms, err, L);
+  } else if (first && r.pre0) {
+    // (a) ran with the input copy; each vertex's min original id = itself
+    identity_labels(r.lv.mo, ni, L);
   } else {
     // (a): ranks (and, in phase 0, each vertex's min original id = itself)
     init_keys(c->minkey, first ? r.lv.mo : nullptr, ni, rk, bp, L);
@@ -642,8 +655,10 @@ static lc_status enqueue_phase(lc_ctx* c) {
     edge_min(src0, dst0, pk, mi, ni, rk, c->minkey, err, c->window_bytes, bp, L, true);
     tree_names(c->minkey, r.lv.root, r.lv.mo, ni, rk, bp, err, L);
   } else {
-    // (b): closed-neighbourhood minimum
-    edge_min(src0, dst0, pk, mi, ni, rk, c->minkey, err, c->window_bytes, bp, L);
+    // (b): closed-neighbourhood minimum (phase 0 of lc_run_host: done as the
+    // input arrived)
+    if (!(first && r.pre0))
+      edge_min(src0, dst0, pk, mi, ni, rk, c->minkey, err, c->window_bytes, bp, L);
     if (c->variant == LC_VARIANT_TWO_HOP) {
       // second hop; names are label vertices, node minima in their own array
       uint32_t* nmo = c->arena.alloc(ni, &aerr);
@@ -852,7 +867,57 @@ static lc_status enqueue_labels(lc_ctx* c) {
   return st == LC_OK ? st : fail(c, st);
 }
 
-static lc_status run_begin(lc_ctx* c, uint32_t* d_labels) {
+// Phase 0's steps that need only part of the input, run while the host edges
+// are copied: the copies go chunk by chunk on a second stream, and each chunk
+// gets the bucket counts of the edge grouping and its share of the
+// closed-neighbourhood minimum (atomic minima: any order of chunks gives the
+// same minkey) as soon as it has arrived.  Everything after the minimum needs
+// all edges.
+static lc_status copy_input_overlapped(lc_ctx* c, const uint32_t* h_src, const uint32_t* h_dst) {
+  const Launch& L = c->L;
+  unsigned* err = &c->ctr->err;
+  const uint64_t rk = phase_seed(c->seed, 0);
+  if (!c->copy_stream &&
+      cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking) != cudaSuccess)
+    return LC_ERR_CUDA;
+  if (!c->copy_ev && cudaEventCreateWithFlags(&c->copy_ev, cudaEventDisableTiming) != cudaSuccess)
+    return LC_ERR_CUDA;
+  init_keys(c->minkey, nullptr, c->n, rk, nullptr, L);
+  const uint32_t nb = bucket_blocks(c, c->n);
+  if (nb > 1) bucket_clear(c->n, nb, c->bucket_scratch, L);
+  // the copies may not overwrite the input before the work queued so far ends
+  if (cudaEventRecord(c->copy_ev, c->stream) != cudaSuccess ||
+      cudaStreamWaitEvent(c->copy_stream, c->copy_ev, 0) != cudaSuccess)
+    return LC_ERR_CUDA;
+  const uint64_t chunk = std::max<uint64_t>(c->host_chunk_edges, 1);
+  for (uint64_t off = 0; off < c->m; off += chunk) {
+    const uint64_t len = std::min(chunk, c->m - off);
+    if (cudaMemcpyAsync(c->own_src + off, h_src + off, len * 4, cudaMemcpyHostToDevice,
+                        c->copy_stream) != cudaSuccess ||
+        cudaMemcpyAsync(c->own_dst + off, h_dst + off, len * 4, cudaMemcpyHostToDevice,
+                        c->copy_stream) != cudaSuccess ||
+        cudaEventRecord(c->copy_ev, c->copy_stream) != cudaSuccess ||
+        cudaStreamWaitEvent(c->stream, c->copy_ev, 0) != cudaSuccess)
+      return LC_ERR_CUDA;
+    if (nb > 1) bucket_count(c->own_src + off, c->own_dst + off, len, c->n, nb,
+                             c->bucket_scratch, err, L);
+    edge_min(c->own_src + off, c->own_dst + off, nullptr, len, c->n, rk, c->minkey, err,
+             c->window_bytes, nullptr, L);
+  }
+  c->rs.pre0 = true;
+  return LC_OK;
+}
+
+// Whether lc_run_host can overlap phase 0 with the input copy: a single graph
+// whose phase 0 takes the closed-neighbourhood minimum.
+static bool overlap_input(const lc_ctx* c) {
+  return c->batch == nullptr && c->m > 0 && c->n > 0 &&
+         (c->variant == LC_VARIANT_FOREST || c->variant == LC_VARIANT_TWO_HOP) &&
+         !(c->finish_edges != 0 && c->m <= c->finish_edges);
+}
+
+static lc_status run_begin(lc_ctx* c, uint32_t* d_labels, const uint32_t* h_src = nullptr,
+                           const uint32_t* h_dst = nullptr) {
   RunState& r = c->rs;
   r = RunState{};
   r.d_labels = d_labels;
@@ -890,6 +955,10 @@ static lc_status run_begin(lc_ctx* c, uint32_t* d_labels) {
   r.mo_cur = c->arena.alloc(r.ni, &aerr);
   if (aerr != cudaSuccess) return fail(c, status_of(aerr));
   r.i = 0;
+  if (h_src) {
+    lc_status st = copy_input_overlapped(c, h_src, h_dst);
+    if (st != LC_OK) return fail(c, st);
+  }
   return enqueue_phase(c);
 }
 
@@ -1017,9 +1086,10 @@ static lc_status run_complete(lc_ctx* c) {
 }
 
 static lc_status run_loop(lc_ctx* c, uint32_t* d_labels, uint32_t* rounds, uint64_t* n_i,
-                          uint64_t* m_i, uint32_t cap) {
+                          uint64_t* m_i, uint32_t cap, const uint32_t* h_src = nullptr,
+                          const uint32_t* h_dst = nullptr) {
   if (rounds) *rounds = 0;
-  lc_status st = run_begin(c, d_labels);
+  lc_status st = run_begin(c, d_labels, h_src, h_dst);
   while (st == LC_OK && c->rs.state != RunState::kDone) {
     st = run_wait(c);
     if (st == LC_OK) st = run_complete(c);
@@ -1051,11 +1121,16 @@ extern "C" lc_status lc_run_host(lc_ctx* c, const uint32_t* h_src, const uint32_
   if (c->m > 0 && (!h_src || !h_dst)) return LC_ERR_INVALID;
   if (c->n > 0 && !h_labels) return LC_ERR_INVALID;
   DeviceGuard g(c->device);
-  if (c->m > 0) {
-    LC_TRY(cudaMemcpyAsync(c->own_src, h_src, c->m * 4, cudaMemcpyHostToDevice, c->stream));
-    LC_TRY(cudaMemcpyAsync(c->own_dst, h_dst, c->m * 4, cudaMemcpyHostToDevice, c->stream));
+  lc_status st;
+  if (overlap_input(c)) {
+    st = run_loop(c, c->own_labels, rounds, n_i, m_i, cap, h_src, h_dst);
+  } else {
+    if (c->m > 0) {
+      LC_TRY(cudaMemcpyAsync(c->own_src, h_src, c->m * 4, cudaMemcpyHostToDevice, c->stream));
+      LC_TRY(cudaMemcpyAsync(c->own_dst, h_dst, c->m * 4, cudaMemcpyHostToDevice, c->stream));
+    }
+    st = run_loop(c, c->own_labels, rounds, n_i, m_i, cap);
   }
-  lc_status st = run_loop(c, c->own_labels, rounds, n_i, m_i, cap);
   if (st != LC_OK && st != LC_ERR_INVALID) return st;
   if (c->n > 0) {
     LC_TRY(cudaMemcpyAsync(h_labels, c->own_labels, (uint64_t)c->n * 4, cudaMemcpyDeviceToHost,
@@ -1248,6 +1323,11 @@ extern "C" lc_status lc_set_param(lc_ctx* c, const char* name, uint64_t value) {
       LC_TRY(alloc_late(c));
     }
     c->late_min_edges = value;
+    return LC_OK;
+  }
+  if (std::strcmp(name, "host_chunk_edges") == 0) {
+    if (value == 0 || value > 0xFFFFFFFFull) return LC_ERR_INVALID;
+    c->host_chunk_edges = value;
     return LC_OK;
   }
   if (std::strcmp(name, "bucket_blocks") == 0) {

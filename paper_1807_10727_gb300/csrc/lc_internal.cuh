@@ -192,6 +192,13 @@ uint32_t bucket_blocks_for(uint32_t n, uint64_t window_bytes);
 // out[0, m) = the input edges (u << 32 | v) grouped by bucket (order inside a
 // bucket unspecified).  Ids >= n set kErrBadVertex and become the self-loop
 // (0, 0), which no step counts.  scratch: kBucketScratchWords words.
+// bucket_edges = bucket_clear, then bucket_count over all edges (which may be
+// split into several calls on consecutive parts), then bucket_place.
+void bucket_clear(uint32_t n, uint32_t nb, uint32_t* scratch, const Launch& L);
+void bucket_count(const uint32_t* src, const uint32_t* dst, uint64_t m, uint32_t n, uint32_t nb,
+                  uint32_t* scratch, unsigned* err, const Launch& L);
+void bucket_place(const uint32_t* src, const uint32_t* dst, uint64_t m, uint32_t n, uint32_t nb,
+                  uint64_t* out, uint32_t* scratch, unsigned* err, const Launch& L);
 void bucket_edges(const uint32_t* src, const uint32_t* dst, uint64_t m, uint32_t n, uint32_t nb,
                   uint64_t* out, uint32_t* scratch, unsigned* err, const Launch& L);
 

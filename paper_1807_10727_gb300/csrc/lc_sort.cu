@@ -1087,23 +1087,48 @@ uint32_t bucket_blocks_for(uint32_t n, uint64_t window_bytes) {
   return (uint32_t)std::min<uint64_t>(kBucketMaxBlocks, std::max<uint64_t>(2, nb));
 }
 
+// scale = ceil(nb * 2^32 / n); blocks are clamped to nb - 1 (needs n >= nb)
+static EdgeBlocks edge_blocks(uint32_t n, uint32_t* nb) {
+  *nb = std::max<uint32_t>(2, std::min(*nb, kBucketMaxBlocks));
+  const uint64_t sc = (((uint64_t)*nb << 32) + n - 1) / std::max<uint32_t>(n, *nb);
+  return EdgeBlocks{(uint32_t)std::min<uint64_t>(sc, 0xFFFFFFFFull), *nb};
+}
+
+static int both_aligned16(const uint32_t* src, const uint32_t* dst) {
+  return ((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst)) & 15) == 0;
+}
+
+void bucket_clear(uint32_t n, uint32_t nb, uint32_t* scratch, const Launch& L) {
+  edge_blocks(n, &nb);
+  cudaMemsetAsync(scratch, 0, sizeof(uint32_t) * nb * nb, L.stream);
+}
+
+void bucket_count(const uint32_t* src, const uint32_t* dst, uint64_t m, uint32_t n, uint32_t nb,
+                  uint32_t* scratch, unsigned* err, const Launch& L) {
+  if (m == 0) return;
+  const EdgeBlocks eb = edge_blocks(n, &nb);
+  KScope ks(L, kKBucketEdges);
+  const int hgrid = (int)std::min<uint64_t>((m + 4095) / 4096, (uint64_t)L.sms * 8);
+  k_bucket_hist<<<hgrid, kSortThreads, 0, L.stream>>>(src, dst, m, n, both_aligned16(src, dst),
+                                                      eb, scratch, err);
+}
+
 void bucket_edges(const uint32_t* src, const uint32_t* dst, uint64_t m, uint32_t n, uint32_t nb,
                   uint64_t* out, uint32_t* scratch, unsigned* err, const Launch& L) {
   if (m == 0) return;
-  nb = std::max<uint32_t>(2, std::min(nb, kBucketMaxBlocks));
-  // scale = ceil(nb * 2^32 / n); blocks are clamped to nb - 1 (needs n >= nb)
-  const uint64_t sc = (((uint64_t)nb << 32) + n - 1) / std::max<uint32_t>(n, nb);
-  const EdgeBlocks eb{(uint32_t)std::min<uint64_t>(sc, 0xFFFFFFFFull), nb};
+  bucket_clear(n, nb, scratch, L);
+  bucket_count(src, dst, m, n, nb, scratch, err, L);
+  bucket_place(src, dst, m, n, nb, out, scratch, err, L);
+}
+
+void bucket_place(const uint32_t* src, const uint32_t* dst, uint64_t m, uint32_t n, uint32_t nb,
+                  uint64_t* out, uint32_t* scratch, unsigned* err, const Launch& L) {
+  if (m == 0) return;
+  const EdgeBlocks eb = edge_blocks(n, &nb);
   const uint32_t nd = nb * nb;
-  const int vec = ((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst)) & 15) == 0;
+  const int vec = both_aligned16(src, dst);
   uint32_t* hist = scratch;
   uint32_t* fill = scratch + kBucketMaxDigits;
-  cudaMemsetAsync(hist, 0, sizeof(uint32_t) * nd, L.stream);
-  {
-    KScope ks(L, kKBucketEdges);
-    const int hgrid = (int)std::min<uint64_t>((m + 4095) / 4096, (uint64_t)L.sms * 8);
-    k_bucket_hist<<<hgrid, kSortThreads, 0, L.stream>>>(src, dst, m, n, vec, eb, hist, err);
-  }
   {
     KScope ks(L, kKBucketEdges);
     k_bucket_starts<<<1, kSortThreads, 0, L.stream>>>(hist, nd, fill);
