@@ -74,12 +74,12 @@ void Prof::release() {
 namespace {
 
 // Level storage of one phase: the root map, the min-original-id of each
-// node, and the exclusive scan of "node keeps an edge" (n + 1 words).
+// node, and the keep ranks of the nodes (see rank_words).
 struct Level {
   uint32_t n;
   uint32_t* root;
   uint32_t* mo;
-  uint32_t* scan;
+  uint64_t* rank;  // keep ranks, rank_words(n) words
 };
 
 // Test hook: the allocation with this number (counted from the last
@@ -567,7 +567,7 @@ static lc_status enqueue_phase(lc_ctx* c) {
   const uint64_t mi = r.mi;
   r.lv = Level{ni, c->arena.alloc(ni, &aerr), r.mo_cur, nullptr};
   if (aerr != cudaSuccess) return fail(c, status_of(aerr));
-  r.lv.scan = c->arena.alloc((uint64_t)ni + 1, &aerr);
+  r.lv.rank = reinterpret_cast<uint64_t*>(c->arena.alloc(2 * rank_words(ni), &aerr));
   if (aerr != cudaSuccess) return fail(c, status_of(aerr));
   r.mo_next = c->arena.alloc(ni, &aerr);
   if (aerr != cudaSuccess) return fail(c, status_of(aerr));
@@ -582,7 +582,7 @@ static lc_status enqueue_phase(lc_ctx* c) {
       if (aerr != cudaSuccess) return fail(c, status_of(aerr));
       uint32_t* mcnt = c->arena.alloc(b->k, &aerr);
       if (aerr != cudaSuccess) return fail(c, status_of(aerr));
-      batch_next_level(b->voff.back(), c->levels.back().scan, b->k, voff, r.packed, mi, mcnt, L);
+      batch_next_level(b->voff.back(), c->levels.back().rank, b->k, voff, r.packed, mi, mcnt, L);
       b->voff.push_back(voff);
       b->mcnt.push_back(mcnt);
     }
@@ -632,7 +632,7 @@ static lc_status enqueue_phase(lc_ctx* c) {
     if (aerr != cudaSuccess) return fail(c, status_of(aerr));
     ms.big = c->arena.alloc(merge_big_words(prev.n), &aerr);
     if (aerr != cudaSuccess) return fail(c, status_of(aerr));
-    merge_to_large_names(prev.root, prev.scan, prev.n, rk, c->merge_alpha[i], r.packed, mi, ni,
+    merge_to_large_names(prev.root, prev.rank, prev.n, rk, c->merge_alpha[i], r.packed, mi, ni,
                          r.lv.root, r.lv.mo, ms, err, L);
   } else if (first && r.pre0) {
     // (a) ran with the input copy; each vertex's min original id = itself
@@ -785,8 +785,8 @@ static bool enqueue_seg_dedup(lc_ctx* c, uint64_t slots) {
   r.passes = 0;
   r.part = r.keys;
   r.next = r.alt;
-  scan_flags(c->flags, r.lv.scan, r.ni, r.lv.mo, r.mo_next, &c->ctr->n_next, c->sort, err, L);
-  rename_edges(r.next, &c->ctr->m_next, r.mi, r.bits, r.lv.scan, r.ni, err, L);
+  scan_flags(c->flags, r.lv.rank, r.ni, r.lv.mo, r.mo_next, &c->ctr->n_next, c->sort, err, L);
+  rename_edges(r.next, &c->ctr->m_next, r.mi, r.bits, r.lv.rank, r.ni, err, L);
   r.state = RunState::kPhase;
   stamp_counters(c->ctr, ++c->tag, L);
   if (cudaMemcpyAsync(c->h_ctr, c->ctr, sizeof(Counters), cudaMemcpyDeviceToHost, c->stream) !=
@@ -811,8 +811,8 @@ static lc_status enqueue_dedup(lc_ctx* c, const PassPlan& hplan, int hb, bool hi
                            c->flags, ni, c->bounds, &c->ctr->m_next, c->sort, err, L);
     r.part = which ? r.alt : r.keys;
     r.next = which ? r.keys : r.alt;
-    scan_flags(c->flags, r.lv.scan, ni, r.lv.mo, r.mo_next, &c->ctr->n_next, c->sort, err, L);
-    rename_edges(r.next, &c->ctr->m_next, mi, r.bits, r.lv.scan, ni, err, L);
+    scan_flags(c->flags, r.lv.rank, ni, r.lv.mo, r.mo_next, &c->ctr->n_next, c->sort, err, L);
+    rename_edges(r.next, &c->ctr->m_next, mi, r.bits, r.lv.rank, ni, err, L);
     r.state = RunState::kPhase;
   } else {
     r.part = r.keys;
@@ -840,8 +840,8 @@ static lc_status enqueue_sort_dedup(lc_ctx* c) {
                           c->flags, r.bits, L);
   uint64_t* sorted = w2 ? r.next : r.part;
   r.next = w2 ? r.part : r.next;
-  scan_flags(c->flags, r.lv.scan, r.ni, r.lv.mo, r.mo_next, &c->ctr->n_next, c->sort, err, L);
-  unique_rename(sorted, kept_count(c), r.mi, r.bits, r.lv.scan, r.ni, r.next,
+  scan_flags(c->flags, r.lv.rank, r.ni, r.lv.mo, r.mo_next, &c->ctr->n_next, c->sort, err, L);
+  unique_rename(sorted, kept_count(c), r.mi, r.bits, r.lv.rank, r.ni, r.next,
                 &c->ctr->m_next, c->sort, err, L);
   return LC_OK;
 }
@@ -855,7 +855,7 @@ static lc_status enqueue_labels(lc_ctx* c) {
     const uint32_t* up = (i + 1 < (int)R) ? c->levels[i + 1].root : nullptr;
     const uint32_t n_up = (i + 1 < (int)R) ? c->levels[i + 1].n : 0;
     uint32_t* out = i == 0 ? c->rs.d_labels : lv.root;
-    propagate(lv.root, lv.scan, lv.mo, up, out, lv.n, n_up, &c->ctr->err, c->L);
+    propagate(lv.root, lv.rank, lv.mo, up, out, lv.n, n_up, &c->ctr->err, c->L);
   }
   if (c->batch) batch_localize(c->rs.d_labels, c->n, c->batch->d_voff0, c->batch->k, c->L);
   stamp_counters(c->ctr, ++c->tag, c->L);

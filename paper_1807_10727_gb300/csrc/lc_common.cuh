@@ -140,6 +140,24 @@ __device__ __forceinline__ void mark_flag(uint32_t* flags, uint64_t v) {
   if ((*w & bit) == 0u) atomicOr(w, bit);
 }
 
+// Keep ranks of a level's nodes (a node is kept when it still has an edge
+// after the relabel): word w of the rank_words(n) words holds, in its high
+// half, the number of kept nodes below node 32w and, in its low half, the
+// keep bits of nodes 32w..32w+31 (the last word covers node n, so the rank
+// of n is the kept total).  A kept node's new id is one 8-byte read and a
+// popcount, from 1/16 of the bytes of a per-node prefix: 16 MB at n = 2^26,
+// which the renumbering's random reads find in L2.
+__host__ __device__ __forceinline__ constexpr uint64_t rank_words(uint64_t n) {
+  return (n >> 5) + 1;
+}
+// *id = number of kept nodes below v; returns whether v is kept (v <= n).
+__device__ __forceinline__ bool keep_rank(const uint64_t* rank, uint32_t v, uint32_t* id) {
+  const uint64_t x = __ldg(rank + (v >> 5));
+  const uint32_t bits = (uint32_t)x, b = v & 31u;
+  *id = (uint32_t)(x >> 32) + __popc(bits & ((1u << b) - 1u));
+  return (bits >> b) & 1u;
+}
+
 __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
 
 __device__ __forceinline__ unsigned lanemask_lt() {

@@ -256,28 +256,29 @@ int hash_dedup(uint64_t* keys, uint64_t* alt, const unsigned long long* d_count,
                int half_bits, uint32_t* flags, uint32_t n, uint32_t* bounds,
                unsigned long long* m_next, SortScratch& s, unsigned* err, const Launch& L);
 
-// e[j] = (newid[a] << 32 | newid[b]) for each mixed key
-// e[j] = key_mix(a << half_bits | b), j < *d_count.
+// e[j] = (id(a) << 32 | id(b)) for each mixed key e[j] = key_mix(a <<
+// half_bits | b), j < *d_count, with id the keep rank (keep_rank).
 void rename_edges(uint64_t* e, const unsigned long long* d_count, uint64_t max_count,
-                  int half_bits, const uint32_t* newid, uint32_t n, unsigned* err,
+                  int half_bits, const uint64_t* rank, uint32_t n, unsigned* err,
                   const Launch& L);
 
 // In place: e[j] = key_unmix(e[j]) for j < *d_count.
 void unmix_keys(uint64_t* e, const unsigned long long* d_count, uint64_t max_count,
                 const Launch& L);
 
-// In-place exclusive scan of the flag bits 0..n-1 (bitmap, see flag_words) into
-// out[0, n] (uint32, out[n] = total); for every kept r (flag set) also copies
-// mo_in[r] to mo_out[out[r]] when mo_out is non-null.  *total gets the sum.
-void scan_flags(const uint32_t* flags, uint32_t* out, uint32_t n, const uint32_t* mo_in,
+// Keep ranks rank[0, rank_words(n)) of the flag bits 0..n-1 (bitmap, see
+// flag_words): an exclusive scan of the words' popcounts; for every kept r
+// (flag set) also copies mo_in[r] to mo_out[id(r)] when mo_out is non-null.
+// *total gets the number of kept nodes.
+void scan_flags(const uint32_t* flags, uint64_t* rank, uint32_t n, const uint32_t* mo_in,
                 uint32_t* mo_out, unsigned long long* total, SortScratch& s, unsigned* err,
                 const Launch& L);
 
 // Compaction of the sorted keys[0, *d_count): keeps the first key of each run
-// of equal keys and writes it renamed through newid as (newid[a] << 32 |
-// newid[b]) to out in sorted order; *m_next gets the number kept.
+// of equal keys and writes it renamed through the keep ranks as (id(a) << 32
+// | id(b)) to out in sorted order; *m_next gets the number kept.
 void unique_rename(const uint64_t* keys, const unsigned long long* d_count, uint64_t max_count,
-                   int half_bits, const uint32_t* newid, uint32_t n, uint64_t* out,
+                   int half_bits, const uint64_t* rank, uint32_t n, uint64_t* out,
                    unsigned long long* m_next, SortScratch& s, unsigned* err, const Launch& L);
 
 // ---------------------------------------------------------- phase steps
@@ -308,7 +309,8 @@ void edge_min(const uint32_t* src, const uint32_t* dst, const uint64_t* packed, 
               uint64_t window_bytes, const BatchView* batch, const Launch& L, bool open = false);
 
 // Batches: phase seeds rk[g] for phase i; local -> global edge ids (ids
-// validated per graph); next level offsets voff_next[g] = scan[voff[g]] and
+// validated per graph); next level offsets voff_next[g] = id(voff[g]) (keep
+// ranks of the level) and
 // per-graph edge counts of the next level's packed edges e[0, m); global ->
 // local labels.
 void batch_phase_seeds(const uint64_t* seeds, uint32_t k, uint32_t i, uint64_t* rk,
@@ -316,7 +318,7 @@ void batch_phase_seeds(const uint64_t* seeds, uint32_t k, uint32_t i, uint64_t* 
 void batch_globalize(const uint32_t* src, const uint32_t* dst, const uint64_t* eoff,
                      const uint32_t* voff, uint32_t k, uint64_t m, uint32_t* gsrc, uint32_t* gdst,
                      unsigned* err, const Launch& L);
-void batch_next_level(const uint32_t* voff, const uint32_t* scan, uint32_t k, uint32_t* voff_next,
+void batch_next_level(const uint32_t* voff, const uint64_t* rank, uint32_t k, uint32_t* voff_next,
                       const uint64_t* e, uint64_t m, uint32_t* mcnt, const Launch& L);
 void batch_localize(uint32_t* labels, uint32_t n, const uint32_t* voff, uint32_t k,
                     const Launch& L);
@@ -349,9 +351,9 @@ void relabel(const uint32_t* src, const uint32_t* dst, const uint64_t* packed, u
              unsigned long long* gcache, uint32_t gslots, int admit, unsigned* ticket,
              unsigned* err, const Launch& L);
 
-// labels_out[v] = kept(root[v]) ? labels_up[scan[root[v]]] : mo[root[v]], with
-// kept(r) = scan[r+1] > scan[r].  labels_out may alias root.
-void propagate(const uint32_t* root, const uint32_t* scan, const uint32_t* mo,
+// labels_out[v] = kept(root[v]) ? labels_up[id(root[v])] : mo[root[v]], with
+// kept and id from the level's keep ranks.  labels_out may alias root.
+void propagate(const uint32_t* root, const uint64_t* rank, const uint32_t* mo,
                const uint32_t* labels_up, uint32_t* labels_out, uint32_t n, uint32_t n_up,
                unsigned* err, const Launch& L);
 
@@ -400,10 +402,10 @@ inline uint64_t merge_big_words(uint32_t n_i) {
 }
 
 // MergeToLarge (Section 5) on the graph G' (n2 nodes, packed edges e[m])
-// that the last phase made from G_i (n_i vertices; root_i, scan_i its root
-// map and keep-scan; rk its key seed): t[x] = node that x joins (x itself
+// that the last phase made from G_i (n_i vertices; root_i, rank_i its root
+// map and keep ranks; rk its key seed): t[x] = node that x joins (x itself
 // when it stays); node minima mo aggregated in place at the targets.
-void merge_to_large_names(const uint32_t* root_i, const uint32_t* scan_i, uint32_t n_i,
+void merge_to_large_names(const uint32_t* root_i, const uint64_t* rank_i, uint32_t n_i,
                           uint64_t rk, uint32_t alpha, const uint64_t* e, uint64_t m,
                           uint32_t n2, uint32_t* t, uint32_t* mo, const MergeScratch& s,
                           unsigned* err, const Launch& L);

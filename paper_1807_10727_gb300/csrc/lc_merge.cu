@@ -28,22 +28,22 @@ inline int grid_for(uint64_t work, int per_block, const Launch& L, int blocks_pe
 
 // Node of G' that vertex v of G_i was contracted into, or n' when v's node
 // was dropped (it kept no edge).
-__device__ __forceinline__ uint32_t node_of(const uint32_t* root, const uint32_t* scan,
+__device__ __forceinline__ uint32_t node_of(const uint32_t* root, const uint64_t* rank,
                                             uint32_t v, uint32_t n_i, uint32_t n2, unsigned* err,
                                             int kernel) {
   const uint32_t r = root[v];
   if (!index_ok(err, kernel, r, n_i)) return n2;
-  const uint32_t s0 = scan[r], s1 = scan[r + 1];
-  if (s1 == s0) return n2;
+  uint32_t s0;
+  if (!keep_rank(rank, r, &s0)) return n2;
   return index_ok(err, kernel, s0, n2) ? s0 : n2;
 }
 
 // cnt[x] = number of G_i vertices contracted into node x.
-__global__ void k_m2l_count(const uint32_t* __restrict__ root, const uint32_t* __restrict__ scan,
+__global__ void k_m2l_count(const uint32_t* __restrict__ root, const uint64_t* __restrict__ rank,
                             uint32_t n_i, uint32_t n2, uint32_t* cnt, unsigned* err) {
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n_i; v += stride) {
-    const uint32_t x = node_of(root, scan, (uint32_t)v, n_i, n2, err, kKMergeGroup);
+    const uint32_t x = node_of(root, rank, (uint32_t)v, n_i, n2, err, kKMergeGroup);
     if (x < n2) atomicAdd(&cnt[x], 1u);
   }
 }
@@ -139,13 +139,13 @@ __global__ void __launch_bounds__(kSelThreads) k_m2l_big_compact(
 }
 
 // members[off[x] + j] = the j-th (in any order) G_i vertex of large node x.
-__global__ void k_m2l_scatter(const uint32_t* __restrict__ root, const uint32_t* __restrict__ scan,
+__global__ void k_m2l_scatter(const uint32_t* __restrict__ root, const uint64_t* __restrict__ rank,
                               uint32_t n_i, uint32_t n2, const uint32_t* __restrict__ cnt,
                               const uint32_t* __restrict__ off, uint32_t alpha, uint32_t* fill,
                               uint32_t* members, unsigned* err) {
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n_i; v += stride) {
-    const uint32_t x = node_of(root, scan, (uint32_t)v, n_i, n2, err, kKMergeGroup);
+    const uint32_t x = node_of(root, rank, (uint32_t)v, n_i, n2, err, kKMergeGroup);
     if (x >= n2 || cnt[x] < alpha) continue;
     const uint32_t j = atomicAdd(&fill[x], 1u);
     const uint64_t pos = (uint64_t)off[x] + j;
@@ -263,7 +263,7 @@ __global__ void k_m2l_copy(unsigned long long* __restrict__ dst,
 // target is large and never moves, so node minima are aggregated in place.
 __global__ void k_m2l_target(const unsigned long long* __restrict__ prio,
                              const unsigned long long* __restrict__ h2,
-                             const uint32_t* __restrict__ root, const uint32_t* __restrict__ scan,
+                             const uint32_t* __restrict__ root, const uint64_t* __restrict__ rank,
                              uint32_t n_i, uint32_t n2, uint32_t* t, uint32_t* mo, unsigned* err) {
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n2; x += stride) {
@@ -272,7 +272,7 @@ __global__ void k_m2l_target(const unsigned long long* __restrict__ prio,
     if (prio[x] == 0 && h != 0) {
       const uint32_t w = (uint32_t)(h - 1);
       if (index_ok(err, kKMergeTarget, w, n_i)) {
-        const uint32_t z = node_of(root, scan, w, n_i, n2, err, kKMergeTarget);
+        const uint32_t z = node_of(root, rank, w, n_i, n2, err, kKMergeTarget);
         if (index_ok(err, kKMergeTarget, z, n2)) y = z;
       }
     }
@@ -283,7 +283,7 @@ __global__ void k_m2l_target(const unsigned long long* __restrict__ prio,
 
 }  // namespace
 
-void merge_to_large_names(const uint32_t* root_i, const uint32_t* scan_i, uint32_t n_i,
+void merge_to_large_names(const uint32_t* root_i, const uint64_t* rank_i, uint32_t n_i,
                           uint64_t rk, uint32_t alpha, const uint64_t* e, uint64_t m,
                           uint32_t n2, uint32_t* t, uint32_t* mo, const MergeScratch& s,
                           unsigned* err, const Launch& L) {
@@ -301,7 +301,7 @@ void merge_to_large_names(const uint32_t* root_i, const uint32_t* scan_i, uint32
   cudaMemsetAsync(s.prio, 0, sizeof(unsigned long long) * n2, L.stream);
   {
     KScope ks(L, kKMergeGroup);
-    k_m2l_count<<<grid_for(n_i, kThreads, L), kThreads, 0, L.stream>>>(root_i, scan_i, n_i, n2,
+    k_m2l_count<<<grid_for(n_i, kThreads, L), kThreads, 0, L.stream>>>(root_i, rank_i, n_i, n2,
                                                                        s.cnt, err);
   }
   {
@@ -312,7 +312,7 @@ void merge_to_large_names(const uint32_t* root_i, const uint32_t* scan_i, uint32
   {
     KScope ks(L, kKMergeGroup);
     k_m2l_scatter<<<grid_for(n_i, kThreads, L), kThreads, 0, L.stream>>>(
-        root_i, scan_i, n_i, n2, s.cnt, s.off, alpha, s.fill, s.members, err);
+        root_i, rank_i, n_i, n2, s.cnt, s.off, alpha, s.fill, s.members, err);
   }
   {
     KScope ks(L, kKMergeSelect);
@@ -366,7 +366,7 @@ void merge_to_large_names(const uint32_t* root_i, const uint32_t* scan_i, uint32
     k_m2l_hop<<<grid_for(m, kThreads, L), kThreads, 0, L.stream>>>(e, m, n2, s.h1, s.h2, err);
   }
   KScope ks(L, kKMergeTarget);
-  k_m2l_target<<<grid_for(n2, kThreads, L), kThreads, 0, L.stream>>>(s.prio, s.h2, root_i, scan_i,
+  k_m2l_target<<<grid_for(n2, kThreads, L), kThreads, 0, L.stream>>>(s.prio, s.h2, root_i, rank_i,
                                                                      n_i, n2, t, mo, err);
 }
 

@@ -211,13 +211,16 @@ __global__ void k_batch_globalize(const uint32_t* __restrict__ src, const uint32
   }
 }
 
-// Offsets of the next level: graph g's surviving nodes are the scan values of
-// its range, so voff_next[g] = scan[voff[g]] (g <= k).
+// Offsets of the next level: graph g's surviving nodes are the new ids of its
+// range, so voff_next[g] = id(voff[g]) (g <= k; voff[k] = n has the total).
 __global__ void k_batch_next_offsets(const uint32_t* __restrict__ voff,
-                                     const uint32_t* __restrict__ scan, uint32_t k,
+                                     const uint64_t* __restrict__ rank, uint32_t k,
                                      uint32_t* __restrict__ voff_next) {
-  for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g <= k; g += gridDim.x * blockDim.x)
-    voff_next[g] = scan[voff[g]];
+  for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g <= k; g += gridDim.x * blockDim.x) {
+    uint32_t id;
+    keep_rank(rank, voff[g], &id);
+    voff_next[g] = id;
+  }
 }
 
 // mcnt[g] += number of packed edges (a << 32 | b) whose endpoint a lies in
@@ -731,7 +734,7 @@ __global__ void __launch_bounds__(kThreads) k_relabel(
 // ------------------------------------------------------ label composition
 
 __global__ void __launch_bounds__(kThreads) k_propagate(const uint32_t* root,
-                                                        const uint32_t* __restrict__ scan,
+                                                        const uint64_t* __restrict__ rank,
                                                         const uint32_t* __restrict__ mo,
                                                         const uint32_t* __restrict__ labels_up,
                                                         uint32_t* labels_out, uint32_t n,
@@ -743,12 +746,13 @@ __global__ void __launch_bounds__(kThreads) k_propagate(const uint32_t* root,
       labels_out[v] = (uint32_t)v;
       continue;
     }
-    uint32_t s0 = scan[r], s1 = scan[r + 1];
-    if (s1 > s0 && !index_ok(err, kKPropagate, s0, n_up)) {
+    uint32_t s0;
+    const bool kept = keep_rank(rank, r, &s0);
+    if (kept && !index_ok(err, kKPropagate, s0, n_up)) {
       labels_out[v] = (uint32_t)v;
       continue;
     }
-    labels_out[v] = s1 > s0 ? labels_up[s0] : mo[r];
+    labels_out[v] = kept ? labels_up[s0] : mo[r];
   }
 }
 
@@ -827,10 +831,10 @@ void batch_globalize(const uint32_t* src, const uint32_t* dst, const uint64_t* e
                                                                          m, gsrc, gdst, err);
 }
 
-void batch_next_level(const uint32_t* voff, const uint32_t* scan, uint32_t k, uint32_t* voff_next,
+void batch_next_level(const uint32_t* voff, const uint64_t* rank, uint32_t k, uint32_t* voff_next,
                       const uint64_t* e, uint64_t m, uint32_t* mcnt, const Launch& L) {
   KScope ks(L, kKBatch);
-  k_batch_next_offsets<<<grid_for(k + 1, kThreads, L), kThreads, 0, L.stream>>>(voff, scan, k,
+  k_batch_next_offsets<<<grid_for(k + 1, kThreads, L), kThreads, 0, L.stream>>>(voff, rank, k,
                                                                                 voff_next);
   cudaMemsetAsync(mcnt, 0, sizeof(uint32_t) * k, L.stream);
   if (m)
@@ -897,12 +901,12 @@ void relabel(const uint32_t* src, const uint32_t* dst, const uint64_t* packed, u
   }
 }
 
-void propagate(const uint32_t* root, const uint32_t* scan, const uint32_t* mo,
+void propagate(const uint32_t* root, const uint64_t* rank, const uint32_t* mo,
                const uint32_t* labels_up, uint32_t* labels_out, uint32_t n, uint32_t n_up,
                unsigned* err, const Launch& L) {
   if (n == 0) return;
   KScope ks(L, kKPropagate);
-  k_propagate<<<grid_for(n, kThreads, L), kThreads, 0, L.stream>>>(root, scan, mo, labels_up,
+  k_propagate<<<grid_for(n, kThreads, L), kThreads, 0, L.stream>>>(root, rank, mo, labels_up,
                                                                    labels_out, n, n_up, err);
 }
 

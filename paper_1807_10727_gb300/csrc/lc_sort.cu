@@ -522,9 +522,10 @@ __global__ void __launch_bounds__(kSortThreads) k_bucket_dedup(
   }
 }
 
-// e[j] = (newid[a] << 32 | newid[b]) for e[j] = key_mix(a << half_bits | b).
+// e[j] = (id(a) << 32 | id(b)) for e[j] = key_mix(a << half_bits | b), id the
+// keep rank.
 __global__ void k_rename(uint64_t* __restrict__ e, const unsigned long long* d_count,
-                         uint64_t cap, int half_bits, const uint32_t* __restrict__ newid,
+                         uint64_t cap, int half_bits, const uint64_t* __restrict__ rank,
                          uint32_t n, unsigned* err) {
   const uint64_t count = *d_count;
   if (!index_ok(err, kKRename, count, cap + 1)) return;
@@ -534,7 +535,10 @@ __global__ void k_rename(uint64_t* __restrict__ e, const unsigned long long* d_c
     uint64_t k = key_unmix(e[j]);
     const uint64_t a = k >> half_bits, b = k & half_mask;
     if (!index_ok(err, kKRename, a > b ? a : b, n)) continue;
-    e[j] = ((uint64_t)newid[a] << 32) | newid[b];
+    uint32_t ia, ib;
+    keep_rank(rank, (uint32_t)a, &ia);
+    keep_rank(rank, (uint32_t)b, &ib);
+    e[j] = ((uint64_t)ia << 32) | ib;
   }
 }
 
@@ -550,9 +554,14 @@ __global__ void k_unmix(uint64_t* __restrict__ e, const unsigned long long* d_co
 
 constexpr int kScanItems = 16;
 constexpr int kScanTile = kSortThreads * kScanItems;
+constexpr int kRankItems = 4;  // flag words per thread
+constexpr int kRankTile = kSortThreads * kRankItems;
 
+// Keep ranks (rank_words) from the flag bitmap, by a single-pass scan of the
+// words' popcounts with decoupled look-back; each kept node's mo value is
+// copied to its new id.
 __global__ void __launch_bounds__(kSortThreads) k_scan_flags(
-    const uint32_t* __restrict__ flags, uint32_t* __restrict__ out, uint32_t n,
+    const uint32_t* __restrict__ flags, uint64_t* __restrict__ rank, uint32_t n,
     const uint32_t* __restrict__ mo_in, uint32_t* __restrict__ mo_out,
     unsigned long long* total_out, uint64_t* status, uint32_t epoch, unsigned* ticket,
     unsigned* err) {
@@ -562,50 +571,46 @@ __global__ void __launch_bounds__(kSortThreads) k_scan_flags(
   if (tid == 0) s_tile = atomicAdd(ticket, 1u);
   __syncthreads();
   const uint32_t tile = s_tile;
-  const uint64_t base = (uint64_t)tile * kScanTile;
-  if (base >= n) return;
-  const uint64_t i0 = base + (uint64_t)tid * kScanItems;
-  // i0 is a multiple of kScanItems (16): a thread's bits are one half word
-  static_assert(32 % kScanItems == 0, "a thread's flag bits must not straddle words");
-  const uint32_t w = (i0 < n) ? (flags[i0 >> 5] >> (i0 & 31)) : 0u;
-  uint8_t f[kScanItems];
+  const uint64_t nw = rank_words(n), fw = flag_words(n);
+  const uint64_t base = (uint64_t)tile * kRankTile;
+  if (base >= nw) return;
+  const uint64_t w0 = base + (uint64_t)tid * kRankItems;
+  uint32_t f[kRankItems];
+  if (w0 + kRankItems <= fw) {
+    const uint4 q = *reinterpret_cast<const uint4*>(flags + w0);
+    f[0] = q.x; f[1] = q.y; f[2] = q.z; f[3] = q.w;
+  } else {
 #pragma unroll
-  for (int i = 0; i < kScanItems; ++i) f[i] = (i0 + i < n) ? ((w >> i) & 1u) : 0u;
+    for (int i = 0; i < kRankItems; ++i) f[i] = w0 + i < fw ? flags[w0 + i] : 0u;
+  }
   uint32_t sum = 0;
 #pragma unroll
-  for (int i = 0; i < kScanItems; ++i) sum += f[i];
+  for (int i = 0; i < kRankItems; ++i) sum += __popc(f[i]);
   uint32_t tile_total;
-  uint32_t e = block_exclusive_scan(sum, ws, &tile_total);
+  const uint32_t e = block_exclusive_scan(sum, ws, &tile_total);
   if (tid == 0) s_excl = look_back(status, tile, tile_total, epoch, err);
   __syncthreads();
   uint32_t run = s_excl + e;
-  uint32_t o[kScanItems];
 #pragma unroll
-  for (int i = 0; i < kScanItems; ++i) {
-    o[i] = run;
-    if (f[i] && mo_out != nullptr) mo_out[run] = mo_in[i0 + i];
-    run += f[i];
+  for (int i = 0; i < kRankItems; ++i) {
+    if (w0 + i < nw) rank[w0 + i] = ((uint64_t)run << 32) | f[i];
+    if (mo_out != nullptr) {
+      uint32_t bits = f[i], r = run;
+      while (bits) {
+        const uint64_t v = 32 * (w0 + i) + (uint32_t)(__ffs(bits) - 1);
+        if (index_ok(err, kKScanFlags, v, n)) mo_out[r] = mo_in[v];
+        ++r;
+        bits &= bits - 1u;
+      }
+    }
+    run += __popc(f[i]);
   }
-  if (i0 + kScanItems <= n) {
-    uint4* dst = reinterpret_cast<uint4*>(out + i0);
-#pragma unroll
-    for (int i = 0; i < kScanItems / 4; ++i)
-      dst[i] = make_uint4(o[4 * i], o[4 * i + 1], o[4 * i + 2], o[4 * i + 3]);
-  } else {
-#pragma unroll
-    for (int i = 0; i < kScanItems; ++i)
-      if (i0 + i < n) out[i0 + i] = o[i];
-  }
-  if (base + kScanTile >= n && tid == 0) {
-    uint32_t t = s_excl + tile_total;
-    out[n] = t;
-    *total_out = t;
-  }
+  if (base + kRankTile >= nw && tid == 0) *total_out = s_excl + tile_total;
 }
 
 __global__ void __launch_bounds__(kSortThreads) k_unique_rename(
     const uint64_t* __restrict__ keys, const unsigned long long* d_count, int half_bits,
-    const uint32_t* __restrict__ newid, uint32_t n, uint64_t* __restrict__ out,
+    const uint64_t* __restrict__ rank, uint32_t n, uint64_t* __restrict__ out,
     unsigned long long* m_next, uint64_t* status, uint32_t epoch, unsigned* ticket,
     unsigned* err) {
   __shared__ uint32_t ws[kWarps];
@@ -651,8 +656,9 @@ __global__ void __launch_bounds__(kSortThreads) k_unique_rename(
     if (fl & (1u << i)) {
       const uint64_t ka = k[i] >> half_bits, kb = k[i] & half_mask;
       if (index_ok(err, kKUniqueRename, ka > kb ? ka : kb, n)) {
-        uint32_t a = newid[ka];
-        uint32_t b = newid[kb];
+        uint32_t a, b;
+        keep_rank(rank, (uint32_t)ka, &a);
+        keep_rank(rank, (uint32_t)kb, &b);
         out[pos] = ((uint64_t)a << 32) | b;
       }
       ++pos;
@@ -1351,28 +1357,29 @@ void unmix_keys(uint64_t* e, const unsigned long long* d_count, uint64_t max_cou
 }
 
 void rename_edges(uint64_t* e, const unsigned long long* d_count, uint64_t max_count,
-                  int half_bits, const uint32_t* newid, uint32_t n, unsigned* err,
+                  int half_bits, const uint64_t* rank, uint32_t n, unsigned* err,
                   const Launch& L) {
   if (max_count == 0) return;
   KScope ks(L, kKRename);
   int g = (int)std::min<uint64_t>((max_count + 255) / 256, (uint64_t)L.sms * 8);
-  k_rename<<<g, 256, 0, L.stream>>>(e, d_count, max_count, half_bits, newid, n, err);
+  k_rename<<<g, 256, 0, L.stream>>>(e, d_count, max_count, half_bits, rank, n, err);
 }
 
-void scan_flags(const uint32_t* flags, uint32_t* out, uint32_t n, const uint32_t* mo_in,
+void scan_flags(const uint32_t* flags, uint64_t* rank, uint32_t n, const uint32_t* mo_in,
                 uint32_t* mo_out, unsigned long long* total, SortScratch& s, unsigned* err,
                 const Launch& L) {
   if (n == 0) return;
   uint32_t epoch = next_epoch(s, L);
   cudaMemsetAsync(s.tickets + 8, 0, sizeof(unsigned), L.stream);
-  uint64_t tiles = ((uint64_t)n + kScanTile - 1) / kScanTile;
+  uint64_t tiles = (rank_words(n) + kRankTile - 1) / kRankTile;
   KScope ks(L, kKScanFlags);
-  k_scan_flags<<<(unsigned)tiles, kSortThreads, 0, L.stream>>>(flags, out, n, mo_in, mo_out, total,
-                                                              s.status, epoch, s.tickets + 8, err);
+  k_scan_flags<<<(unsigned)tiles, kSortThreads, 0, L.stream>>>(flags, rank, n, mo_in, mo_out,
+                                                              total, s.status, epoch,
+                                                              s.tickets + 8, err);
 }
 
 void unique_rename(const uint64_t* keys, const unsigned long long* d_count, uint64_t max_count,
-                   int half_bits, const uint32_t* newid, uint32_t n, uint64_t* out,
+                   int half_bits, const uint64_t* rank, uint32_t n, uint64_t* out,
                    unsigned long long* m_next, SortScratch& s, unsigned* err, const Launch& L) {
   if (max_count == 0) return;
   uint32_t epoch = next_epoch(s, L);
@@ -1380,7 +1387,7 @@ void unique_rename(const uint64_t* keys, const unsigned long long* d_count, uint
   uint64_t tiles = (max_count + kScanTile - 1) / kScanTile;
   KScope ks(L, kKUniqueRename);
   k_unique_rename<<<(unsigned)tiles, kSortThreads, 0, L.stream>>>(
-      keys, d_count, half_bits, newid, n, out, m_next, s.status, epoch, s.tickets + 9, err);
+      keys, d_count, half_bits, rank, n, out, m_next, s.status, epoch, s.tickets + 9, err);
 }
 
 }  // namespace lc
