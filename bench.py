@@ -352,7 +352,7 @@ def bench_variants(ctx, labels, stream, steps, warmup, peak, lc):
     return out
 
 
-def bench_batch(dev, stream, steps=5, k=4096, world=1, rank=0, barrier=None, reduce_max=None):
+def bench_batch(dev, stream, steps=9, k=4096, world=1, rank=0, barrier=None, reduce_max=None):
     """Config 4: 4096 independent graphs (n log-uniform in [2^6, 2^16]; half ER
     with average degree 4, half R-MAT with average degree 16), one batched
     context vs one lc_run per graph on the same GPU (contexts created up front
@@ -373,26 +373,35 @@ def bench_batch(dev, stream, steps=5, k=4096, world=1, rank=0, barrier=None, red
     dst = torch.from_numpy(b.dst.view(np.int32)).to(dev)
     total = int(b.n.astype(np.int64).sum())
     labels = torch.empty(max(total, 1), dtype=torch.int32, device=dev)
-    def time_batch(tuned):
-        bl = lc.BatchLocalContraction(b.n, b.eoff, src, dst, b.seeds, stream=stream, tuned=tuned)
+    # the tuned and the default context take turns, each run timed alone, so
+    # that drift of the box between the two does not decide the comparison
+    bls = {True: lc.BatchLocalContraction(b.n, b.eoff, src, dst, b.seeds, stream=stream,
+                                          tuned=True)}
+    params = dict(bls[True].params)
+    if params:
+        bls[False] = lc.BatchLocalContraction(b.n, b.eoff, src, dst, b.seeds, stream=stream,
+                                              tuned=False)
+    for bl in bls.values():
         for _ in range(2):
             bl.run(labels)
-        torch.cuda.synchronize(dev)
-        if barrier:
-            barrier()
-        t0 = time.perf_counter()
-        for _ in range(steps):
-            _, rounds, _, _ = bl.run(labels)
-        torch.cuda.synchronize(dev)
-        sec = (time.perf_counter() - t0) / steps
-        if reduce_max:
-            sec = reduce_max(sec)
-        params = dict(bl.params)
+    samples = {t: [] for t in bls}
+    rounds = None
+    for _ in range(steps):
+        for t, bl in bls.items():
+            torch.cuda.synchronize(dev)
+            if barrier:
+                barrier()
+            t0 = time.perf_counter()
+            _, r, _, _ = bl.run(labels)
+            torch.cuda.synchronize(dev)
+            sec = time.perf_counter() - t0
+            samples[t].append(reduce_max(sec) if reduce_max else sec)
+            if t:
+                rounds = r
+    for bl in bls.values():
         bl.close()
-        return sec, rounds, params
-
-    batched_s, rounds, params = time_batch(True)
-    default_s = time_batch(False)[0] if params else batched_s
+    batched_s = float(np.median(samples[True]))
+    default_s = float(np.median(samples[False])) if params else batched_s
     workload = "4096 graphs, n log-uniform [2^6, 2^16], ER deg 4 / R-MAT deg 16"
     if world > 1:
         return {"workload": workload, "graphs": k, "ranks": world, "graphs_this_rank": k_mine,
@@ -767,8 +776,9 @@ def main():
         torch.cuda.empty_cache()
         batched = bench_batch(dev, stream, world=world, rank=rank, barrier=barrier,
                               reduce_max=reduce_max)
-        log("batched: %.0f graphs/s (one run per graph: %s graphs/s)" % (
-            batched["batched_graphs_per_s"], batched.get("per_graph_graphs_per_s")))
+        log("batched: %.0f graphs/s, %.2f ms tuned vs %.2f ms defaults (one run per graph: %s "
+            "graphs/s)" % (batched["batched_graphs_per_s"], batched["batched_ms"],
+                           batched["default_params_ms"], batched.get("per_graph_graphs_per_s")))
     serving = None
     if not args.no_serving:
         torch.cuda.empty_cache()

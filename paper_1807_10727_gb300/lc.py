@@ -260,12 +260,13 @@ class Result:
     m_i: list
 
 
-def _apply_tuned(ctx: int, n: int, m: int) -> dict:
+def _apply_tuned(ctx: int, n: int, m: int, kind: str = "single") -> dict:
     """Speed parameters measured by the autotuner (tune.py) for the size class
-    nearest to (n, m), set on the context; {} when the table has none."""
+    of this kind nearest to (n, m), set on the context; {} when the table has
+    none."""
     from . import tune
     applied = {}
-    for name, value in tune.params_for(n, m).items():
+    for name, value in tune.params_for(n, m, kind).items():
         try:
             lc_set_param(ctx, name, int(value))
             applied[name] = int(value)
@@ -372,7 +373,7 @@ class BatchLocalContraction:
                                    _stream_handle(stream))
         if variant != LC_VARIANT_FOREST:
             lc_configure(self.ctx, variant, 0)
-        self.params = _apply_tuned(self.ctx, int(self.voff[-1]), m) if tuned else {}
+        self.params = _apply_tuned(self.ctx, int(self.voff[-1]), m, "batch") if tuned else {}
 
     def run(self, labels=None, cap: int = 256):
         import torch

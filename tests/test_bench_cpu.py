@@ -68,12 +68,13 @@ def test_step_report_and_roofline():
 
 
 def test_tuned_table_lookup(tmp_path, monkeypatch):
-    """The binding applies the entry of the nearest size class in (log2 n,
-    log2 m), and nothing when no class is near."""
+    """The binding applies the entry of the nearest size class of the same
+    kind in (log2 n, log2 m), and nothing when no class is near."""
     from paper_1807_10727_gb300 import tune
     table = {"classes": [
         {"n_log2": 20, "m_log2": 24, "params": {"relabel_cache_admit": 2}},
-        {"n_log2": 26, "m_log2": 30, "params": {"bucket_window_bytes": 32 << 20}}]}
+        {"n_log2": 26, "m_log2": 30, "kind": "single", "params": {"bucket_window_bytes": 32 << 20}},
+        {"n_log2": 26, "m_log2": 28, "kind": "batch", "params": {"seg_dedup": 0}}]}
     path = tmp_path / "tuned.json"
     path.write_text(json.dumps(table))
     monkeypatch.setattr(tune, "_table", None)
@@ -81,5 +82,10 @@ def test_tuned_table_lookup(tmp_path, monkeypatch):
     assert tune.params_for(1 << 26, 1 << 30) == {"bucket_window_bytes": 32 << 20}
     assert tune.params_for((1 << 20) + 5, 3 << 22) == {"relabel_cache_admit": 2}
     assert tune.params_for(1 << 10, 1 << 12) == {}
+    # batches take batch classes only, single graphs single-graph classes only
+    assert tune.params_for(1 << 26, 1 << 28, "batch") == {"seg_dedup": 0}
+    assert tune.params_for(1 << 26, 1 << 30, "batch") == {"seg_dedup": 0}
+    assert tune.params_for(1 << 20, 1 << 24, "batch") == {}
+    assert tune.params_for(1 << 26, 1 << 28) == {"bucket_window_bytes": 32 << 20}
     assert tune.class_key(1, 0) == (0, 0)
     monkeypatch.setattr(tune, "_table", None)
