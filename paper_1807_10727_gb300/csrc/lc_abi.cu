@@ -241,6 +241,7 @@ struct BatchState {
   uint32_t* d_voff0 = nullptr;  // [k+1] vertex offsets of the input
   uint64_t* d_eoff = nullptr;   // [k+1] edge offsets of the input
   uint64_t* d_rk = nullptr;     // [k] phase seeds of the current phase
+  uint32_t* d_gid = nullptr;    // [n] graph of every vertex of the current level
   const uint32_t* user_src = nullptr;  // caller's edges, local ids
   const uint32_t* user_dst = nullptr;
   std::vector<uint64_t> h_eoff;
@@ -354,6 +355,7 @@ static void free_ctx(lc_ctx* c) {
     dev_free(c->mem, c->batch->d_voff0);
     dev_free(c->mem, c->batch->d_eoff);
     dev_free(c->mem, c->batch->d_rk);
+    dev_free(c->mem, c->batch->d_gid);
     delete c->batch;
   }
   dev_free(c->mem, c->sort.status);
@@ -582,12 +584,13 @@ static lc_status enqueue_phase(lc_ctx* c) {
       if (aerr != cudaSuccess) return fail(c, status_of(aerr));
       uint32_t* mcnt = c->arena.alloc(b->k, &aerr);
       if (aerr != cudaSuccess) return fail(c, status_of(aerr));
-      batch_next_level(b->voff.back(), c->levels.back().rank, b->k, voff, r.packed, mi, mcnt, L);
+      batch_next_level(b->voff.back(), c->levels.back().rank, b->k, voff, r.packed, mi, mcnt, ni,
+                       b->d_gid, L);
       b->voff.push_back(voff);
       b->mcnt.push_back(mcnt);
     }
     batch_phase_seeds(b->d_seeds, b->k, i, b->d_rk, L);
-    bv = BatchView{b->d_rk, b->voff.back(), b->k};
+    bv = BatchView{b->d_rk, b->voff.back(), b->k, b->d_gid};
   }
   const BatchView* bp = c->batch ? &bv : nullptr;
   // the input edges are read only by phase 0 itself (a merge step after
@@ -947,6 +950,7 @@ static lc_status run_begin(lc_ctx* c, uint32_t* d_labels, const uint32_t* h_src 
     b->mcnt.clear();
     batch_globalize(b->user_src, b->user_dst, b->d_eoff, b->d_voff0, b->k, c->m, c->own_src,
                     c->own_dst, &c->ctr->err, c->L);
+    batch_graph_ids(b->d_voff0, b->k, c->n, b->d_gid, c->L);
   }
   cudaError_t aerr = cudaSuccess;
   r.ni = c->n;
@@ -1177,6 +1181,7 @@ extern "C" lc_status lc_batch_create(uint32_t k, const uint32_t* h_n, const uint
   if (e == cudaSuccess) e = dev_alloc(c->mem, &b->d_voff0, 4ull * (k + 1));
   if (e == cudaSuccess) e = dev_alloc(c->mem, &b->d_eoff, 8ull * (k + 1));
   if (e == cudaSuccess) e = dev_alloc(c->mem, &b->d_rk, 8ull * k);
+  if (e == cudaSuccess) e = dev_alloc(c->mem, &b->d_gid, 4ull * std::max<uint64_t>(tot, 1));
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(b->d_seeds, h_seeds, 8ull * k, cudaMemcpyHostToDevice, c->stream);
   if (e == cudaSuccess)

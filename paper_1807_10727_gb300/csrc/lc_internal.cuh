@@ -288,6 +288,7 @@ struct BatchView {
   const uint64_t* rk;
   const uint32_t* voff;
   uint32_t k;
+  const uint32_t* gid;  // graph of every vertex of the level (batch_graph_ids)
 };
 
 // minkey[v] = key(v) for v < n; when mo is non-null also mo[v] = v (phase 0).
@@ -310,16 +311,19 @@ void edge_min(const uint32_t* src, const uint32_t* dst, const uint64_t* packed, 
 
 // Batches: phase seeds rk[g] for phase i; local -> global edge ids (ids
 // validated per graph); next level offsets voff_next[g] = id(voff[g]) (keep
-// ranks of the level) and
-// per-graph edge counts of the next level's packed edges e[0, m); global ->
-// local labels.
+// ranks of the level), the next level's graph ids gid[0, n_next) and the
+// per-graph edge counts of its packed edges e[0, m); global -> local labels.
 void batch_phase_seeds(const uint64_t* seeds, uint32_t k, uint32_t i, uint64_t* rk,
                        const Launch& L);
 void batch_globalize(const uint32_t* src, const uint32_t* dst, const uint64_t* eoff,
                      const uint32_t* voff, uint32_t k, uint64_t m, uint32_t* gsrc, uint32_t* gdst,
                      unsigned* err, const Launch& L);
 void batch_next_level(const uint32_t* voff, const uint64_t* rank, uint32_t k, uint32_t* voff_next,
-                      const uint64_t* e, uint64_t m, uint32_t* mcnt, const Launch& L);
+                      const uint64_t* e, uint64_t m, uint32_t* mcnt, uint32_t n_next,
+                      uint32_t* gid, const Launch& L);
+// gid[v] = graph of vertex v, v < n = voff[k].
+void batch_graph_ids(const uint32_t* voff, uint32_t k, uint32_t n, uint32_t* gid,
+                     const Launch& L);
 void batch_localize(uint32_t* labels, uint32_t n, const uint32_t* voff, uint32_t k,
                     const Launch& L);
 

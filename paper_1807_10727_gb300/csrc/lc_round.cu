@@ -41,7 +41,9 @@ struct BatchKeys {
   const uint64_t* rk;
   const uint32_t* voff;
   uint32_t k;
+  const uint32_t* gid = nullptr;  // graph of every vertex of the level (nullptr: search voff)
   __device__ __forceinline__ uint32_t graph_of(uint32_t v) const {
+    if (gid != nullptr) return __ldg(gid + v);
     uint32_t lo = 0, hi = k - 1;  // last g with voff[g] <= v
     while (lo < hi) {
       uint32_t mid = (lo + hi + 1) >> 1;
@@ -184,30 +186,73 @@ __global__ void k_batch_phase_seeds(const uint64_t* __restrict__ seeds, uint32_t
     rk[g] = splitmix_mix(seeds[g] + (uint64_t)(i + 1) * kGamma);
 }
 
+// Last g with off[g] <= x in a non-decreasing offset array off[0..k].
+template <class T>
+__device__ __forceinline__ uint32_t segment_of(const T* __restrict__ off, uint32_t k, uint64_t x) {
+  uint32_t lo = 0, hi = k - 1;
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi + 1) >> 1;
+    if ((uint64_t)__ldg(off + mid) <= x) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Work split of the batch kernels that walk a range in offset order: warp w
+// takes items [w * chunk, (w + 1) * chunk) (chunk a multiple of 32), four
+// per lane per step; lane 0 finds the segment of the chunk's first item by
+// binary search and every lane carries its segment index forward, so a warp
+// searches once per chunk and each lane walks past every segment boundary of
+// the chunk once.
+constexpr int kWalkItems = 4;
+
 // Local edge ids -> global ids: edge j of graph g (eoff[g] <= j < eoff[g+1])
 // gets voff[g] added to both endpoints; local ids >= n_g set kErrBadVertex
 // and become a self-loop on the graph's first vertex.
 __global__ void k_batch_globalize(const uint32_t* __restrict__ src, const uint32_t* __restrict__ dst,
                                   const uint64_t* __restrict__ eoff,
                                   const uint32_t* __restrict__ voff, uint32_t k, uint64_t m,
-                                  uint32_t* __restrict__ gsrc, uint32_t* __restrict__ gdst,
-                                  unsigned* err) {
-  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += stride) {
-    uint32_t lo = 0, hi = k - 1;  // last g with eoff[g] <= j
-    while (lo < hi) {
-      uint32_t mid = (lo + hi + 1) >> 1;
-      if (__ldg(eoff + mid) <= j) lo = mid;
-      else hi = mid - 1;
+                                  uint64_t chunk, uint32_t* __restrict__ gsrc,
+                                  uint32_t* __restrict__ gdst, unsigned* err) {
+  const uint64_t c0 = (((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * chunk;
+  if (c0 >= m) return;  // whole warps leave together
+  const uint64_t c1 = c0 + chunk < m ? c0 + chunk : m;
+  const unsigned lane = lane_id();
+  uint32_t g = lane == 0 ? segment_of(eoff, k, c0) : 0u;
+  g = __shfl_sync(kFull, g, 0);
+  for (uint64_t j0 = c0 + lane; j0 < c1; j0 += 32 * kWalkItems) {
+    uint32_t u[kWalkItems], v[kWalkItems];
+#pragma unroll
+    for (int q = 0; q < kWalkItems; ++q) {
+      const uint64_t j = j0 + 32ull * q;
+      u[q] = j < c1 ? src[j] : 0u;
+      v[q] = j < c1 ? dst[j] : 0u;
     }
-    const uint32_t base = __ldg(voff + lo), ng = __ldg(voff + lo + 1) - base;
-    uint32_t u = src[j], v = dst[j];
-    if (u >= ng || v >= ng) {
-      atomicOr(err, kErrBadVertex);
-      u = v = 0;
+#pragma unroll
+    for (int q = 0; q < kWalkItems; ++q) {
+      const uint64_t j = j0 + 32ull * q;
+      if (j >= c1) break;
+      while (g + 1 < k && __ldg(eoff + g + 1) <= j) ++g;
+      const uint32_t base = __ldg(voff + g), ng = __ldg(voff + g + 1) - base;
+      uint32_t a = u[q], b = v[q];
+      if (a >= ng || b >= ng) {
+        atomicOr(err, kErrBadVertex);
+        a = b = 0;
+      }
+      gsrc[j] = base + a;
+      gdst[j] = base + b;
     }
-    gsrc[j] = base + u;
-    gdst[j] = base + v;
+  }
+}
+
+// gid[v] = graph of vertex v for v < voff[k]: one warp per graph, so that a
+// level whose graphs are mostly empty costs one check per graph.
+__global__ void k_batch_gid(const uint32_t* __restrict__ voff, uint32_t k,
+                            uint32_t* __restrict__ gid) {
+  const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+  for (uint32_t g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < k; g += nw) {
+    const uint32_t a = __ldg(voff + g), b = __ldg(voff + g + 1);
+    for (uint32_t v = a + lane_id(); v < b; v += 32) gid[v] = g;
   }
 }
 
@@ -224,23 +269,43 @@ __global__ void k_batch_next_offsets(const uint32_t* __restrict__ voff,
 }
 
 // mcnt[g] += number of packed edges (a << 32 | b) whose endpoint a lies in
-// graph g's range of voff.
+// graph g (gid: graph of every vertex of the level).  With `local` (k words
+// of dynamic shared memory) a block first counts in shared memory and then
+// adds its nonzero counts, so the global atomics no longer pile up on the
+// few lines that hold the counters.
 __global__ void k_batch_count_edges(const uint64_t* __restrict__ e, uint64_t m,
-                                    const uint32_t* __restrict__ voff, uint32_t k,
+                                    const uint32_t* __restrict__ gid, uint32_t k, int local,
                                     uint32_t* __restrict__ mcnt) {
-  BatchKeys b{nullptr, voff, k};
+  extern __shared__ uint32_t s_cnt[];
+  if (local) {
+    for (uint32_t g = threadIdx.x; g < k; g += blockDim.x) s_cnt[g] = 0;
+    __syncthreads();
+  }
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += stride)
-    atomicAdd(&mcnt[b.graph_of((uint32_t)(e[j] >> 32))], 1u);
+  for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += stride) {
+    const uint32_t g = __ldg(gid + (uint32_t)(e[j] >> 32));
+    atomicAdd(local ? &s_cnt[g] : &mcnt[g], 1u);
+  }
+  if (local) {
+    __syncthreads();
+    for (uint32_t g = threadIdx.x; g < k; g += blockDim.x)
+      if (s_cnt[g]) atomicAdd(&mcnt[g], s_cnt[g]);
+  }
 }
 
-// labels[v] -= voff[graph of v]: global labels to per-graph local labels.
+// labels[v] -= voff[graph of v]: global labels to per-graph local labels
+// (vertex chunks per warp as in k_batch_globalize).
 __global__ void k_batch_localize(uint32_t* __restrict__ labels, uint32_t n,
-                                 const uint32_t* __restrict__ voff, uint32_t k) {
-  BatchKeys b{nullptr, voff, k};
-  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride)
-    labels[v] -= __ldg(voff + b.graph_of((uint32_t)v));
+                                 const uint32_t* __restrict__ voff, uint32_t k, uint64_t chunk) {
+  const uint64_t c0 = (((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * chunk;
+  if (c0 >= n) return;  // whole warps leave together
+  const uint64_t c1 = c0 + chunk < n ? c0 + chunk : n;
+  uint32_t g = lane_id() == 0 ? segment_of(voff, k, c0) : 0u;
+  g = __shfl_sync(kFull, g, 0);
+  for (uint64_t v = c0 + lane_id(); v < c1; v += 32) {
+    while (g + 1 < k && __ldg(voff + g + 1) <= v) ++g;
+    labels[v] -= __ldg(voff + g);
+  }
 }
 
 // ------------------------------------------------------- pointer jumping
@@ -772,7 +837,7 @@ void init_keys(unsigned long long* minkey, uint32_t* mo, uint32_t n, uint64_t rk
   KScope ks(L, kKInitKeys);
   if (batch)
     k_init_keys<<<grid_for(n, kThreads, L), kThreads, 0, L.stream>>>(
-        minkey, mo, n, BatchKeys{batch->rk, batch->voff, batch->k});
+        minkey, mo, n, BatchKeys{batch->rk, batch->voff, batch->k, batch->gid});
   else
     k_init_keys<<<grid_for(n, kThreads, L), kThreads, 0, L.stream>>>(minkey, mo, n, GraphKeys{rk});
 }
@@ -806,7 +871,7 @@ void edge_min(const uint32_t* src, const uint32_t* dst, const uint64_t* packed, 
               uint64_t window_bytes, const BatchView* batch, const Launch& L, bool open) {
   if (m == 0) return;
   if (batch) {
-    const BatchKeys k{batch->rk, batch->voff, batch->k};
+    const BatchKeys k{batch->rk, batch->voff, batch->k, batch->gid};
     if (open) edge_min_impl<true>(src, dst, packed, m, n, k, minkey, err, window_bytes, L);
     else edge_min_impl<false>(src, dst, packed, m, n, k, minkey, err, window_bytes, L);
   } else {
@@ -815,6 +880,16 @@ void edge_min(const uint32_t* src, const uint32_t* dst, const uint64_t* packed, 
     else edge_min_impl<false>(src, dst, packed, m, n, k, minkey, err, window_bytes, L);
   }
 }
+
+// Items per warp of the chunked walks (a multiple of 32), for `grid` blocks.
+static uint64_t walk_chunk(uint64_t items, int grid) {
+  const uint64_t warps = (uint64_t)grid * (kThreads / 32);
+  const uint64_t per = (items + warps - 1) / warps;
+  return (per + 31) / 32 * 32;
+}
+
+// Largest k whose per-graph edge counts a block keeps in shared memory.
+constexpr uint32_t kCountLocalMax = 8192;
 
 void batch_phase_seeds(const uint64_t* seeds, uint32_t k, uint32_t i, uint64_t* rk,
                        const Launch& L) {
@@ -826,27 +901,47 @@ void batch_globalize(const uint32_t* src, const uint32_t* dst, const uint64_t* e
                      const uint32_t* voff, uint32_t k, uint64_t m, uint32_t* gsrc, uint32_t* gdst,
                      unsigned* err, const Launch& L) {
   if (m == 0) return;
+  const int grid = grid_for(m, kThreads, L);
+  const uint64_t chunk = walk_chunk(m, grid);
   KScope ks(L, kKBatch);
-  k_batch_globalize<<<grid_for(m, kThreads, L), kThreads, 0, L.stream>>>(src, dst, eoff, voff, k,
-                                                                         m, gsrc, gdst, err);
+  k_batch_globalize<<<grid, kThreads, 0, L.stream>>>(src, dst, eoff, voff, k, m, chunk, gsrc,
+                                                     gdst, err);
+}
+
+void batch_graph_ids(const uint32_t* voff, uint32_t k, uint32_t n, uint32_t* gid,
+                     const Launch& L) {
+  if (n == 0) return;
+  KScope ks(L, kKBatch);
+  k_batch_gid<<<grid_for(32ull * k, kThreads, L), kThreads, 0, L.stream>>>(voff, k, gid);
 }
 
 void batch_next_level(const uint32_t* voff, const uint64_t* rank, uint32_t k, uint32_t* voff_next,
-                      const uint64_t* e, uint64_t m, uint32_t* mcnt, const Launch& L) {
-  KScope ks(L, kKBatch);
-  k_batch_next_offsets<<<grid_for(k + 1, kThreads, L), kThreads, 0, L.stream>>>(voff, rank, k,
-                                                                                voff_next);
+                      const uint64_t* e, uint64_t m, uint32_t* mcnt, uint32_t n_next,
+                      uint32_t* gid, const Launch& L) {
+  {
+    KScope ks(L, kKBatch);
+    k_batch_next_offsets<<<grid_for(k + 1, kThreads, L), kThreads, 0, L.stream>>>(voff, rank, k,
+                                                                                  voff_next);
+  }
+  batch_graph_ids(voff_next, k, n_next, gid, L);
   cudaMemsetAsync(mcnt, 0, sizeof(uint32_t) * k, L.stream);
-  if (m)
-    k_batch_count_edges<<<grid_for(m, kThreads, L), kThreads, 0, L.stream>>>(e, m, voff_next, k,
-                                                                             mcnt);
+  if (m) {
+    KScope ks(L, kKBatch);
+    const int local = k <= kCountLocalMax;
+    // fewer blocks when counting locally: each block adds up to k counts
+    const int grid = grid_for(m, kThreads, L, local ? 4 : 8);
+    k_batch_count_edges<<<grid, kThreads, local ? 4 * k : 0, L.stream>>>(
+        e, m, gid, k, local, mcnt);
+  }
 }
 
 void batch_localize(uint32_t* labels, uint32_t n, const uint32_t* voff, uint32_t k,
                     const Launch& L) {
   if (n == 0) return;
+  const int grid = grid_for(n, kThreads, L);
+  const uint64_t chunk = walk_chunk(n, grid);
   KScope ks(L, kKBatch);
-  k_batch_localize<<<grid_for(n, kThreads, L), kThreads, 0, L.stream>>>(labels, n, voff, k);
+  k_batch_localize<<<grid, kThreads, 0, L.stream>>>(labels, n, voff, k, chunk);
 }
 
 void jump(unsigned long long* minkey, uint32_t* root, uint32_t* mo, uint32_t n, unsigned* err,
@@ -946,7 +1041,7 @@ void two_hop_names(const uint32_t* src, const uint32_t* dst, const uint64_t* pac
   }
   if (m) {
     if (batch)
-      two_hop_impl(src, dst, packed, m, n, BatchKeys{batch->rk, batch->voff, batch->k}, fpar,
+      two_hop_impl(src, dst, packed, m, n, BatchKeys{batch->rk, batch->voff, batch->k, batch->gid}, fpar,
                    mk2, err, L);
     else
       two_hop_impl(src, dst, packed, m, n, GraphKeys{rk}, fpar, mk2, err, L);
@@ -963,7 +1058,7 @@ void tree_names(const unsigned long long* minkey, uint32_t* root, uint32_t* mo, 
   KScope ks(L, kKTreeNames);
   if (batch)
     k_tree_names<<<grid_for(n, kThreads, L), kThreads, 0, L.stream>>>(
-        minkey, root, mo, n, BatchKeys{batch->rk, batch->voff, batch->k}, err);
+        minkey, root, mo, n, BatchKeys{batch->rk, batch->voff, batch->k, batch->gid}, err);
   else
     k_tree_names<<<grid_for(n, kThreads, L), kThreads, 0, L.stream>>>(minkey, root, mo, n,
                                                                       GraphKeys{rk}, err);

@@ -53,7 +53,10 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* w
 
 // Publishes this tile's aggregate, walks back over preceding tiles until an
 // inclusive prefix is found, publishes its own inclusive prefix and returns
-// the exclusive prefix.  Every wait is bounded by kSpinLimit.
+// the exclusive prefix.  Every wait is bounded by kSpinLimit.  After a wait
+// runs out, the published prefix is only a lower bound (the offsets behind it
+// come out too low, so writes stay inside the output) and kErrTimeout makes
+// the host discard the phase.
 __device__ __forceinline__ uint32_t look_back(uint64_t* status, uint32_t tile, uint32_t agg,
                                               uint32_t epoch, unsigned* err) {
   if (tile == 0) {
@@ -74,7 +77,9 @@ __device__ __forceinline__ uint32_t look_back(uint64_t* status, uint32_t tile, u
       }
       if (flag == kFlagAgg) {
         excl += (uint32_t)w;
-        --j;  // tile 0 always publishes a prefix, so j never wraps
+        // j stops at 0 at the latest: tile 0 publishes only prefixes, and
+        // if it publishes nothing the wait runs out at j = 0
+        --j;
         spins = 0;
         continue;
       }
@@ -994,12 +999,18 @@ __global__ void __launch_bounds__(kSortThreads) k_seg_insert(
   const uint32_t t0 = tiles[seg_lo], t1 = tiles[seg_hi];
   const uint64_t half_mask = (1ull << half_bits) - 1;
   const uint64_t smask = slots - 1;
-  if (tid == 0) s_new = 0;
+  // thread 0 claims the next tile while this one is processed (the claim's
+  // round trip is hidden) and publishes it after the tile's closing barrier
+  uint32_t next_t = 0;
+  if (tid == 0) {
+    s_new = 0;
+    s_t = t0 + atomicAdd(ticket, 1u);
+  }
+  __syncthreads();
   for (;;) {
-    if (tid == 0) s_t = t0 + atomicAdd(ticket, 1u);
-    __syncthreads();
     const uint32_t t = s_t;
     if (t >= t1) break;
+    if (tid == 0) next_t = t0 + atomicAdd(ticket, 1u);
     // segment of tile t: last s in [seg_lo, seg_hi) with tiles[s] <= t
     uint32_t lo = seg_lo, hi = seg_hi - 1;
     while (lo < hi) {
@@ -1060,7 +1071,11 @@ __global__ void __launch_bounds__(kSortThreads) k_seg_insert(
       }
     }
     __syncthreads();
-    if (tid == 0) s_new = 0;
+    if (tid == 0) {
+      s_new = 0;
+      s_t = next_t;
+    }
+    __syncthreads();
   }
 }
 
