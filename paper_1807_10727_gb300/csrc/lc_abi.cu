@@ -240,7 +240,7 @@ struct BatchState {
   uint64_t* d_seeds = nullptr;  // [k] rank seeds
   uint32_t* d_voff0 = nullptr;  // [k+1] vertex offsets of the input
   uint64_t* d_eoff = nullptr;   // [k+1] edge offsets of the input
-  uint64_t* d_rk = nullptr;     // [k] phase seeds of the current phase
+  uint64_t* d_rk = nullptr;     // [k] phase seeds of the current phase (BatchView::gs)
   uint32_t* d_gid = nullptr;    // [n] graph of every vertex of the current level
   const uint32_t* user_src = nullptr;  // caller's edges, local ids
   const uint32_t* user_dst = nullptr;
@@ -589,7 +589,7 @@ static lc_status enqueue_phase(lc_ctx* c) {
       b->voff.push_back(voff);
       b->mcnt.push_back(mcnt);
     }
-    batch_phase_seeds(b->d_seeds, b->k, i, b->d_rk, L);
+    batch_phase_seeds(b->d_seeds, b->k, i, b->voff.back(), b->d_rk, L);
     bv = BatchView{b->d_rk, b->voff.back(), b->k, b->d_gid};
   }
   const BatchView* bp = c->batch ? &bv : nullptr;

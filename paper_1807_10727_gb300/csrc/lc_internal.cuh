@@ -283,9 +283,10 @@ void unique_rename(const uint64_t* keys, const unsigned long long* d_count, uint
 
 // ---------------------------------------------------------- phase steps
 // A batch of independent graphs in one id space (device pointers): graph g
-// owns ids [voff[g], voff[g+1]) and uses phase seed rk[g].
+// owns ids [voff[g], voff[g+1]) and uses phase seed rk[g], passed as
+// gs[g] = rk[g] + (1 - voff[g]) * kGamma (batch_phase_seeds).
 struct BatchView {
-  const uint64_t* rk;
+  const uint64_t* gs;
   const uint32_t* voff;
   uint32_t k;
   const uint32_t* gid;  // graph of every vertex of the level (batch_graph_ids)
@@ -309,12 +310,12 @@ void edge_min(const uint32_t* src, const uint32_t* dst, const uint64_t* packed, 
               uint32_t n, uint64_t rk, unsigned long long* minkey, unsigned* err,
               uint64_t window_bytes, const BatchView* batch, const Launch& L, bool open = false);
 
-// Batches: phase seeds rk[g] for phase i; local -> global edge ids (ids
+// Batches: phase seeds gs[g] for phase i (see BatchView); local -> global edge ids (ids
 // validated per graph); next level offsets voff_next[g] = id(voff[g]) (keep
 // ranks of the level), the next level's graph ids gid[0, n_next) and the
 // per-graph edge counts of its packed edges e[0, m); global -> local labels.
-void batch_phase_seeds(const uint64_t* seeds, uint32_t k, uint32_t i, uint64_t* rk,
-                       const Launch& L);
+void batch_phase_seeds(const uint64_t* seeds, uint32_t k, uint32_t i, const uint32_t* voff,
+                       uint64_t* gs, const Launch& L);
 void batch_globalize(const uint32_t* src, const uint32_t* dst, const uint64_t* eoff,
                      const uint32_t* voff, uint32_t k, uint64_t m, uint32_t* gsrc, uint32_t* gdst,
                      unsigned* err, const Launch& L);

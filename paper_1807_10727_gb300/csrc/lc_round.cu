@@ -38,7 +38,7 @@ struct GraphKeys {
 // the same) so that it can index the per-vertex arrays.  Edges never cross
 // graphs, so both endpoints of an edge share one lookup.
 struct BatchKeys {
-  const uint64_t* rk;
+  const uint64_t* gs;  // per graph: phase seed rk[g] + (1 - voff[g]) * kGamma (mod 2^64)
   const uint32_t* voff;
   uint32_t k;
   const uint32_t* gid = nullptr;  // graph of every vertex of the level (nullptr: search voff)
@@ -52,9 +52,10 @@ struct BatchKeys {
     }
     return lo;
   }
+  // rk[g] + (v - voff[g] + 1) * kGamma, the stream input of local id
+  // v - voff[g], equals gs[g] + v * kGamma: one per-graph word per key
   __device__ __forceinline__ uint64_t key_in(uint32_t g, uint32_t v) const {
-    const uint64_t local = v - __ldg(voff + g);
-    return (splitmix_mix(__ldg(rk + g) + (local + 1ull) * kGamma) & 0xFFFFFFFF00000000ull) | v;
+    return (splitmix_mix(__ldg(gs + g) + (uint64_t)v * kGamma) & 0xFFFFFFFF00000000ull) | v;
   }
   __device__ __forceinline__ uint64_t key(uint32_t v) const { return key_in(graph_of(v), v); }
   __device__ __forceinline__ void pair(uint32_t u, uint32_t v, uint64_t& ku, uint64_t& kv) const {
@@ -179,11 +180,13 @@ __global__ void __launch_bounds__(kThreads) k_edge_min_packed(
 
 // ------------------------------------------------------- batches
 
-// rk[g] = stream seed of phase i for graph g.
+// gs[g] = rk[g] + (1 - voff[g]) * kGamma, with rk[g] the stream seed of
+// phase i for graph g (see BatchKeys).
 __global__ void k_batch_phase_seeds(const uint64_t* __restrict__ seeds, uint32_t k, uint32_t i,
-                                    uint64_t* __restrict__ rk) {
+                                    const uint32_t* __restrict__ voff, uint64_t* __restrict__ gs) {
   for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < k; g += gridDim.x * blockDim.x)
-    rk[g] = splitmix_mix(seeds[g] + (uint64_t)(i + 1) * kGamma);
+    gs[g] = splitmix_mix(seeds[g] + (uint64_t)(i + 1) * kGamma) + kGamma -
+            (uint64_t)voff[g] * kGamma;
 }
 
 // Last g with off[g] <= x in a non-decreasing offset array off[0..k].
@@ -837,7 +840,7 @@ void init_keys(unsigned long long* minkey, uint32_t* mo, uint32_t n, uint64_t rk
   KScope ks(L, kKInitKeys);
   if (batch)
     k_init_keys<<<grid_for(n, kThreads, L), kThreads, 0, L.stream>>>(
-        minkey, mo, n, BatchKeys{batch->rk, batch->voff, batch->k, batch->gid});
+        minkey, mo, n, BatchKeys{batch->gs, batch->voff, batch->k, batch->gid});
   else
     k_init_keys<<<grid_for(n, kThreads, L), kThreads, 0, L.stream>>>(minkey, mo, n, GraphKeys{rk});
 }
@@ -871,7 +874,7 @@ void edge_min(const uint32_t* src, const uint32_t* dst, const uint64_t* packed, 
               uint64_t window_bytes, const BatchView* batch, const Launch& L, bool open) {
   if (m == 0) return;
   if (batch) {
-    const BatchKeys k{batch->rk, batch->voff, batch->k, batch->gid};
+    const BatchKeys k{batch->gs, batch->voff, batch->k, batch->gid};
     if (open) edge_min_impl<true>(src, dst, packed, m, n, k, minkey, err, window_bytes, L);
     else edge_min_impl<false>(src, dst, packed, m, n, k, minkey, err, window_bytes, L);
   } else {
@@ -891,10 +894,10 @@ static uint64_t walk_chunk(uint64_t items, int grid) {
 // Largest k whose per-graph edge counts a block keeps in shared memory.
 constexpr uint32_t kCountLocalMax = 8192;
 
-void batch_phase_seeds(const uint64_t* seeds, uint32_t k, uint32_t i, uint64_t* rk,
-                       const Launch& L) {
+void batch_phase_seeds(const uint64_t* seeds, uint32_t k, uint32_t i, const uint32_t* voff,
+                       uint64_t* gs, const Launch& L) {
   KScope ks(L, kKBatch);
-  k_batch_phase_seeds<<<grid_for(k, kThreads, L), kThreads, 0, L.stream>>>(seeds, k, i, rk);
+  k_batch_phase_seeds<<<grid_for(k, kThreads, L), kThreads, 0, L.stream>>>(seeds, k, i, voff, gs);
 }
 
 void batch_globalize(const uint32_t* src, const uint32_t* dst, const uint64_t* eoff,
@@ -1041,7 +1044,7 @@ void two_hop_names(const uint32_t* src, const uint32_t* dst, const uint64_t* pac
   }
   if (m) {
     if (batch)
-      two_hop_impl(src, dst, packed, m, n, BatchKeys{batch->rk, batch->voff, batch->k, batch->gid}, fpar,
+      two_hop_impl(src, dst, packed, m, n, BatchKeys{batch->gs, batch->voff, batch->k, batch->gid}, fpar,
                    mk2, err, L);
     else
       two_hop_impl(src, dst, packed, m, n, GraphKeys{rk}, fpar, mk2, err, L);
@@ -1058,7 +1061,7 @@ void tree_names(const unsigned long long* minkey, uint32_t* root, uint32_t* mo, 
   KScope ks(L, kKTreeNames);
   if (batch)
     k_tree_names<<<grid_for(n, kThreads, L), kThreads, 0, L.stream>>>(
-        minkey, root, mo, n, BatchKeys{batch->rk, batch->voff, batch->k, batch->gid}, err);
+        minkey, root, mo, n, BatchKeys{batch->gs, batch->voff, batch->k, batch->gid}, err);
   else
     k_tree_names<<<grid_for(n, kThreads, L), kThreads, 0, L.stream>>>(minkey, root, mo, n,
                                                                       GraphKeys{rk}, err);
