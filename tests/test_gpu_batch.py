@@ -79,6 +79,22 @@ def test_batch_single_graph_equals_config1(lc_lib, cuda):
                 np.array([g.seed], np.uint64), cuda)
 
 
+def test_batch_many_small_graphs(lc_lib, cuda):
+    """More graphs than a block keeps per-graph edge counts for in shared
+    memory (8192), with empty and edgeless graphs in between: the per-level
+    graph ids, the chunked offset walks and the global edge counting."""
+    rng = np.random.default_rng(77)
+    k = 9000
+    n = rng.integers(0, 40, size=k).astype(np.uint32)
+    n[rng.random(k) < 0.1] = 0
+    m = np.where(n > 0, rng.integers(0, 3 * n + 1), 0).astype(np.uint64)
+    eoff = np.concatenate([[0], np.cumsum(m)]).astype(np.uint64)
+    src = np.concatenate([rng.integers(0, max(int(x), 1), size=int(c)) for x, c in zip(n, m)])
+    dst = np.concatenate([rng.integers(0, max(int(x), 1), size=int(c)) for x, c in zip(n, m)])
+    check_batch(n, eoff, src.astype(np.uint32), dst.astype(np.uint32),
+                np.arange(k, dtype=np.uint64) * 7 + 1, cuda)
+
+
 def test_batch_local_id_out_of_range(lc_lib, cuda):
     n = np.array([3, 3], dtype=np.uint32)
     eoff = np.array([0, 1, 2], dtype=np.uint64)
