@@ -222,6 +222,7 @@ struct RunState {
   bool seg = false;         // the kept keys lie in segment regions (segmented dedup)
   bool pre0 = false;        // phase 0's ranks, bucket counts and minimum ran as the input
                             // arrived (lc_run_host)
+  uint32_t pre0_chunks = 0; // > 0: each of these input chunks was grouped on arrival
   uint32_t* d_labels = nullptr;
   uint32_t i = 0, ni = 0;
   uint64_t mi = 0;
@@ -294,6 +295,10 @@ struct lc_ctx {
   uint64_t window_bytes = 192ull << 20;  // L2 budget of one phase-0 minimum pass
   uint64_t relabel_window_bytes = 160ull << 20;  // root-array size above which relabel splits
   uint32_t* bucket_scratch = nullptr;            // counts and fill counters of the edge buckets
+  uint32_t* chunk_scratch = nullptr;             // lc_run_host: bucket scratch per input chunk
+  uint64_t chunk_scratch_bytes = 0;
+  uint64_t* chunk_tile_buf = nullptr;            // lc_run_host: relabel tiles over the chunks
+  uint64_t chunk_tile_bytes = 0;
   uint32_t bucket_blocks = 0;                    // phase-0 edge buckets: 0 auto, 1 off, else blocks
   uint64_t bucket_window_bytes = 64ull << 20;    // auto: two blocks of minima fit in this
   uint32_t bucket_min_vertices = 1u << 23;       // auto: bucket only graphs of this many vertices
@@ -363,6 +368,8 @@ static void free_ctx(lc_ctx* c) {
   dev_free(c->mem, c->sort.tickets);
   dev_free(c->mem, c->bounds);
   dev_free(c->mem, c->bucket_scratch);
+  dev_free(c->mem, c->chunk_scratch);
+  dev_free(c->mem, c->chunk_tile_buf);
   dev_free(c->mem, c->dtable);
   c->arena.release();
   c->prof.release();
@@ -601,12 +608,22 @@ static lc_status enqueue_phase(lc_ctx* c) {
   // current edges in packed form (phases >= 1, or phase 0's bucketed input)
   const uint64_t* pk = r.packed;
   const uint32_t nb = first ? bucket_blocks(c, ni) : 1u;
+  const uint64_t* tiles = nullptr;  // relabel tile list (chunk-local grouping)
+  const unsigned long long* d_ntiles = nullptr;
   if (nb > 1 && mi > 0) {
     // phase 0: group the input edges by vertex-block pair, so that the steps
     // below gather from an L2-sized slice of the per-vertex arrays at a time;
     // the grouped copy goes to the buffer the relabel does not write
     uint64_t* grouped = c->ebuf[1];
-    if (r.pre0)
+    if (r.pre0 && r.pre0_chunks > 0) {
+      // grouped chunk by chunk as the input arrived: the relabel takes the
+      // (bucket, chunk) runs through a tile list, in bucket order
+      chunk_tiles(c->chunk_scratch, r.pre0_chunks, std::max<uint64_t>(c->host_chunk_edges, 1),
+                  mi, ni, nb, kRelabelTileEdges, c->chunk_tile_buf + 2,
+                  reinterpret_cast<unsigned long long*>(c->chunk_tile_buf), err, L);
+      tiles = c->chunk_tile_buf + 2;
+      d_ntiles = reinterpret_cast<const unsigned long long*>(c->chunk_tile_buf);
+    } else if (r.pre0)
       bucket_place(src0, dst0, mi, ni, nb, grouped, c->bucket_scratch, err, L);
     else
       bucket_edges(src0, dst0, mi, ni, nb, grouped, c->bucket_scratch, err, L);
@@ -718,7 +735,8 @@ static lc_status enqueue_phase(lc_ctx* c) {
           seg ? c->bucket_scratch : c->sort.hist,
           (first && pk == nullptr) ? r.alt : nullptr,
           c->relabel_window_bytes, gcache_in_relabel ? c->gcache : nullptr,
-          gcache_in_relabel ? c->gcache_slots : 0, c->gcache_admit, c->sort.tickets + 13, err, L);
+          gcache_in_relabel ? c->gcache_slots : 0, c->gcache_admit, c->sort.tickets + 13, err, L,
+          tiles, d_ntiles);
   if (late) {
     // drop repeats through the device-wide cache while sketching the distinct
     // count; the kept keys (counted in `filtered`) replace the relabelled ones
@@ -870,12 +888,19 @@ static lc_status enqueue_labels(lc_ctx* c) {
   return st == LC_OK ? st : fail(c, st);
 }
 
+// Limits of the chunk-local grouping of lc_run_host: input chunks, and
+// (bucket, chunk) runs, whose tile counts one block scans.
+constexpr uint64_t kMaxGroupedChunks = 256;
+constexpr uint64_t kMaxChunkSegments = 16384;
+
 // Phase 0's steps that need only part of the input, run while the host edges
-// are copied: the copies go chunk by chunk on a second stream, and each chunk
-// gets the bucket counts of the edge grouping and its share of the
+// are copied: the copies go chunk by chunk on a second stream, and each chunk,
+// as soon as it has arrived, is grouped by vertex-block pair inside its own
+// range of the grouped buffer (or, beyond the limits above, only counted for
+// a grouping of all edges afterwards) and gets its share of the
 // closed-neighbourhood minimum (atomic minima: any order of chunks gives the
-// same minkey) as soon as it has arrived.  Everything after the minimum needs
-// all edges.
+// same minkey).  Everything after the minimum needs all edges; the relabel
+// then walks the (bucket, chunk) runs in bucket order through a tile list.
 static lc_status copy_input_overlapped(lc_ctx* c, const uint32_t* h_src, const uint32_t* h_dst) {
   const Launch& L = c->L;
   unsigned* err = &c->ctr->err;
@@ -887,12 +912,36 @@ static lc_status copy_input_overlapped(lc_ctx* c, const uint32_t* h_src, const u
     return LC_ERR_CUDA;
   init_keys(c->minkey, nullptr, c->n, rk, nullptr, L);
   const uint32_t nb = bucket_blocks(c, c->n);
-  if (nb > 1) bucket_clear(c->n, nb, c->bucket_scratch, L);
+  const uint64_t chunk = std::max<uint64_t>(c->host_chunk_edges, 1);
+  const uint64_t chunks = (c->m + chunk - 1) / chunk;
+  // group every chunk as it arrives (its scatter then runs under the copy)
+  // when the chunks are few enough for their scratch and tile list; else
+  // count the buckets per chunk and place all edges once they are in
+  const uint64_t nbc = std::max<uint32_t>(2, std::min(nb, kBucketMaxBlocks));
+  c->rs.pre0_chunks = 0;
+  if (nb > 1 && chunks <= kMaxGroupedChunks && nbc * nbc * chunks <= kMaxChunkSegments) {
+    const uint64_t sb = 4 * kChunkScratchWords * chunks;
+    const uint64_t tb = chunk_tiles_bytes(c->m, nb, (uint32_t)chunks, kRelabelTileEdges) + 16;
+    if (c->chunk_scratch_bytes < sb) {
+      dev_free(c->mem, c->chunk_scratch);
+      c->chunk_scratch_bytes = 0;
+      if (dev_alloc(c->mem, &c->chunk_scratch, sb) != cudaSuccess) return LC_ERR_OOM;
+      c->chunk_scratch_bytes = sb;
+    }
+    if (c->chunk_tile_bytes < tb) {
+      dev_free(c->mem, c->chunk_tile_buf);
+      c->chunk_tile_bytes = 0;
+      if (dev_alloc(c->mem, &c->chunk_tile_buf, tb) != cudaSuccess) return LC_ERR_OOM;
+      c->chunk_tile_bytes = tb;
+    }
+    c->rs.pre0_chunks = (uint32_t)chunks;
+  } else if (nb > 1) {
+    bucket_clear(c->n, nb, c->bucket_scratch, L);
+  }
   // the copies may not overwrite the input before the work queued so far ends
   if (cudaEventRecord(c->copy_ev, c->stream) != cudaSuccess ||
       cudaStreamWaitEvent(c->copy_stream, c->copy_ev, 0) != cudaSuccess)
     return LC_ERR_CUDA;
-  const uint64_t chunk = std::max<uint64_t>(c->host_chunk_edges, 1);
   for (uint64_t off = 0; off < c->m; off += chunk) {
     const uint64_t len = std::min(chunk, c->m - off);
     if (cudaMemcpyAsync(c->own_src + off, h_src + off, len * 4, cudaMemcpyHostToDevice,
@@ -902,8 +951,11 @@ static lc_status copy_input_overlapped(lc_ctx* c, const uint32_t* h_src, const u
         cudaEventRecord(c->copy_ev, c->copy_stream) != cudaSuccess ||
         cudaStreamWaitEvent(c->stream, c->copy_ev, 0) != cudaSuccess)
       return LC_ERR_CUDA;
-    if (nb > 1) bucket_count(c->own_src + off, c->own_dst + off, len, c->n, nb,
-                             c->bucket_scratch, err, L);
+    if (c->rs.pre0_chunks > 0)
+      bucket_edges(c->own_src + off, c->own_dst + off, len, c->n, nb, c->ebuf[1] + off,
+                   c->chunk_scratch + (off / chunk) * kChunkScratchWords, err, L);
+    else if (nb > 1)
+      bucket_count(c->own_src + off, c->own_dst + off, len, c->n, nb, c->bucket_scratch, err, L);
     edge_min(c->own_src + off, c->own_dst + off, nullptr, len, c->n, rk, c->minkey, err,
              c->window_bytes, nullptr, L);
   }

@@ -202,6 +202,20 @@ void bucket_place(const uint32_t* src, const uint32_t* dst, uint64_t m, uint32_t
 void bucket_edges(const uint32_t* src, const uint32_t* dst, uint64_t m, uint32_t n, uint32_t nb,
                   uint64_t* out, uint32_t* scratch, unsigned* err, const Launch& L);
 
+// Chunk-local grouping (lc_run_host): chunk c = edges [c * chunk, ...) is
+// grouped on its own into out[c * chunk, ...) with bucket_edges, using
+// chunk_scratch + c * kChunkScratchWords; chunk_tiles then lists, in bucket
+// order and chunk order inside a bucket, tiles of at most tile_edges edges
+// that never cross a (bucket, chunk) run: tiles[2t] = first edge, tiles[2t+1]
+// = end; *ntiles = their number.  `tiles` holds chunk_tiles_bytes(...) bytes;
+// the launch scans nb^2 * chunks segments in one block (keep that small).
+constexpr uint64_t kChunkScratchWords = (uint64_t)kBucketMaxDigits * (1 + kBucketFillStride);
+constexpr uint32_t kRelabelTileEdges = 4096;  // edges per relabel tile (kernel constant)
+uint64_t chunk_tiles_bytes(uint64_t m, uint32_t nb, uint32_t chunks, uint32_t tile_edges);
+void chunk_tiles(const uint32_t* chunk_scratch, uint32_t chunks, uint64_t chunk, uint64_t m,
+                 uint32_t n, uint32_t nb, uint32_t tile_edges, uint64_t* tiles,
+                 unsigned long long* ntiles, unsigned* err, const Launch& L);
+
 // -------------------------------------------- segmented deduplication
 // Large phases: the relabel counts its (mixed) keys per segment, the top
 // kSegBits bits, into scratch[0, kSegs); seg_begin turns the counts into
@@ -349,12 +363,15 @@ void jump(unsigned long long* minkey, uint32_t* root, uint32_t* mo, uint32_t n, 
 // starts; nullptr / 0 = no such cache; a missing key enters it at one in
 // 2^admit of its occurrences).  The written keys hold every distinct key.
 // Tiles are claimed in order through the device word `ticket` (cleared here).
+// Packed edges may come with a tile list (tiles, *d_ntiles: see chunk_tiles),
+// which then replaces the tiles of consecutive edges.
 void relabel(const uint32_t* src, const uint32_t* dst, const uint64_t* packed, uint64_t m,
              uint32_t n, const uint32_t* root, int bits, uint64_t* keys_out,
              unsigned long long* mprime, unsigned long long* emitted, bool mix,
              const PassPlan* plan, uint32_t* ghist, uint64_t* tmp, uint64_t window_bytes,
              unsigned long long* gcache, uint32_t gslots, int admit, unsigned* ticket,
-             unsigned* err, const Launch& L);
+             unsigned* err, const Launch& L, const uint64_t* tiles = nullptr,
+             const unsigned long long* d_ntiles = nullptr);
 
 // labels_out[v] = kept(root[v]) ? labels_up[id(root[v])] : mo[root[v]], with
 // kept and id from the level's keep ranks.  labels_out may alias root.

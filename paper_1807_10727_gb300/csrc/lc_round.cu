@@ -584,6 +584,7 @@ __global__ void k_uf_flatten(const uint32_t* parent, uint32_t* root, uint32_t n,
 // ----------------------------------------------------------- relabel
 
 constexpr int kRelItems = 16;
+static_assert(kThreads * kRelItems == kRelabelTileEdges, "relabel tile size");
 
 __device__ __forceinline__ void relabel_one(uint32_t u, uint32_t v, bool valid, uint32_t n,
                                             const uint32_t* __restrict__ root, int bits,
@@ -667,7 +668,7 @@ __global__ void __launch_bounds__(kThreads) k_relabel(
     int bits, uint64_t* __restrict__ keys_out, unsigned long long* mprime,
     unsigned long long* emitted, int mix, PassPlan plan, uint32_t* __restrict__ ghist,
     unsigned* mprime_err, unsigned long long* gcache, uint32_t gmask, int admit,
-    unsigned* ticket) {
+    unsigned* ticket, const uint64_t* __restrict__ tiles, const unsigned long long* d_ntiles) {
   __shared__ uint64_t cache[kRelCache];
   __shared__ uint32_t hist[3][kRadixMax];
   __shared__ uint32_t ws[kThreads / 32];
@@ -675,7 +676,10 @@ __global__ void __launch_bounds__(kThreads) k_relabel(
   __shared__ unsigned long long s_base;
   __shared__ uint32_t s_t;
   const uint64_t tile_edges = (uint64_t)kThreads * kRelItems;
-  const uint64_t ntiles = (m + tile_edges - 1) / tile_edges;
+  // with a tile list (chunk-local grouping, packed edges only): tile t covers
+  // edges [tiles[2t], tiles[2t+1]), at most tile_edges of them
+  const uint64_t ntiles =
+      (kMode == 1 && tiles != nullptr) ? *d_ntiles : (m + tile_edges - 1) / tile_edges;
   const unsigned tid = threadIdx.x, lane = lane_id(), w = tid >> 5;
   for (int i = tid; i < kRelCache; i += kThreads) cache[i] = ~0ull;
   for (int i = tid; i < 3 * kRadixMax; i += kThreads) (&hist[0][0])[i] = 0;
@@ -689,14 +693,22 @@ __global__ void __launch_bounds__(kThreads) k_relabel(
     __syncthreads();
     const uint64_t t = s_t;
     if (t >= ntiles) break;
+    uint64_t tb = t * tile_edges, te = m;
+    if (kMode == 1 && tiles != nullptr) {
+      tb = tiles[2 * t];
+      te = tiles[2 * t + 1];
+      if (!index_ok(mprime_err, kKRelabelPacked, te, m + 1) ||
+          !index_ok(mprime_err, kKRelabelPacked, te - tb, tile_edges + 1))
+        te = tb;  // corrupted entry: the tile does nothing
+    }
     // thread item i handles edge base + w*32*kRelItems + i*32 + lane (coalesced)
-    const uint64_t base = t * tile_edges + (uint64_t)w * 32 * kRelItems;
+    const uint64_t base = tb + (uint64_t)w * 32 * kRelItems;
     uint64_t key[kRelItems];
     uint32_t keepmask = 0, emitmask = 0;
 #pragma unroll
     for (int i = 0; i < kRelItems; ++i) {
       uint64_t j = base + (uint64_t)i * 32 + lane;
-      bool valid = j < m;
+      bool valid = j < te;
       uint32_t u = 0, v = 0;
       if (valid) {
         if (kMode != 0) {
@@ -959,7 +971,8 @@ void relabel(const uint32_t* src, const uint32_t* dst, const uint64_t* packed, u
              unsigned long long* mprime, unsigned long long* emitted, bool mix,
              const PassPlan* plan, uint32_t* ghist, uint64_t* tmp, uint64_t window_bytes,
              unsigned long long* gcache, uint32_t gslots, int admit, unsigned* ticket,
-             unsigned* err, const Launch& L) {
+             unsigned* err, const Launch& L, const uint64_t* tiles,
+             const unsigned long long* d_ntiles) {
   const uint32_t gmask = gslots ? gslots - 1 : 0;
   if (gslots == 0) gcache = nullptr;
   PassPlan pl{};
@@ -971,7 +984,8 @@ void relabel(const uint32_t* src, const uint32_t* dst, const uint64_t* packed, u
     KScope ks(L, kKRelabelPacked);
     k_relabel<1><<<grid, kThreads, 0, L.stream>>>(nullptr, nullptr, packed, m, n, root, bits,
                                                   keys_out, mprime, emitted, mix, pl, ghist,
-                                                  err, gcache, gmask, admit, ticket);
+                                                  err, gcache, gmask, admit, ticket, tiles,
+                                                  d_ntiles);
   } else if (tmp != nullptr && n < kResolved && (uint64_t)n * 4 > window_bytes) {
     // one pass per L2-sized part of root (see k_relabel_first_half)
     const uint64_t parts = std::min<uint64_t>(8, ((uint64_t)n * 4 + window_bytes - 1) /
@@ -990,12 +1004,13 @@ void relabel(const uint32_t* src, const uint32_t* dst, const uint64_t* packed, u
     KScope ks(L, kKRelabelSoa);
     k_relabel<2><<<grid, kThreads, 0, L.stream>>>(nullptr, nullptr, tmp, m, n, root, bits,
                                                   keys_out, mprime, emitted, mix, pl, ghist,
-                                                  err, gcache, gmask, admit, ticket);
+                                                  err, gcache, gmask, admit, ticket, nullptr,
+                                                  nullptr);
   } else {
     KScope ks(L, kKRelabelSoa);
     k_relabel<0><<<grid, kThreads, 0, L.stream>>>(src, dst, nullptr, m, n, root, bits, keys_out,
                                                   mprime, emitted, mix, pl, ghist, err, gcache,
-                                                  gmask, admit, ticket);
+                                                  gmask, admit, ticket, nullptr, nullptr);
   }
 }
 

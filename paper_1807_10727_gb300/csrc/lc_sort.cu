@@ -1165,6 +1165,89 @@ void bucket_place(const uint32_t* src, const uint32_t* dst, uint64_t m, uint32_t
   k_bucket_scatter<<<sgrid, kSortThreads, 0, L.stream>>>(src, dst, m, n, vec, eb, fill, out, err);
 }
 
+// ---- tiles over chunk-local buckets
+
+// Segment s = d * chunks + c is bucket d of chunk c (bucket order first, so
+// the tiles of one vertex-block pair stay together).  One block: exclusive
+// scan of the segments' tile counts into first[s] (first[segs] = total).
+__global__ void __launch_bounds__(kSortThreads) k_chunk_tile_scan(
+    const uint32_t* __restrict__ chunk_scratch, uint32_t chunks, uint32_t nd, uint32_t tile_edges,
+    uint32_t* __restrict__ first, unsigned long long* ntiles) {
+  __shared__ uint32_t ws[kWarps];
+  const uint32_t segs = nd * chunks;
+  uint32_t carry = 0;
+  for (uint32_t s0 = 0; s0 < segs; s0 += kSortThreads) {
+    const uint32_t s = s0 + threadIdx.x;
+    uint32_t t = 0;
+    if (s < segs) {
+      const uint32_t d = s / chunks, c = s % chunks;
+      const uint32_t cnt = chunk_scratch[(uint64_t)c * kChunkScratchWords + d];
+      t = (cnt + tile_edges - 1) / tile_edges;
+    }
+    uint32_t tot;
+    const uint32_t e = block_exclusive_scan(t, ws, &tot);
+    if (s < segs) first[s] = carry + e;
+    carry += tot;
+  }
+  if (threadIdx.x == 0) {
+    first[segs] = carry;
+    *ntiles = carry;
+  }
+}
+
+// One warp per segment writes its tiles' (first edge, end).
+__global__ void k_chunk_tile_fill(const uint32_t* __restrict__ chunk_scratch, uint32_t chunks,
+                                  uint32_t nd, uint64_t chunk, uint32_t tile_edges,
+                                  const uint32_t* __restrict__ first, uint64_t* __restrict__ tiles,
+                                  uint64_t max_tiles, unsigned* err) {
+  const uint32_t segs = nd * chunks;
+  const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+  for (uint32_t s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; s < segs; s += nw) {
+    const uint32_t d = s / chunks, c = s % chunks;
+    const uint32_t* cs = chunk_scratch + (uint64_t)c * kChunkScratchWords;
+    const uint32_t cnt = cs[d];
+    // after bucket_place, the fill counter of bucket d is its end in the chunk
+    const uint64_t begin = (uint64_t)c * chunk + cs[kBucketMaxDigits + d * kBucketFillStride] - cnt;
+    const uint32_t f = first[s], nt = first[s + 1] - f;
+    for (uint32_t q = lane_id(); q < nt; q += 32) {
+      const uint64_t b = begin + (uint64_t)q * tile_edges;
+      const uint64_t e = b + tile_edges < begin + cnt ? b + tile_edges : begin + cnt;
+      if (index_ok(err, kKBucketEdges, (uint64_t)f + q, max_tiles)) {
+        tiles[2ull * (f + q)] = b;
+        tiles[2ull * (f + q) + 1] = e;
+      }
+    }
+  }
+}
+
+static uint64_t max_chunk_tiles(uint64_t m, uint32_t nd, uint32_t chunks, uint32_t tile_edges) {
+  return m / tile_edges + (uint64_t)nd * chunks + 1;
+}
+
+uint64_t chunk_tiles_bytes(uint64_t m, uint32_t nb, uint32_t chunks, uint32_t tile_edges) {
+  nb = std::max<uint32_t>(2, std::min(nb, kBucketMaxBlocks));
+  const uint64_t nd = (uint64_t)nb * nb;
+  return 16 * max_chunk_tiles(m, (uint32_t)nd, chunks, tile_edges) + 4 * (nd * chunks + 1);
+}
+
+void chunk_tiles(const uint32_t* chunk_scratch, uint32_t chunks, uint64_t chunk, uint64_t m,
+                 uint32_t n, uint32_t nb, uint32_t tile_edges, uint64_t* tiles,
+                 unsigned long long* ntiles, unsigned* err, const Launch& L) {
+  edge_blocks(n, &nb);
+  const uint32_t nd = nb * nb;
+  // the segments' first tiles are kept behind the tiles (see chunk_tiles_bytes)
+  const uint64_t max_tiles = max_chunk_tiles(m, nd, chunks, tile_edges);
+  uint32_t* first = reinterpret_cast<uint32_t*>(tiles + 2 * max_tiles);
+  KScope ks(L, kKBucketEdges);
+  k_chunk_tile_scan<<<1, kSortThreads, 0, L.stream>>>(chunk_scratch, chunks, nd, tile_edges,
+                                                      first, ntiles);
+  const uint32_t segs = nd * chunks;
+  const int grid = (int)std::min<uint64_t>((32ull * segs + kSortThreads - 1) / kSortThreads,
+                                           (uint64_t)L.sms * 8);
+  k_chunk_tile_fill<<<grid, kSortThreads, 0, L.stream>>>(chunk_scratch, chunks, nd, chunk,
+                                                         tile_edges, first, tiles, max_tiles, err);
+}
+
 void seg_begin(uint32_t* scratch, const Launch& L) {
   KScope ks(L, kKSegDedup);
   k_seg_starts<<<1, kSortThreads, 0, L.stream>>>(scratch);

@@ -1,7 +1,7 @@
 """lc_run_host end to end: the input copy overlapped with phase 0 (chunks of
-"host_chunk_edges" edges; each chunk gets the bucket counts of the edge
-grouping and its share of the closed-neighbourhood minimum once it has
-arrived) and the copy-then-run path of the variants that do not overlap.
+"host_chunk_edges" edges; each chunk is grouped by vertex-block pair, or
+only counted beyond the chunk limits, and gets its share of the
+closed-neighbourhood minimum once it has arrived) and the copy-then-run path of the variants that do not overlap.
 Labels, R and every per-phase (n_i, m_i) and m'_i bit-exact against the
 oracle, from pinned and from pageable host arrays."""
 from types import SimpleNamespace
@@ -66,6 +66,16 @@ def test_overlapped_chunks_grouped(lc_lib, cuda, blocks):
     chunks before the edges are placed."""
     g = synth.workload("rmat18")
     check_host(g, [("bucket_blocks", blocks), ("host_chunk_edges", 300007)])
+
+
+@pytest.mark.parametrize("blocks,chunk", [(3, 8192), (32, 220000), (4, (1 << 20) - 3)])
+def test_overlapped_grouping_limits(lc_lib, cuda, blocks, chunk):
+    """Each chunk is grouped on arrival while there are at most 256 chunks
+    and 16384 (bucket, chunk) runs; beyond either limit (512 chunks; 1024
+    buckets x 20 chunks) the chunks are only counted and grouped together
+    afterwards.  The last case has 5 chunks, the last one of 12 edges."""
+    g = synth.workload("rmat18")
+    check_host(g, [("bucket_blocks", blocks), ("host_chunk_edges", chunk)])
 
 
 def test_overlapped_pageable(lc_lib, cuda):
