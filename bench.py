@@ -758,7 +758,8 @@ def main():
         del h_src, h_dst, h_lab
         e2e = {"value": world * g.m / e2e_s, "unit": UNIT,
                "h2d_bytes_per_step": 8 * g.m, "d2h_bytes_per_step": 4 * g.n,
-               "ms_per_step": e2e_s * 1e3, "runs_ms": [round(x, 2) for x in run_ms],
+               "ms_per_step": e2e_s * 1e3, "median_ms": float(np.median(run_ms)),
+               "runs_ms": [round(x, 2) for x in run_ms],
                "h2d_copy_ms": copy_ms,
                "h2d_gbs": 8 * g.m / (copy_ms / 1e3) / 1e9}
         log("e2e: %.2f ms/step" % (e2e_s * 1e3))
