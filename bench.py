@@ -80,7 +80,7 @@ STEP_KERNELS = {
 # algorithmic byte of a step, measured on R-MAT 23 with one-kernel captures
 # of phase 0, keyed by the hash of the CUDA sources they were taken on: a
 # changed kernel invalidates them (the line then reports traffic null).
-TRAFFIC = {"sources": "96f9478dbe27cfc5", "workload": "rmat23",
+TRAFFIC = {"sources": "5671513a3cdfe5d5", "workload": "rmat23",
            "per_alg_byte": {"parent": 3.833, "relabel": 0.875, "dedup": 1.000}}
 
 

@@ -186,6 +186,10 @@ lc_status lc_set_dedup(lc_ctx* ctx, lc_dedup mode);
  *                   by the filter pass.
  *   "seg_dedup"     1 (default) / 0: whether those phases deduplicate by
  *                   segments (below) or by the bucket partition.
+ *   "jump_bits_min_vertices"  phases of at least this many vertices (default
+ *                   2^23) and an average degree below 4 find the roots with
+ *                   a bitmap of the roots (one bit per vertex, in L2) before
+ *                   reading another vertex's parent pointer.
  *   "table_slots"   cap (a power of two >= 2^14, or 0 = none) on the table slots
  *                   the segmented deduplication uses; when the slices do not
  *                   fit at once they are processed in groups, and when one

@@ -309,6 +309,7 @@ struct lc_ctx {
   uint32_t target_permille = 1000;               // scale of the distinct-key estimate (tests)
   uint64_t late_min_edges = 1ull << 22;          // phases this large plan their dedup late
   bool cache_in_relabel = false;                 // segmented phases probe the cache in the relabel
+  uint32_t jump_bits_min_vertices = 1u << 23;    // sparse phases this large chase with a root bitmap
 
   uint32_t max_rounds = 0;  // phase cap (0: 64 + 4 log2 n)
   uint32_t last_rounds = 0;
@@ -690,7 +691,8 @@ static lc_status enqueue_phase(lc_ctx* c) {
       r.lv.mo = nmo;
     } else {
       // (c): roots of the parent arborescences
-      jump(c->minkey, r.lv.root, r.lv.mo, ni, err, L);
+      // (the node-flag bitmap, cleared below, holds the root bitmap meanwhile)
+      jump(c->minkey, r.lv.root, r.lv.mo, ni, mi, c->flags, c->jump_bits_min_vertices, err, L);
     }
   }
   // (d): relabel, drop loops, deduplicate, compact
@@ -1353,6 +1355,11 @@ extern "C" lc_status lc_set_param(lc_ctx* c, const char* name, uint64_t value) {
   if (std::strcmp(name, "cache_in_relabel") == 0) {
     if (value > 1) return LC_ERR_INVALID;
     c->cache_in_relabel = value != 0;
+    return LC_OK;
+  }
+  if (std::strcmp(name, "jump_bits_min_vertices") == 0) {
+    if (value == 0 || value > 0xFFFFFFFFull) return LC_ERR_INVALID;
+    c->jump_bits_min_vertices = (uint32_t)value;
     return LC_OK;
   }
   if (std::strcmp(name, "seg_dedup") == 0) {

@@ -344,11 +344,13 @@ void batch_localize(uint32_t* labels, uint32_t n, const uint32_t* voff, uint32_t
 
 // root[v] = root of v's arborescence (follows the parent stored in the low
 // half of minkey, compressing as it goes); mo[root] = min over the tree of
-// mo[v] (phase 0: mo[v] = v).
+// mo[v] (phase 0: mo[v] = v).  isroot: flag_words(n) words of scratch, which
+// receive a bitmap of the roots when the phase (n vertices, m edges) has at
+// least bits_min_vertices vertices and an average degree below 4.
 // A chase longer than n steps (only possible with corrupted data) stops and
-// sets kErrTimeout.
-void jump(unsigned long long* minkey, uint32_t* root, uint32_t* mo, uint32_t n, unsigned* err,
-          const Launch& L);
+// records the failed index check.
+void jump(unsigned long long* minkey, uint32_t* root, uint32_t* mo, uint32_t n, uint64_t m,
+          uint32_t* isroot, uint32_t bits_min_vertices, unsigned* err, const Launch& L);
 
 // Relabel every edge through root, drop self-loops, emit (min << bits | max)
 // keys (mixed with key_mix when `mix`) compacted to keys_out.  With `plan`

@@ -313,29 +313,54 @@ __global__ void k_batch_localize(uint32_t* __restrict__ labels, uint32_t n,
 
 // ------------------------------------------------------- pointer jumping
 
+// Root bitmap: bit v of isroot is set when v's stored pointer is v itself.
+// Roots stay roots while the chase compresses the other pointers, so the
+// bitmap stays exact during k_jump; at one bit per vertex (8 MB at n = 2^26)
+// it sits in L2, where the 8-byte pointers of a large phase do not.
+__global__ void __launch_bounds__(kThreads) k_root_bits(const unsigned long long* __restrict__ minkey,
+                                                        uint32_t n, uint32_t* __restrict__ isroot) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  // whole warps step together over 32 consecutive vertices (one bitmap word)
+  for (uint64_t v0 = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); v0 < n;
+       v0 += stride) {
+    const uint64_t v = v0 + lane_id();
+    const bool r = v < n && (uint32_t)minkey[v] == (uint32_t)v;
+    const unsigned bits = __ballot_sync(kFull, r);
+    if (lane_id() == 0) isroot[v0 >> 5] = bits;
+  }
+}
+
+// kBits: consult the root bitmap (k_root_bits) before reading a pointer.
+template <bool kBits>
 __global__ void __launch_bounds__(kThreads) k_jump(unsigned long long* minkey,
                                                    uint32_t* __restrict__ root,
-                                                   uint32_t* mo, uint32_t n, unsigned* err) {
+                                                   uint32_t* mo, uint32_t n,
+                                                   const uint32_t* __restrict__ isroot,
+                                                   unsigned* err) {
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
-    uint32_t p = (uint32_t)minkey[v];
-    if (!index_ok(err, kKJump, p, n)) {
+    const uint32_t p0 = (uint32_t)minkey[v];
+    if (!index_ok(err, kKJump, p0, n)) {
       root[v] = (uint32_t)v;
       continue;
     }
+    uint32_t p = p0;
     if (p != (uint32_t)v) {
       // every stored pointer leads to an ancestor, so chasing ends at the
       // root (the only vertex whose stored pointer is itself) within n steps;
-      // the checks only guard against corrupted data
+      // with kBits the root bitmap answers "is p a root" from L2, so a vertex
+      // whose parent is a root reads no other vertex's pointer; the checks
+      // only guard against corrupted data
       uint32_t steps = 0;
-      for (;;) {
-        uint32_t q = (uint32_t)minkey[p];
+      while (!kBits || !((__ldg(isroot + (p >> 5)) >> (p & 31u)) & 1u)) {
+        const uint32_t q = (uint32_t)minkey[p];
         if (q == p) break;
         if (!index_ok(err, kKJump, q, n) || !index_ok(err, kKJump, ++steps, (uint64_t)n + 1))
           break;
         p = q;
       }
-      minkey[v] = p;  // compress: later chases through v go straight to the root
+      // compress: later chases through v go straight to the root
+      if (p != p0) minkey[v] = p;
       min_if_lower(&mo[p], mo[v]);
     }
     root[v] = p;
@@ -959,11 +984,22 @@ void batch_localize(uint32_t* labels, uint32_t n, const uint32_t* voff, uint32_t
   k_batch_localize<<<grid, kThreads, 0, L.stream>>>(labels, n, voff, k, chunk);
 }
 
-void jump(unsigned long long* minkey, uint32_t* root, uint32_t* mo, uint32_t n, unsigned* err,
-          const Launch& L) {
+void jump(unsigned long long* minkey, uint32_t* root, uint32_t* mo, uint32_t n, uint64_t m,
+          uint32_t* isroot, uint32_t bits_min_vertices, unsigned* err, const Launch& L) {
   if (n == 0) return;
   KScope ks(L, kKJump);
-  k_jump<<<grid_for(n, kThreads, L), kThreads, 0, L.stream>>>(minkey, root, mo, n, err);
+  // The bitmap pays when the pointers do not fit L2 and the forest is deep
+  // and scattered, as on sparse graphs (grids, meshes: average degree below
+  // 4); on skewed dense graphs most parents are a few hubs, whose pointers
+  // L2 already holds, and the extra pass and bitmap reads only cost.
+  if (isroot != nullptr && n >= bits_min_vertices && m < 4ull * n) {
+    k_root_bits<<<grid_for(n, kThreads, L), kThreads, 0, L.stream>>>(minkey, n, isroot);
+    k_jump<true><<<grid_for(n, kThreads, L), kThreads, 0, L.stream>>>(minkey, root, mo, n,
+                                                                      isroot, err);
+  } else {
+    k_jump<false><<<grid_for(n, kThreads, L), kThreads, 0, L.stream>>>(minkey, root, mo, n,
+                                                                       nullptr, err);
+  }
 }
 
 void relabel(const uint32_t* src, const uint32_t* dst, const uint64_t* packed, uint64_t m,

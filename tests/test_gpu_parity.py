@@ -1,6 +1,8 @@
 """GPU path (through the C ABI of liblc.so) against the CPU oracle: labels,
 phase count and every per-phase (n_i, m_i) bit-exact, plus the diagnostic m'_i.
 """
+from types import SimpleNamespace
+
 import numpy as np
 import pytest
 
@@ -267,3 +269,29 @@ def test_round_cap_and_wait_timeout(lc_lib, cuda):
     assert res.rounds == ref.rounds and list(zip(res.n_i, res.m_i)) == ref.sizes()
     assert np.array_equal(labels.cpu().numpy().view(np.uint32), ref.labels)
     ctx.close()
+
+
+@pytest.mark.parametrize("name", ["gridmix_small", "er16", "path"])
+def test_root_bitmap_jump(lc_lib, cuda, name):
+    """The pointer chase with the root bitmap (forced on small phases; taken
+    only by phases whose average degree is below 4) gives the oracle's
+    result, also on a long path (deep parent chains)."""
+    if name == "path":
+        n = 100000
+        perm = np.random.default_rng(4).permutation(n).astype(np.uint32)
+        g = SimpleNamespace(n=n, src=perm[:-1].copy(), dst=perm[1:].copy(), seed=9)
+    else:
+        g = synth.workload(name)
+    src, dst = dev(g.src, cuda), dev(g.dst, cuda)
+    ctx = lc.LocalContraction(g.n, src, dst, seed=g.seed, tuned=False)
+    try:
+        ctx.set_param("jump_bits_min_vertices", 1)
+        labels, res = ctx.run()
+        labels2, res2 = ctx.run()
+    finally:
+        ctx.close()
+    ref = oracle.lc_run(g.n, g.src, g.dst, g.seed)
+    for lab, r in ((labels, res), (labels2, res2)):
+        assert r.rounds == ref.rounds
+        assert list(zip(r.n_i, r.m_i)) == ref.sizes()
+        assert np.array_equal(lab.cpu().numpy().view(np.uint32), ref.labels)
