@@ -1,9 +1,10 @@
 """Autotuner of the library's speed parameters, per graph-size class.
 
-The parameters (lc_set_param: vertex blocks of the phase-0 edge buckets,
-size and admission of the device-wide duplicate cache, the edge count from
-which phases plan their deduplication late, segmented or bucket-partition
-deduplication) change the speed of a run, never its result.  For each size
+The parameters (lc_set_param: vertex blocks of the phase-0 edge buckets and
+whether phase 0 groups its edges at all, size and admission of the
+device-wide duplicate cache, the edge count from which phases plan their
+deduplication late, segmented or bucket-partition deduplication) change the
+speed of a run, never its result.  For each size
 class, represented by one synthetic graph of the benchmark's recipes (or,
 for the batch class, the benchmark's batch of 4096 graphs run as one), this
 script times whole runs (CUDA events, after warm-up) and improves the
@@ -41,6 +42,7 @@ CANDIDATES = {
     "relabel_cache_admit": [3, 2, 4],
     "late_min_edges": [1 << 22, 1 << 20, 1 << 24],
     "seg_dedup": [1, 0],
+    "bucket_blocks": [0, 1],  # phase-0 edge grouping: automatic, or off
 }
 
 # size classes: one workload each (synth.workload names; "batch<k>": synth.batch(k))
