@@ -233,8 +233,10 @@ lc_status lc_run(lc_ctx* ctx, uint32_t* d_labels, uint32_t* rounds, uint64_t* n_
  * minimum (forest and two-hop variants, no union-find finish in phase 0) the
  * copy overlaps phase 0: the edges go over in chunks of "host_chunk_edges"
  * on a second stream of the context, and each chunk, as soon as it has
- * arrived, is grouped by vertex-block pair (up to 256 chunks; more chunks
- * only get phase 0's bucket counts) and gets its share of the minimum
+ * arrived, is grouped by vertex-block pair (up to 256 chunks and 16384
+ * (bucket, chunk) runs; beyond that the chunks only get phase 0's bucket
+ * counts and all edges are grouped once they are in) and gets its share of
+ * the minimum
  * (Section 2's parent over N(v); a minimum of atomic updates, the same in
  * any order).  The chunk-local grouping takes 132 KB of device memory per
  * chunk and a relabel tile list of 16 bytes per 4096 edges, allocated at the
