@@ -233,17 +233,15 @@ lc_status lc_run(lc_ctx* ctx, uint32_t* d_labels, uint32_t* rounds, uint64_t* n_
  * minimum (forest and two-hop variants, no union-find finish in phase 0) the
  * copy overlaps phase 0: the edges go over in chunks of "host_chunk_edges"
  * on a second stream of the context, and each chunk, as soon as it has
- * arrived, is grouped by vertex-block pair (up to 256 chunks and 16384
- * (bucket, chunk) runs; beyond that the chunks only get phase 0's bucket
- * counts and all edges are grouped once they are in) and gets its share of
- * the minimum
- * (Section 2's parent over N(v); a minimum of atomic updates, the same in
- * any order).  The chunk-local grouping takes 132 KB of device memory per
- * chunk and a relabel tile list of 16 bytes per 4096 edges, allocated at the
- * first such call (LC_ERR_OOM if that fails).  The result is the one lc_run
- * gives on the same edges.  Pinned
- * host buffers give full copy speed; pageable ones are staged by the CUDA
- * runtime. */
+ * arrived, is grouped by vertex-block pair and gets its share of the minimum
+ * (Section 2's parent over N(v); a minimum of atomic updates, the same in any
+ * order).  Beyond 256 chunks or 16384 (bucket, chunk) runs the chunks only
+ * get phase 0's bucket counts and all edges are grouped once they are in.
+ * The chunk-local grouping takes 132 KB of device memory per chunk and a
+ * relabel tile list of 16 bytes per 4096 edges, allocated at the first such
+ * call (LC_ERR_OOM if that fails).  The result is the one lc_run gives on the
+ * same edges.  Pinned host buffers give full copy speed; pageable ones are
+ * staged by the CUDA runtime. */
 lc_status lc_run_host(lc_ctx* ctx, const uint32_t* h_src, const uint32_t* h_dst,
                       uint32_t* h_labels, uint32_t* rounds, uint64_t* n_i, uint64_t* m_i,
                       uint32_t cap);
