@@ -1,8 +1,8 @@
 """Autotuner of the library's speed parameters, per graph-size class.
 
 The parameters (lc_set_param: vertex blocks of the phase-0 edge buckets and
-whether phase 0 groups its edges at all, size and admission of the
-device-wide duplicate cache, the edge count from which phases plan their
+whether phase 0 groups its edges at all, the vertex window of the ungrouped
+minimum, size and admission of the device-wide duplicate cache, the edge count from which phases plan their
 deduplication late, segmented or bucket-partition deduplication) change the
 speed of a run, never its result.  For each size
 class, represented by one synthetic graph of the benchmark's recipes (or,
@@ -43,6 +43,7 @@ CANDIDATES = {
     "late_min_edges": [1 << 22, 1 << 20, 1 << 24],
     "seg_dedup": [1, 0],
     "bucket_blocks": [0, 1],  # phase-0 edge grouping: automatic, or off
+    "window_bytes": [192 << 20, 2 << 30],  # ungrouped minimum: L2-sized windows, or one pass
 }
 
 # size classes: one workload each (synth.workload names; "batch<k>": synth.batch(k))
